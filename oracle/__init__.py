@@ -1,0 +1,209 @@
+"""CPU oracle for the GraphZeppelin hot path -- TEST INFRASTRUCTURE ONLY.
+
+A plain, slow, single-threaded restatement (``gz_oracle.c``) of CubeSketch
+ingestion (Fig. cube_code, Eq. 1-2) and Boruvka connected components over node
+sketches (Section 2.2; Lemma (CC I/O) proof), plus brute-force connected
+components of the net graph (the adjacency-bit-vector check of Section 6.3).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU baseline /
+reference leg may import this package.  It shares no code with the CUDA
+library in ``paper_2203_14927_b300``; both follow the same written definitions.
+Parity pins for every function live in ``tests/test_oracle.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gz_oracle.c")
+_LIB = os.path.join(_HERE, "libgz_oracle.so")
+
+COLS = 7
+EMPTY = -1
+FAIL = -2
+NOT_ROOT = -3
+NOT_RUN = -4
+
+
+def build(force: bool = False) -> str:
+    """Compile gz_oracle.c into libgz_oracle.so (plain gcc, -O2)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-Wextra", "-shared",
+                               "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        u64, u32, sz, p = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_size_t, ctypes.c_void_p
+        L.gzo_splitmix64_at.restype = u64
+        L.gzo_splitmix64_at.argtypes = [u64, u64]
+        L.gzo_fmix64.restype = u64
+        L.gzo_fmix64.argtypes = [u64]
+        L.gzo_h1.restype = u64
+        L.gzo_h1.argtypes = [u64, u64, u64]
+        L.gzo_h2.restype = u32
+        L.gzo_h2.argtypes = [u64, u64]
+        L.gzo_geometry.restype = ctypes.c_int
+        L.gzo_geometry.argtypes = [u32, p, p]
+        L.gzo_keys.restype = None
+        L.gzo_keys.argtypes = [u64, u32, p, p, p]
+        L.gzo_ingest.restype = ctypes.c_int
+        L.gzo_ingest.argtypes = [u32, u64, sz, p, p, p, p]
+        L.gzo_sketch_node.restype = ctypes.c_int
+        L.gzo_sketch_node.argtypes = [u32, u64, u32, sz, p, p, p]
+        L.gzo_query_vector.restype = ctypes.c_int64
+        L.gzo_query_vector.argtypes = [u32, u64, u32, p, p]
+        L.gzo_boruvka.restype = ctypes.c_int
+        L.gzo_boruvka.argtypes = [u32, u64, p, p, p, p, p, p, p]
+        L.gzo_brute_cc.restype = ctypes.c_int
+        L.gzo_brute_cc.argtypes = [u32, sz, p, p, p]
+        L.gzo_cc_edges.restype = ctypes.c_int
+        L.gzo_cc_edges.argtypes = [u32, sz, p, p, p]
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def geometry(V: int) -> tuple[int, int]:
+    """(K, R): CubeSketches per node and rows per column."""
+    K = np.zeros(1, np.uint32)
+    R = np.zeros(1, np.uint32)
+    if lib().gzo_geometry(V, _ptr(K), _ptr(R)) != 0:
+        raise ValueError(f"V={V} must be >= 2")
+    return int(K[0]), int(R[0])
+
+
+def keys(seed: int, K: int):
+    a = np.zeros(K * COLS, np.uint64)
+    b = np.zeros(K * COLS, np.uint64)
+    c = np.zeros(K * COLS, np.uint64)
+    lib().gzo_keys(seed, K, _ptr(a), _ptr(b), _ptr(c))
+    return a, b, c
+
+
+def splitmix64_at(seed: int, n: int) -> int:
+    return int(lib().gzo_splitmix64_at(seed, n))
+
+
+def fmix64(x: int) -> int:
+    return int(lib().gzo_fmix64(x))
+
+
+def h1(a: int, b: int, x: int) -> int:
+    return int(lib().gzo_h1(a, b, x))
+
+
+def h2(c: int, x: int) -> int:
+    return int(lib().gzo_h2(c, x))
+
+
+def empty_sketches(V: int, nodes: int | None = None):
+    """Zeroed nested-form sketches for `nodes` nodes (default V):
+    alpha[node][k][j][row] u64 and gamma[node][k][j][row] u32."""
+    K, R = geometry(V)
+    n = V if nodes is None else nodes
+    return (np.zeros((n, K, COLS, R), np.uint64), np.zeros((n, K, COLS, R), np.uint32))
+
+
+def ingest(V: int, seed: int, u, v, alpha=None, gamma=None):
+    """Apply the stream (u[i], v[i]) to all V node sketches (nested form)."""
+    u = np.ascontiguousarray(u, np.uint32)
+    v = np.ascontiguousarray(v, np.uint32)
+    if alpha is None:
+        alpha, gamma = empty_sketches(V)
+    rc = lib().gzo_ingest(V, seed, len(u), _ptr(u), _ptr(v), _ptr(alpha), _ptr(gamma))
+    if rc != 0:
+        raise ValueError(f"gzo_ingest returned {rc}")
+    return alpha, gamma
+
+
+def sketch_node(V: int, seed: int, node: int, nbrs):
+    """Nested-form sketch of one node from its net neighbour list."""
+    K, R = geometry(V)
+    nbrs = np.ascontiguousarray(nbrs, np.uint32)
+    a = np.zeros((K, COLS, R), np.uint64)
+    g = np.zeros((K, COLS, R), np.uint32)
+    rc = lib().gzo_sketch_node(V, seed, node, len(nbrs), _ptr(nbrs), _ptr(a), _ptr(g))
+    if rc != 0:
+        raise ValueError(f"gzo_sketch_node returned {rc}")
+    return a, g
+
+
+def query_vector(V: int, seed: int, k: int, A, G) -> int:
+    """query_sketch of Fig. cube_code on one CubeSketch ([j][row] arrays)."""
+    A = np.ascontiguousarray(A, np.uint64)
+    G = np.ascontiguousarray(G, np.uint32)
+    return int(lib().gzo_query_vector(V, seed, k, _ptr(A), _ptr(G)))
+
+
+def boruvka(V: int, seed: int, alpha, gamma):
+    """Boruvka over node sketches.  Returns a dict with labels (min vertex id
+    per component), forest (n,2) in acceptance order, samples (K,V) per
+    round and component, stats and the return code (1 = possible failure)."""
+    K, _ = geometry(V)
+    labels = np.zeros(V, np.uint32)
+    forest = np.zeros(2 * max(V - 1, 1), np.uint32)
+    nf = np.zeros(1, np.uint64)
+    samples = np.zeros(K * V, np.int64)
+    stats = np.zeros(4, np.uint64)
+    rc = lib().gzo_boruvka(V, seed, _ptr(alpha), _ptr(gamma), _ptr(labels), _ptr(forest),
+                           _ptr(nf), _ptr(samples), _ptr(stats))
+    if rc < 0:
+        raise ValueError(f"gzo_boruvka returned {rc}")
+    n = int(nf[0])
+    return {
+        "labels": labels,
+        "forest": forest[: 2 * n].reshape(n, 2).copy(),
+        "samples": samples.reshape(K, V),
+        "rounds": int(stats[0]),
+        "fails_last": int(stats[1]),
+        "exhausted": int(stats[2]),
+        "n_components": int(stats[3]),
+        "rc": rc,
+    }
+
+
+def brute_cc(V: int, u, v) -> np.ndarray:
+    """Min-id component labels of the net graph of the stream (bit vector)."""
+    u = np.ascontiguousarray(u, np.uint32)
+    v = np.ascontiguousarray(v, np.uint32)
+    labels = np.zeros(V, np.uint32)
+    rc = lib().gzo_brute_cc(V, len(u), _ptr(u), _ptr(v), _ptr(labels))
+    if rc != 0:
+        raise ValueError(f"gzo_brute_cc returned {rc}")
+    return labels
+
+
+def cc_edges(V: int, u, v) -> np.ndarray:
+    """Min-id component labels of the graph with the given edge list."""
+    u = np.ascontiguousarray(u, np.uint32)
+    v = np.ascontiguousarray(v, np.uint32)
+    labels = np.zeros(V, np.uint32)
+    rc = lib().gzo_cc_edges(V, len(u), _ptr(u), _ptr(v), _ptr(labels))
+    if rc != 0:
+        raise ValueError(f"gzo_cc_edges returned {rc}")
+    return labels
+
+
+def to_exact(alpha_nested: np.ndarray) -> np.ndarray:
+    """Nested rows -> exact-depth rows (row i XOR row i+1): the inverse of the
+    suffix-XOR that defines the nested form; used by tests only."""
+    out = alpha_nested.copy()
+    out[..., :-1] ^= alpha_nested[..., 1:]
+    return out
