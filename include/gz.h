@@ -1,0 +1,183 @@
+/*
+ * gz.h -- C ABI of the B300 GraphZeppelin hot path.
+ *
+ * GraphZeppelin (Tench et al., SIGMOD 2022, arXiv 2203.14927) answers
+ * connected-components queries on a graph given as a stream of edge
+ * insertions and deletions, by keeping one "node sketch" per vertex: K
+ * CubeSketch l0-samplers of the vertex's characteristic vector (Section 2.2,
+ * Section 3.2) and running Boruvka's algorithm on the sketches when queried.
+ * This library keeps every node sketch resident in device memory and runs
+ * ingestion and queries in CUDA kernels for sm_103a.
+ *
+ * Conventions shared by every call:
+ *   - Return value: gz_status.  GZ_OK on success.  On any other value a
+ *     one-line reason is available from gz_last_error(handle).
+ *   - Pointers: "host" pointers are ordinary CPU memory (pinned memory gives
+ *     faster copies); "device" pointers are CUDA global memory of the device
+ *     current when the handle was created.  Buffers stay owned by the caller.
+ *   - Streams: all device work of a handle is issued on the handle's CUDA
+ *     stream (gz_create / gz_set_stream; NULL = the legacy default stream).
+ *     Calls return once the work is queued unless stated otherwise.
+ *   - Threading: a handle must not be used by two threads at once; distinct
+ *     handles are independent and may be driven concurrently.
+ *   - Geometry (readings of Section 5.1 and Table tab:size): every node sketch
+ *     holds K = ceil(log_{3/2} V) CubeSketches of 7 columns x R rows,
+ *     R = 2*ceil(log2 V); a bucket is a 64-bit alpha and a 32-bit gamma, so a
+ *     node sketch takes K*7*R*12 bytes.
+ *   - Edge index of an unordered pair {u,v}: idx = min*V + max (a position
+ *     of the characteristic vector of Section 2.2).
+ */
+#ifndef GZ_H
+#define GZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gz_handle gz_handle;
+
+typedef enum {
+    GZ_OK = 0,
+    GZ_EINVAL = 1,       /* bad argument, or a rejected update batch */
+    GZ_ENOMEM = 2,       /* device or host allocation failed */
+    GZ_ECUDA = 3,        /* a CUDA call failed; see gz_last_error */
+    GZ_ESKETCH_FAIL = 4, /* query finished but a sketch failed (result may be wrong) */
+    GZ_ETIMEOUT = 5,     /* reserved: a bounded device wait ran out */
+    GZ_EBUSY = 6         /* reserved */
+} gz_status;
+
+/* Ingestion kernel choice. */
+enum {
+    GZ_KERNEL_BATCHED = 0, /* partition by endpoint + per-node batched update (default) */
+    GZ_KERNEL_PLAIN = 1    /* one thread per (update, column), global atomics */
+};
+
+/* Tuning knobs; a zero field takes the built-in default. */
+typedef struct {
+    uint32_t chunk_log2;    /* updates processed per partition pass = 2^chunk_log2 (default 24) */
+    uint32_t kernel;        /* GZ_KERNEL_BATCHED or GZ_KERNEL_PLAIN */
+    uint32_t smem_rows;     /* exact-depth rows staged in shared memory (default 16, max 32) */
+    uint32_t tile_records;  /* records per work tile of the batched kernel (default 1024) */
+    uint32_t ctas_per_sm;   /* resident CTAs per SM of the persistent batched kernel (default: max) */
+    uint32_t small_segment; /* node segments shorter than this skip shared-memory staging (default 4) */
+    uint32_t reserved[6];
+} gz_config;
+
+/* Statistics of the last query. */
+typedef struct {
+    uint32_t rounds;        /* Boruvka rounds run */
+    uint32_t fails_last;    /* components whose CubeSketch failed in the last round run */
+    uint32_t exhausted;     /* 1 when round K-1 still produced merges */
+    uint32_t n_components;  /* connected components reported */
+    uint32_t fails_total;   /* FAIL results summed over all rounds */
+    uint32_t reserved;
+    float ms;               /* wall time of the query, host clock, milliseconds */
+} gz_query_stats;
+
+/* Geometry for V vertices: K CubeSketches per node, R rows per column.
+ * Returns GZ_EINVAL for V < 2 or V > 2^31. */
+gz_status gz_geometry(uint32_t V, uint32_t *K, uint32_t *R);
+
+/* Bytes of device memory a handle for V vertices holds (sketches + scratch)
+ * under cfg (may be NULL). */
+gz_status gz_memory_bytes(uint32_t V, const gz_config *cfg, size_t *bytes);
+
+/* Allocate zeroed node sketches for V vertices with hash keys derived from
+ * seed (Section 5, initialisation: "allocates log(V) CubeSketches per node").
+ * cfg may be NULL.  stream is a cudaStream_t (NULL = default stream).
+ * On success *out owns V*K*7*R*12 bytes of device memory plus scratch. */
+gz_status gz_create(uint32_t V, uint64_t seed, const gz_config *cfg,
+                    void *stream, gz_handle **out);
+
+/* Free everything the handle owns (synchronises its stream first). */
+gz_status gz_destroy(gz_handle *h);
+
+/* Change the stream later work is issued on. */
+gz_status gz_set_stream(gz_handle *h, void *stream);
+
+/* Apply n updates: update i toggles edge {u[i], v[i]} in the sketches of both
+ * endpoints (Section 2.2; Fig. cube_code update_sketch; Delta is implicit
+ * because the vectors live in Z_2, Section 3.2).  An insert and a delete of
+ * the same edge are the same toggle; the caller keeps the stream valid in the
+ * sense of Section 2.1 (insert only absent edges, delete only present ones).
+ *   u, v       : n vertex ids each; host memory if on_device == 0, else device
+ *                memory.  Any order of endpoints is accepted.
+ *   Validation : an update with u == v or an id >= V invalidates its batch;
+ *                a batch is the whole call when n <= 2^chunk_log2, else each
+ *                consecutive slice of 2^chunk_log2 updates.  An invalid batch
+ *                is discarded whole before any sketch changes.  Validation
+ *                runs on the device, so the call itself returns GZ_OK and the
+ *                error is reported as GZ_EINVAL by the next gz_sync, query or
+ *                export call on this handle.
+ *   Ownership  : host inputs may be reused when the call returns; device
+ *                inputs must stay unchanged until the handle's stream has
+ *                completed the work queued by this call. */
+gz_status gz_edge_update(gz_handle *h, const uint32_t *u, const uint32_t *v,
+                         size_t n, int on_device);
+
+/* Wait for all queued work of the handle; returns GZ_EINVAL once if a batch
+ * was rejected since the last report. */
+gz_status gz_sync(gz_handle *h);
+
+/* Zero every node sketch (the empty graph). */
+gz_status gz_reset(gz_handle *h);
+
+/* Connected components by Boruvka over the sketches (Section 2.2; the three
+ * phases of each round in the proof of Lemma (CC I/O)): round r samples one
+ * edge per component from CubeSketch r of the XOR of its members' sketches,
+ * then merges.  Synchronous.
+ *   labels : host, V entries, or NULL: labels[x] = minimum vertex id of x's
+ *            component.
+ *   n_cc   : host, or NULL: number of components.
+ *   st     : host, or NULL: statistics.
+ * Returns GZ_ESKETCH_FAIL (labels still filled) when a component's sketch had
+ * no usable bucket in the last round run, or all K rounds still merged. */
+gz_status gz_connected_components(gz_handle *h, uint32_t *labels, uint32_t *n_cc,
+                                  gz_query_stats *st);
+
+/* Spanning forest by the same Boruvka rounds (list_spanning_forest of
+ * Section 5).  uv: host, 2*(V-1) entries; edges are written as (u,v) pairs
+ * with u < v, round by round and, within a round, by ascending component id
+ * (the order in which a sequential union-find over the sampled edges accepts
+ * them).  *n_edges = V - number of components.  labels may be NULL.
+ * Synchronous; same return values as gz_connected_components. */
+gz_status gz_list_spanning_forest(gz_handle *h, uint32_t *uv, size_t *n_edges,
+                                  uint32_t *labels, gz_query_stats *st);
+
+/* Per-round samples of the last query, for checking: out[r*V + c] for round
+ * r < K and vertex c = the sampled edge index of component c (c its minimum
+ * vertex id), -1 when the component's sketch was empty, -2 on FAIL, -3 when c
+ * was not a component id in that round, -4 when round r was not run.
+ * out: host, K*V entries.  Only filled when the query ran after
+ * gz_enable_trace(h, 1). */
+gz_status gz_enable_trace(gz_handle *h, int enable);
+gz_status gz_query_trace(gz_handle *h, int64_t *out);
+
+/* Copy node sketches [node_lo, node_hi) in the paper's NESTED form (bucket
+ * (i,j) = XOR over indices e with h1(e) = 0 mod 2^i, Eq. 1-2) to
+ * alpha[node][k][j][row] (u64) and gamma[node][k][j][row] (u32), rows
+ * ascending.  on_device selects device (1) or host (0) output buffers.
+ * Synchronous. */
+gz_status gz_export_sketch(gz_handle *h, uint32_t node_lo, uint32_t node_hi,
+                           uint64_t *alpha, uint32_t *gamma, int on_device);
+
+/* Geometry and device pointer of the raw sketch array of a handle (exact-
+ * depth form, layout per node: for each k, alpha[row][j] then gamma[row][j]).
+ * Any output pointer may be NULL. */
+gz_status gz_info(gz_handle *h, uint32_t *V, uint32_t *K, uint32_t *R,
+                  size_t *node_bytes, void **sketch_device);
+
+/* Human-readable reason of the last non-OK status (never NULL). */
+const char *gz_last_error(gz_handle *h);
+
+/* Library version string. */
+const char *gz_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GZ_H */

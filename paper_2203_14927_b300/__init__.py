@@ -1,0 +1,259 @@
+"""GraphZeppelin hot path on B300: Python binding of the C ABI in include/gz.h.
+
+Argument marshalling only -- every step (validation, partition by endpoint,
+CubeSketch updates, Boruvka rounds) runs in the CUDA library ``libgz.so``
+built from ``csrc/`` for sm_103a.  There is no CPU fallback: importing works
+without a GPU, but creating a Graph needs the library and a CUDA device.
+
+    g = Graph(V=1 << 13, seed=1)
+    g.edge_update(u, v)            # torch CUDA tensors, or host numpy arrays
+    labels, n_cc, stats = g.connected_components()
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgz.so")
+
+GZ_OK, GZ_EINVAL, GZ_ENOMEM, GZ_ECUDA, GZ_ESKETCH_FAIL, GZ_ETIMEOUT, GZ_EBUSY = range(7)
+KERNELS = {"batched": 0, "plain": 1}
+COLS = 7
+
+
+class GzError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"gz status {status}: {msg}")
+        self.status = status
+
+
+class SketchFailure(GzError):
+    """The query finished but a CubeSketch failed; results are best effort."""
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("chunk_log2", ctypes.c_uint32),
+        ("kernel", ctypes.c_uint32),
+        ("smem_rows", ctypes.c_uint32),
+        ("tile_records", ctypes.c_uint32),
+        ("ctas_per_sm", ctypes.c_uint32),
+        ("small_segment", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 6),
+    ]
+
+
+class QueryStats(ctypes.Structure):
+    _fields_ = [
+        ("rounds", ctypes.c_uint32),
+        ("fails_last", ctypes.c_uint32),
+        ("exhausted", ctypes.c_uint32),
+        ("n_components", ctypes.c_uint32),
+        ("fails_total", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+        ("ms", ctypes.c_float),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+_lib = None
+
+# name -> (restype, argtypes); every symbol of include/gz.h
+_SIGNATURES = {
+    "gz_version": (ctypes.c_char_p, []),
+    "gz_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "gz_geometry": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
+    "gz_memory_bytes": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
+    "gz_create": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p]),
+    "gz_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "gz_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gz_edge_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                      ctypes.c_int]),
+    "gz_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "gz_reset": (ctypes.c_int, [ctypes.c_void_p]),
+    "gz_connected_components": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p]),
+    "gz_list_spanning_forest": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p]),
+    "gz_enable_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "gz_query_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gz_export_sketch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int]),
+    "gz_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_void_p, ctypes.c_void_p]),
+}
+
+
+def lib():
+    """Load libgz.so (raises if it was not built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing; build it with "
+                               "`python -m paper_2203_14927_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def geometry(V: int) -> tuple[int, int]:
+    K = ctypes.c_uint32()
+    R = ctypes.c_uint32()
+    if lib().gz_geometry(V, ctypes.byref(K), ctypes.byref(R)) != GZ_OK:
+        raise ValueError(f"invalid V={V}")
+    return K.value, R.value
+
+
+def _buffer(x):
+    """(pointer, n, on_device, keepalive) of a 1-D uint32/int32 array."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(x, torch.Tensor):
+        if x.dtype not in (torch.int32, torch.uint32):
+            raise TypeError("update tensors must be int32 or uint32")
+        x = x.contiguous().reshape(-1)
+        return x.data_ptr(), x.numel(), 1 if x.is_cuda else 0, x
+    a = np.ascontiguousarray(x, dtype=np.uint32).reshape(-1)
+    return a.ctypes.data, a.size, 0, a
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # pragma: no cover
+        pass
+    return 0
+
+
+class Graph:
+    """Node sketches of one dynamic graph resident on the current CUDA device."""
+
+    def __init__(self, V: int, seed: int = 0, *, kernel: str = "batched", chunk_log2: int = 0,
+                 smem_rows: int = 0, tile_records: int = 0, ctas_per_sm: int = 0,
+                 small_segment: int = 0, stream=None):
+        cfg = Config()
+        cfg.chunk_log2 = chunk_log2
+        cfg.kernel = KERNELS[kernel]
+        cfg.smem_rows = smem_rows
+        cfg.tile_records = tile_records
+        cfg.ctas_per_sm = ctas_per_sm
+        cfg.small_segment = small_segment
+        self._h = ctypes.c_void_p()
+        s = _current_stream() if stream is None else stream
+        st = lib().gz_create(V, seed & ((1 << 64) - 1), ctypes.byref(cfg), ctypes.c_void_p(s),
+                             ctypes.byref(self._h))
+        if st != GZ_OK:
+            raise GzError(st, f"gz_create(V={V}) failed")
+        self.V = V
+        self.seed = seed
+        self.K, self.R = geometry(V)
+
+    # -- plumbing --------------------------------------------------------------
+    def _check(self, st: int, what: str):
+        if st == GZ_OK:
+            return
+        msg = lib().gz_last_error(self._h).decode()
+        if st == GZ_ESKETCH_FAIL:
+            raise SketchFailure(st, f"{what}: {msg}")
+        raise GzError(st, f"{what}: {msg}")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().gz_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream: int):
+        self._check(lib().gz_set_stream(self._h, ctypes.c_void_p(stream)), "gz_set_stream")
+
+    # -- ingestion ---------------------------------------------------------------
+    def edge_update(self, u, v):
+        pu, nu, du, ku = _buffer(u)
+        pv, nv, dv, kv = _buffer(v)
+        if nu != nv or du != dv:
+            raise ValueError("u and v must have equal length and live on the same side")
+        self._check(lib().gz_edge_update(self._h, ctypes.c_void_p(pu), ctypes.c_void_p(pv), nu, du),
+                    "gz_edge_update")
+        return ku, kv
+
+    def sync(self):
+        self._check(lib().gz_sync(self._h), "gz_sync")
+
+    def reset(self):
+        self._check(lib().gz_reset(self._h), "gz_reset")
+
+    # -- queries -------------------------------------------------------------------
+    def connected_components(self, raise_on_failure: bool = False):
+        labels = np.zeros(self.V, np.uint32)
+        ncc = ctypes.c_uint32()
+        st = QueryStats()
+        rc = lib().gz_connected_components(self._h, labels.ctypes.data_as(ctypes.c_void_p),
+                                           ctypes.byref(ncc), ctypes.byref(st))
+        if rc != GZ_ESKETCH_FAIL or raise_on_failure:
+            self._check(rc, "gz_connected_components")
+        d = st.as_dict()
+        d["status"] = rc
+        return labels, ncc.value, d
+
+    def list_spanning_forest(self, raise_on_failure: bool = False):
+        uv = np.zeros(2 * max(self.V - 1, 1), np.uint32)
+        n = ctypes.c_size_t()
+        labels = np.zeros(self.V, np.uint32)
+        st = QueryStats()
+        rc = lib().gz_list_spanning_forest(self._h, uv.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n),
+                                           labels.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st))
+        if rc != GZ_ESKETCH_FAIL or raise_on_failure:
+            self._check(rc, "gz_list_spanning_forest")
+        d = st.as_dict()
+        d["status"] = rc
+        return uv[: 2 * n.value].reshape(-1, 2).copy(), labels, d
+
+    def enable_trace(self, on: bool = True):
+        self._check(lib().gz_enable_trace(self._h, 1 if on else 0), "gz_enable_trace")
+
+    def query_trace(self) -> np.ndarray:
+        out = np.zeros(self.K * self.V, np.int64)
+        self._check(lib().gz_query_trace(self._h, out.ctypes.data_as(ctypes.c_void_p)), "gz_query_trace")
+        return out.reshape(self.K, self.V)
+
+    def export_sketch(self, lo: int = 0, hi: int | None = None):
+        """Nested-form sketches of nodes [lo, hi): alpha/gamma [node][k][j][row]."""
+        hi = self.V if hi is None else hi
+        a = np.zeros((hi - lo, self.K, COLS, self.R), np.uint64)
+        g = np.zeros((hi - lo, self.K, COLS, self.R), np.uint32)
+        self._check(lib().gz_export_sketch(self._h, lo, hi, a.ctypes.data_as(ctypes.c_void_p),
+                                           g.ctypes.data_as(ctypes.c_void_p), 0), "gz_export_sketch")
+        return a, g
+
+    def info(self) -> dict:
+        V, K, R = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        nb = ctypes.c_size_t()
+        ptr = ctypes.c_void_p()
+        self._check(lib().gz_info(self._h, ctypes.byref(V), ctypes.byref(K), ctypes.byref(R),
+                                  ctypes.byref(nb), ctypes.byref(ptr)), "gz_info")
+        return {"V": V.value, "K": K.value, "R": R.value, "node_bytes": nb.value, "sketch_ptr": ptr.value}

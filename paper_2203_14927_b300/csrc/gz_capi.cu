@@ -1,0 +1,300 @@
+// gz_capi.cu -- the extern "C" entry points declared in include/gz.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/gz.h"
+#include "gz_handle.cuh"
+
+namespace gz {
+
+gz_status set_error(gz_handle* h, gz_status s, const std::string& msg) {
+    if (h) h->err = msg;
+    return s;
+}
+
+gz_status cuda_check(gz_handle* h, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return GZ_OK;
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return set_error(h, GZ_ENOMEM, m);
+    return set_error(h, GZ_ECUDA, m);
+}
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the n-th output (n >= 0) of
+// the generator whose state starts at `state`.
+static uint64_t splitmix_nth(uint64_t state, uint64_t n) {
+    uint64_t z = state + 0x9E3779B97F4A7C15ull * (n + 1);
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z;
+}
+
+static bool geometry(uint32_t V, uint32_t* K, uint32_t* R) {
+    if (V < 2 || V > (1u << 31)) return false;
+    uint32_t L = 0;
+    while ((1ull << L) < V) ++L;
+    // least k with (3/2)^k >= V  <=>  3^k >= V * 2^k
+    unsigned __int128 lhs = 1, rhs = V;
+    uint32_t k = 0;
+    while (lhs < rhs) {
+        lhs *= 3;
+        rhs *= 2;
+        ++k;
+    }
+    *K = k;
+    *R = 2 * L;
+    return true;
+}
+
+static size_t scratch_bytes(uint32_t V, uint64_t chunk) {
+    return (size_t)3 * (V + 1) * 4 + (size_t)2 * chunk * 4 + 64;
+}
+
+}  // namespace gz
+
+using namespace gz;
+
+extern "C" {
+
+const char* gz_version(void) { return "gz-b300 0.1 (sm_103a)"; }
+
+const char* gz_last_error(gz_handle* h) {
+    if (!h) return "null handle";
+    return h->err.c_str();
+}
+
+gz_status gz_geometry(uint32_t V, uint32_t* K, uint32_t* R) {
+    uint32_t k, r;
+    if (!gz::geometry(V, &k, &r)) return GZ_EINVAL;
+    if (K) *K = k;
+    if (R) *R = r;
+    return GZ_OK;
+}
+
+gz_status gz_memory_bytes(uint32_t V, const gz_config* cfg, size_t* bytes) {
+    uint32_t K, R;
+    if (!gz::geometry(V, &K, &R) || !bytes) return GZ_EINVAL;
+    const uint32_t cl = cfg && cfg->chunk_log2 ? cfg->chunk_log2 : 24;
+    const uint64_t chunk = 1ull << cl;
+    *bytes = (size_t)V * K * 84ull * R + (size_t)K * 7 * 24 + scratch_bytes(V, chunk);
+    return GZ_OK;
+}
+
+gz_status gz_create(uint32_t V, uint64_t seed, const gz_config* cfg, void* stream, gz_handle** out) {
+    if (!out) return GZ_EINVAL;
+    *out = nullptr;
+    uint32_t K, R;
+    if (!gz::geometry(V, &K, &R)) return GZ_EINVAL;
+    gz_handle* h = new (std::nothrow) gz_handle();
+    if (!h) return GZ_ENOMEM;
+    if (cfg) h->cfg = *cfg;
+    if (h->cfg.chunk_log2 == 0) h->cfg.chunk_log2 = 24;
+    if (h->cfg.chunk_log2 < 8 || h->cfg.chunk_log2 > 30 || h->cfg.kernel > GZ_KERNEL_PLAIN) {
+        delete h;
+        return GZ_EINVAL;
+    }
+    h->V = V;
+    h->K = K;
+    h->R = R;
+    h->ncol = K * GZ_COLS;
+    h->seed = seed;
+    h->per_k_bytes = 84u * R;
+    h->node_bytes = (uint64_t)K * h->per_k_bytes;
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->chunk = 1ull << h->cfg.chunk_log2;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    gz_status s = cuda_check(h, e, "device query");
+    if (s != GZ_OK) {
+        delete h;
+        return s;
+    }
+    // keys: a (odd), b, c per column, from SplitMix64 outputs 3*col, 3*col+1, 3*col+2
+    const size_t ncol = h->ncol;
+    uint64_t* hk = new (std::nothrow) uint64_t[3 * ncol];
+    if (!hk) {
+        delete h;
+        return GZ_ENOMEM;
+    }
+    for (size_t col = 0; col < ncol; ++col) {
+        hk[col] = splitmix_nth(seed, 3 * col) | 1ull;
+        hk[ncol + col] = splitmix_nth(seed, 3 * col + 1);
+        hk[2 * ncol + col] = splitmix_nth(seed, 3 * col + 2);
+    }
+    const size_t sk = (size_t)V * h->node_bytes;
+    e = cudaMalloc(&h->d_sketch, sk);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_sketch, 0, sk, h->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_keys, 3 * ncol * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_keys, hk, 3 * ncol * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    delete[] hk;
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_counts, (size_t)(V + 1) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_offsets, (size_t)(V + 1) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_cursor, (size_t)(V + 1) * 4);
+    if (e == cudaSuccess && h->cfg.kernel == GZ_KERNEL_BATCHED)
+        e = cudaMalloc(&h->d_records, (size_t)2 * h->chunk * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_flags, 16);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, 16, h->stream);
+    s = cuda_check(h, e, "gz_create allocation");
+    if (s == GZ_OK) s = ingest_setup(h);
+    if (s != GZ_OK) {
+        gz_destroy(h);
+        return s;
+    }
+    *out = h;
+    return GZ_OK;
+}
+
+gz_status gz_destroy(gz_handle* h) {
+    if (!h) return GZ_EINVAL;
+    cudaStreamSynchronize(h->stream);
+    void* ptrs[] = {h->d_sketch, h->d_keys, h->d_counts, h->d_offsets, h->d_cursor, h->d_records,
+                    h->d_stage, h->d_flags, h->q_label, h->q_parent, h->q_count, h->q_off,
+                    h->q_cursor, h->q_members, h->q_roots, h->q_target, h->q_item_base,
+                    h->q_item_cnt, h->q_item_comp, h->q_item_lo, h->q_item_hi, h->q_F, h->q_F2,
+                    h->q_M, h->q_M2, h->q_flag, h->q_pos, h->q_forest, h->q_ctr, h->q_res,
+                    h->q_partial, h->q_trace};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->h_ctr) cudaFreeHost(h->h_ctr);
+    delete h;
+    return GZ_OK;
+}
+
+gz_status gz_set_stream(gz_handle* h, void* stream) {
+    if (!h) return GZ_EINVAL;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return GZ_OK;
+}
+
+gz_status gz_edge_update(gz_handle* h, const uint32_t* u, const uint32_t* v, size_t n, int on_device) {
+    if (!h) return GZ_EINVAL;
+    if (n == 0) return GZ_OK;
+    if (!u || !v) return set_error(h, GZ_EINVAL, "null update arrays");
+    if (!on_device && !h->d_stage) {
+        cudaError_t e = cudaMalloc(&h->d_stage, (size_t)2 * h->chunk * 4);
+        if (e != cudaSuccess) return cuda_check(h, e, "staging allocation");
+    }
+    for (size_t off = 0; off < n; off += h->chunk) {
+        const uint64_t m = std::min<uint64_t>(h->chunk, n - off);
+        const uint32_t *du = u + off, *dv = v + off;
+        if (!on_device) {
+            cudaError_t e = cudaMemcpyAsync(h->d_stage, u + off, m * 4, cudaMemcpyHostToDevice, h->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h->d_stage + h->chunk, v + off, m * 4, cudaMemcpyHostToDevice, h->stream);
+            if (e != cudaSuccess) return cuda_check(h, e, "update copy");
+            du = h->d_stage;
+            dv = h->d_stage + h->chunk;
+        }
+        gz_status s = ingest_batch(h, du, dv, m);
+        if (s != GZ_OK) return s;
+    }
+    if (!on_device) {
+        // host buffers may be pageable: do not return before the copies are done
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_check(h, e, "update sync");
+    }
+    return GZ_OK;
+}
+
+static gz_status check_rejected(gz_handle* h) {
+    uint32_t f = 0;
+    cudaError_t e = cudaMemcpyAsync(&f, h->d_flags + 2, 4, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "sync");
+    if (f) {
+        cudaMemsetAsync(h->d_flags + 2, 0, 4, h->stream);
+        return set_error(h, GZ_EINVAL, "an update batch held a self loop or a vertex id >= V and was discarded");
+    }
+    return GZ_OK;
+}
+
+gz_status gz_sync(gz_handle* h) {
+    if (!h) return GZ_EINVAL;
+    return check_rejected(h);
+}
+
+gz_status gz_reset(gz_handle* h) {
+    if (!h) return GZ_EINVAL;
+    cudaError_t e = cudaMemsetAsync(h->d_sketch, 0, (size_t)h->V * h->node_bytes, h->stream);
+    return cuda_check(h, e, "reset");
+}
+
+gz_status gz_connected_components(gz_handle* h, uint32_t* labels, uint32_t* n_cc, gz_query_stats* st) {
+    if (!h) return GZ_EINVAL;
+    gz_status s = check_rejected(h);
+    if (s != GZ_OK) return s;
+    return boruvka(h, false, labels, nullptr, nullptr, n_cc, st);
+}
+
+gz_status gz_list_spanning_forest(gz_handle* h, uint32_t* uv, size_t* n_edges, uint32_t* labels,
+                                  gz_query_stats* st) {
+    if (!h) return GZ_EINVAL;
+    gz_status s = check_rejected(h);
+    if (s != GZ_OK) return s;
+    uint32_t ncc = 0;
+    return boruvka(h, true, labels, uv, n_edges, &ncc, st);
+}
+
+gz_status gz_enable_trace(gz_handle* h, int enable) {
+    if (!h) return GZ_EINVAL;
+    h->trace = enable != 0;
+    h->trace_valid = false;
+    return GZ_OK;
+}
+
+gz_status gz_query_trace(gz_handle* h, int64_t* out) {
+    if (!h || !out) return GZ_EINVAL;
+    if (!h->trace_valid || !h->q_trace) return set_error(h, GZ_EINVAL, "no traced query to report");
+    cudaError_t e = cudaMemcpy(out, h->q_trace, (size_t)h->K * h->V * sizeof(int64_t), cudaMemcpyDeviceToHost);
+    return cuda_check(h, e, "trace copy");
+}
+
+gz_status gz_export_sketch(gz_handle* h, uint32_t node_lo, uint32_t node_hi, uint64_t* alpha,
+                           uint32_t* gamma, int on_device) {
+    if (!h || !alpha || !gamma) return GZ_EINVAL;
+    if (node_lo > node_hi || node_hi > h->V) return set_error(h, GZ_EINVAL, "node range out of bounds");
+    gz_status s = check_rejected(h);
+    if (s != GZ_OK) return s;
+    const size_t n = (size_t)(node_hi - node_lo) * h->ncol * h->R;
+    if (n == 0) return GZ_OK;
+    uint64_t* da = alpha;
+    uint32_t* dg = gamma;
+    if (!on_device) {
+        cudaError_t e = cudaMalloc(&da, n * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&dg, n * 4);
+        if (e != cudaSuccess) return cuda_check(h, e, "export scratch");
+    }
+    s = export_nested(h, node_lo, node_hi, da, dg);
+    cudaError_t e = cudaSuccess;
+    if (s == GZ_OK && !on_device) {
+        e = cudaMemcpyAsync(alpha, da, n * 8, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(gamma, dg, n * 4, cudaMemcpyDeviceToHost, h->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (!on_device) {
+        cudaFree(da);
+        cudaFree(dg);
+    }
+    if (s != GZ_OK) return s;
+    return cuda_check(h, e, "export");
+}
+
+gz_status gz_info(gz_handle* h, uint32_t* V, uint32_t* K, uint32_t* R, size_t* node_bytes,
+                  void** sketch_device) {
+    if (!h) return GZ_EINVAL;
+    if (V) *V = h->V;
+    if (K) *K = h->K;
+    if (R) *R = h->R;
+    if (node_bytes) *node_bytes = h->node_bytes;
+    if (sketch_device) *sketch_device = h->d_sketch;
+    return GZ_OK;
+}
+
+}  // extern "C"

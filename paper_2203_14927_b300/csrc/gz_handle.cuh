@@ -1,0 +1,77 @@
+// gz_handle.cuh -- host-side state of one graph (one gz_handle) and the internal
+// launch entry points shared by the library's .cu files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gz.h"
+#include "gz_internal.cuh"
+
+struct gz_handle {
+    // geometry
+    uint32_t V = 0, K = 0, R = 0, ncol = 0;  // ncol = 7K columns
+    uint64_t seed = 0;
+    uint64_t node_bytes = 0;
+    uint32_t per_k_bytes = 0;
+    gz_config cfg{};
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+
+    // sketches (exact-depth form) and hash keys (3 arrays of 7K)
+    uint8_t* d_sketch = nullptr;
+    uint64_t* d_keys = nullptr;
+
+    // ingestion scratch
+    uint64_t chunk = 0;            // updates per partition pass
+    uint32_t* d_counts = nullptr;  // V+1
+    uint32_t* d_offsets = nullptr; // V+1
+    uint32_t* d_cursor = nullptr;  // V
+    uint32_t* d_records = nullptr; // 2*chunk
+    uint32_t* d_stage = nullptr;   // 2*chunk, host-input staging (lazy)
+    uint32_t* d_flags = nullptr;   // [0] batch invalid, [1] sticky invalid, [2] work counter
+    uint32_t block = 0;            // columns padded to a warp multiple
+    uint32_t smem_rows = 0, tile = 0, small_seg = 0, batched_grid = 0;
+    size_t batched_smem = 0;
+
+    // query scratch (allocated on first query)
+    bool query_ready = false;
+    uint32_t *q_label = nullptr, *q_parent = nullptr, *q_count = nullptr, *q_off = nullptr,
+             *q_cursor = nullptr, *q_members = nullptr, *q_roots = nullptr, *q_target = nullptr,
+             *q_item_base = nullptr, *q_item_cnt = nullptr, *q_item_comp = nullptr,
+             *q_item_lo = nullptr, *q_item_hi = nullptr, *q_F = nullptr, *q_F2 = nullptr,
+             *q_M = nullptr, *q_M2 = nullptr, *q_flag = nullptr, *q_pos = nullptr,
+             *q_forest = nullptr, *q_ctr = nullptr, *h_ctr = nullptr;
+    int64_t* q_res = nullptr;
+    uint8_t* q_partial = nullptr;
+    uint32_t q_items_cap = 0, q_M_members = 0;
+    int64_t* q_trace = nullptr;
+    bool trace = false;
+    bool trace_valid = false;
+
+    std::string err;
+};
+
+namespace gz {
+
+gz_status set_error(gz_handle* h, gz_status s, const std::string& msg);
+gz_status cuda_check(gz_handle* h, cudaError_t e, const char* what);
+
+// ingestion (gz_ingest.cu)
+gz_status ingest_setup(gz_handle* h);
+gz_status ingest_batch(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, uint64_t n);
+gz_status export_nested(gz_handle* h, uint32_t lo, uint32_t hi, uint64_t* d_alpha,
+                        uint32_t* d_gamma);
+
+// query (gz_query.cu)
+gz_status query_setup(gz_handle* h);
+gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* forest_uv,
+                  size_t* n_edges, uint32_t* n_cc, gz_query_stats* st);
+
+// single-CTA exclusive scan: out[0..n] with out[n] = total; out2 (optional) = copy of out[0..n)
+void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* out2, uint32_t n, cudaStream_t s);
+
+}  // namespace gz

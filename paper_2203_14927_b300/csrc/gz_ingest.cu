@@ -1,0 +1,374 @@
+// gz_ingest.cu -- stream ingestion: CubeSketch updates of every node touched by a
+// batch of edge updates (Fig. cube_code update_sketch; Section 5.1 "Sketch
+// updates").
+//
+// The paper buffers updates per node (leaf-only gutters, Section 5.1) and lets
+// Graph Workers apply one node's batch at a time.  Here one batch of updates is
+// partitioned by endpoint on the device (histogram, exclusive scan, scatter: each
+// update lands in the segment of both endpoints with the other endpoint as the
+// record), and a persistent kernel walks fixed-size tiles of the partitioned
+// records.  For every node segment in its tile a CTA keeps a zeroed delta sketch
+// of the first `Rs` exact-depth rows in shared memory (one thread per CubeSketch
+// column, so no shared-memory atomics), applies the segment, then XORs the
+// touched rows into the node's sketch in global memory with red.global.xor --
+// the "apply to an empty sketch, then add" step of Section 5.1 (linearity), which
+// also lets two CTAs share one heavy node whose segment spans tiles.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "gz_handle.cuh"
+#include "gz_internal.cuh"
+
+namespace gz {
+
+// ------------------------------------------------------------------ partition
+
+// Validation + endpoint histogram.  flags[0] = this batch is invalid,
+// flags[2] = sticky "some batch was invalid" (reported by gz_sync).
+__global__ void k_validate_count(const uint32_t* __restrict__ u, const uint32_t* __restrict__ v,
+                                 uint64_t n, uint32_t V, uint32_t* __restrict__ counts,
+                                 uint32_t* __restrict__ flags) {
+    bool bad = false;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t a = u[i], b = v[i];
+        if (a == b || a >= V || b >= V) {
+            bad = true;
+            continue;
+        }
+        if (counts) {
+            atomicAdd(&counts[a], 1u);
+            atomicAdd(&counts[b], 1u);
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) {
+        atomicOr(&flags[0], 1u);
+        atomicOr(&flags[2], 1u);
+    }
+}
+
+// Exclusive scan of n counts by one CTA: out[i] = sum in[0..i), out[n] = total;
+// out2 (optional) receives out[0..n) as well (the scatter cursors).
+__global__ void __launch_bounds__(1024) k_scan(const uint32_t* __restrict__ in,
+                                               uint32_t* __restrict__ out,
+                                               uint32_t* __restrict__ out2, uint32_t n) {
+    __shared__ uint32_t warp_sum[32];
+    const uint32_t T = blockDim.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint32_t per = (n + T - 1) / T;
+    const uint32_t lo = min(tid * per, n), hi = min(lo + per, n);
+    uint32_t s = 0;
+    for (uint32_t i = lo; i < hi; ++i) s += in[i];
+    uint32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    if (lane == 31) warp_sum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t ws = lane < T / 32 ? warp_sum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, ws, o);
+            if (lane >= (uint32_t)o) ws += y;
+        }
+        warp_sum[lane] = ws;
+    }
+    __syncthreads();
+    uint32_t excl = x - s + (w ? warp_sum[w - 1] : 0);
+    for (uint32_t i = lo; i < hi; ++i) {
+        out[i] = excl;
+        if (out2) out2[i] = excl;
+        excl += in[i];
+    }
+    if (tid == T - 1) out[n] = excl;
+}
+
+void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* out2, uint32_t n, cudaStream_t s) {
+    k_scan<<<1, 1024, 0, s>>>(in, out, out2, n);
+}
+
+// Scatter: record of update (a,b) in a's segment is b and in b's segment is a.
+__global__ void k_scatter(const uint32_t* __restrict__ u, const uint32_t* __restrict__ v, uint64_t n,
+                          uint32_t* __restrict__ cursor, uint32_t* __restrict__ records,
+                          const uint32_t* __restrict__ flags) {
+    if (flags[0]) return;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t a = u[i], b = v[i];
+        records[atomicAdd(&cursor[a], 1u)] = b;
+        records[atomicAdd(&cursor[b], 1u)] = a;
+    }
+}
+
+// ------------------------------------------------------------------ batched update
+
+struct BatchedArgs {
+    SketchView s;
+    Keys keys;
+    const uint32_t* offsets;  // V+1
+    const uint32_t* records;
+    const uint32_t* flags;
+    uint32_t* work;  // tile counter
+    uint32_t V, K, R, ncol, Rs, tile, small_seg;
+};
+
+// One CTA = 32*ceil(7K/32) threads; thread c owns CubeSketch column c = 7k + j.
+// Dynamic shared memory: delta alpha[Rs][CP] u64, staged indices [tile] u64,
+// delta gamma[Rs][CP] u32, per-k deepest touched row [K] u32.  With the
+// [row][column] layout a warp's 32 lanes hit 32 distinct banks whatever rows
+// their updates land in.
+__global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
+    extern __shared__ __align__(16) uint64_t smem[];
+    __shared__ uint32_t s_tile, s_node;
+    if (p.flags[0]) return;
+    const uint32_t CP = blockDim.x, c = threadIdx.x;
+    uint64_t* dA = smem;
+    uint64_t* sidx = dA + (size_t)p.Rs * CP;
+    uint32_t* dG = reinterpret_cast<uint32_t*>(sidx + p.tile);
+    uint32_t* maxd = dG + (size_t)p.Rs * CP;
+
+    const bool active = c < p.ncol;
+    const uint32_t k = c / GZ_COLS, j = c - k * GZ_COLS;
+    uint64_t ka = 0, kb = 0, kc = 0;
+    if (active) {
+        ka = p.keys.a[c];
+        kb = p.keys.b[c];
+        kc = p.keys.c[c];
+    }
+    for (uint32_t i = c; i < p.Rs * CP; i += CP) {
+        dA[i] = 0;
+        dG[i] = 0;
+    }
+    for (uint32_t i = c; i < p.K; i += CP) maxd[i] = 0;
+    const uint32_t total = p.offsets[p.V];
+    const uint32_t ntiles = (total + p.tile - 1) / p.tile;
+    const uint32_t Rs = p.Rs, R = p.R;
+
+    for (;;) {
+        __syncthreads();
+        if (c == 0) {
+            const uint32_t t = atomicAdd(p.work, 1u);
+            s_tile = t;
+            if (t < ntiles) {
+                // node x with offsets[x] <= t*tile < offsets[x+1]
+                const uint32_t lo = t * p.tile;
+                uint32_t L = 0, H = p.V;
+                while (H - L > 1) {
+                    const uint32_t mid = (L + H) >> 1;
+                    if (p.offsets[mid] <= lo) L = mid; else H = mid;
+                }
+                s_node = L;
+            }
+        }
+        __syncthreads();
+        const uint32_t t = s_tile;
+        if (t >= ntiles) break;
+        const uint32_t lo = t * p.tile, hi = min(lo + p.tile, total);
+        uint32_t x = s_node, pos = lo;
+        while (pos < hi) {
+            const uint32_t seg_end = min(p.offsets[x + 1], hi);
+            const uint32_t nseg = seg_end - pos;
+            if (nseg > 0) {
+                for (uint32_t i = c; i < nseg; i += CP) sidx[i] = edge_index(x, p.records[pos + i], p.V);
+                __syncthreads();
+                if (nseg < p.small_seg) {
+                    // short segment: straight to global memory
+                    if (active) {
+                        for (uint32_t i = 0; i < nseg; ++i) {
+                            const uint64_t idx = sidx[i];
+                            const uint32_t d = exact_depth(depth_word(ka, kb, idx), R);
+                            atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, d, j)),
+                                      (unsigned long long)idx);
+                            atomicXor(p.s.gamma(x, k, d, j), checksum(kc, idx));
+                        }
+                    }
+                } else {
+                    uint32_t md = 0;
+                    if (active) {
+#pragma unroll 4
+                        for (uint32_t i = 0; i < nseg; ++i) {
+                            const uint64_t idx = sidx[i];
+                            const uint64_t tw = depth_word(ka, kb, idx);
+                            const uint32_t d = __clz(static_cast<uint32_t>(tw >> 32));
+                            const uint32_t g = checksum(kc, idx);
+                            if (d < Rs) {
+                                dA[d * CP + c] ^= idx;
+                                dG[d * CP + c] ^= g;
+                                md = max(md, d);
+                            } else {
+                                const uint32_t dd = exact_depth(tw, R);
+                                atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, dd, j)),
+                                          (unsigned long long)idx);
+                                atomicXor(p.s.gamma(x, k, dd, j), g);
+                            }
+                        }
+                        atomicMax(&maxd[k], md);
+                    }
+                    __syncthreads();
+                    const uint32_t per_k = Rs * GZ_COLS;
+                    for (uint32_t q = c; q < p.K * per_k; q += CP) {
+                        const uint32_t kk = q / per_k, rem = q - kk * per_k;
+                        const uint32_t row = rem / GZ_COLS, jj = rem - row * GZ_COLS;
+                        if (row <= maxd[kk]) {
+                            const uint32_t slot = row * CP + kk * GZ_COLS + jj;
+                            const uint64_t a = dA[slot];
+                            const uint32_t g = dG[slot];
+                            if (a | g) {
+                                atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, kk, row, jj)),
+                                          (unsigned long long)a);
+                                atomicXor(p.s.gamma(x, kk, row, jj), g);
+                                dA[slot] = 0;
+                                dG[slot] = 0;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                    for (uint32_t i = c; i < p.K; i += CP) maxd[i] = 0;
+                }
+                __syncthreads();
+            }
+            pos = seg_end;
+            ++x;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ plain update
+
+// The per-update baseline: thread c of a CTA handles column c of every update
+// the CTA visits and XORs straight into both endpoints' sketches with global
+// atomics (no buffering; the unbuffered configuration of Section 6.5).
+__global__ void __launch_bounds__(1024) k_plain(const uint32_t* __restrict__ u,
+                                                const uint32_t* __restrict__ v, uint64_t n,
+                                                SketchView s, Keys keys, uint32_t V, uint32_t R,
+                                                uint32_t ncol, const uint32_t* __restrict__ flags) {
+    if (flags[0]) return;
+    const uint32_t c = threadIdx.x;
+    if (c >= ncol) return;
+    const uint32_t k = c / GZ_COLS, j = c - k * GZ_COLS;
+    const uint64_t ka = keys.a[c], kb = keys.b[c], kc = keys.c[c];
+    for (uint64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const uint32_t a = u[i], b = v[i];
+        const uint64_t idx = edge_index(a, b, V);
+        const uint32_t d = exact_depth(depth_word(ka, kb, idx), R);
+        const uint32_t g = checksum(kc, idx);
+        atomicXor(reinterpret_cast<unsigned long long*>(s.alpha(a, k, d, j)), (unsigned long long)idx);
+        atomicXor(s.gamma(a, k, d, j), g);
+        atomicXor(reinterpret_cast<unsigned long long*>(s.alpha(b, k, d, j)), (unsigned long long)idx);
+        atomicXor(s.gamma(b, k, d, j), g);
+    }
+}
+
+// ------------------------------------------------------------------ export
+
+// Nested rows (Eq. 1-2) of nodes [lo, hi): thread per (node, k, j), suffix XOR
+// from row R-1 down to row 0.  Output layout [node][k][j][row].
+__global__ void k_export(SketchView s, uint32_t lo, uint32_t hi, uint32_t K, uint32_t R,
+                         uint64_t* __restrict__ oa, uint32_t* __restrict__ og) {
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t ncols = (uint64_t)K * GZ_COLS;
+    if (gid >= (uint64_t)(hi - lo) * ncols) return;
+    const uint32_t node = lo + (uint32_t)(gid / ncols);
+    const uint32_t col = (uint32_t)(gid % ncols);
+    const uint32_t k = col / GZ_COLS, j = col - k * GZ_COLS;
+    uint64_t acc = 0;
+    uint32_t accg = 0;
+    for (int row = (int)R - 1; row >= 0; --row) {
+        acc ^= *s.alpha(node, k, row, j);
+        accg ^= *s.gamma(node, k, row, j);
+        oa[gid * R + row] = acc;
+        og[gid * R + row] = accg;
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+static SketchView view_of(const gz_handle* h) {
+    SketchView s;
+    s.base = h->d_sketch;
+    s.node_bytes = h->node_bytes;
+    s.per_k_bytes = h->per_k_bytes;
+    s.gamma_off = 56u * h->R;
+    return s;
+}
+
+static Keys keys_of(const gz_handle* h) {
+    Keys k;
+    k.a = h->d_keys;
+    k.b = h->d_keys + h->ncol;
+    k.c = h->d_keys + 2 * (size_t)h->ncol;
+    return k;
+}
+
+gz_status ingest_setup(gz_handle* h) {
+    h->block = (h->ncol + 31) / 32 * 32;
+    if (h->block > 1024) return set_error(h, GZ_EINVAL, "too many CubeSketch columns for one CTA");
+    uint32_t rs = h->cfg.smem_rows ? h->cfg.smem_rows : 16;
+    rs = std::min<uint32_t>(rs, 32);
+    rs = std::min<uint32_t>(rs, h->R);
+    h->smem_rows = rs;
+    h->tile = h->cfg.tile_records ? h->cfg.tile_records : 1024;
+    h->small_seg = h->cfg.small_segment ? h->cfg.small_segment : 4;
+    h->batched_smem = (size_t)rs * h->block * 12 + (size_t)h->tile * 8 + (size_t)h->K * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)h->batched_smem);
+    if (e != cudaSuccess) return cuda_check(h, e, "cudaFuncSetAttribute(k_batched)");
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batched, (int)h->block, h->batched_smem);
+    if (e != cudaSuccess) return cuda_check(h, e, "occupancy(k_batched)");
+    if (nb < 1) return set_error(h, GZ_EINVAL, "batched kernel does not fit on an SM");
+    uint32_t per_sm = h->cfg.ctas_per_sm ? std::min<uint32_t>(h->cfg.ctas_per_sm, nb) : nb;
+    h->batched_grid = per_sm * h->sm_count;
+    return GZ_OK;
+}
+
+gz_status ingest_batch(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, uint64_t n) {
+    if (n == 0) return GZ_OK;
+    cudaStream_t st = h->stream;
+    cudaError_t e = cudaMemsetAsync(h->d_flags, 0, 2 * sizeof(uint32_t), st);  // batch flag + work
+    if (e != cudaSuccess) return cuda_check(h, e, "memset flags");
+    const uint32_t tpb = 256;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>((n + tpb - 1) / tpb, (uint64_t)h->sm_count * 8);
+    if (h->cfg.kernel == GZ_KERNEL_PLAIN) {
+        k_validate_count<<<grid, tpb, 0, st>>>(d_u, d_v, n, h->V, nullptr, h->d_flags);
+        const uint32_t pg = (uint32_t)std::min<uint64_t>(n, (uint64_t)h->sm_count * 16);
+        k_plain<<<pg, h->block, 0, st>>>(d_u, d_v, n, view_of(h), keys_of(h), h->V, h->R, h->ncol,
+                                         h->d_flags);
+    } else {
+        e = cudaMemsetAsync(h->d_counts, 0, (size_t)(h->V + 1) * sizeof(uint32_t), st);
+        if (e != cudaSuccess) return cuda_check(h, e, "memset counts");
+        k_validate_count<<<grid, tpb, 0, st>>>(d_u, d_v, n, h->V, h->d_counts, h->d_flags);
+        launch_scan(h->d_counts, h->d_offsets, h->d_cursor, h->V, st);
+        k_scatter<<<grid, tpb, 0, st>>>(d_u, d_v, n, h->d_cursor, h->d_records, h->d_flags);
+        BatchedArgs a;
+        a.s = view_of(h);
+        a.keys = keys_of(h);
+        a.offsets = h->d_offsets;
+        a.records = h->d_records;
+        a.flags = h->d_flags;
+        a.work = h->d_flags + 1;
+        a.V = h->V;
+        a.K = h->K;
+        a.R = h->R;
+        a.ncol = h->ncol;
+        a.Rs = h->smem_rows;
+        a.tile = h->tile;
+        a.small_seg = h->small_seg;
+        k_batched<<<h->batched_grid, h->block, h->batched_smem, st>>>(a);
+    }
+    return cuda_check(h, cudaGetLastError(), "ingest launch");
+}
+
+gz_status export_nested(gz_handle* h, uint32_t lo, uint32_t hi, uint64_t* d_alpha, uint32_t* d_gamma) {
+    const uint64_t threads = (uint64_t)(hi - lo) * h->ncol;
+    if (threads == 0) return GZ_OK;
+    const uint32_t tpb = 256;
+    k_export<<<(uint32_t)((threads + tpb - 1) / tpb), tpb, 0, h->stream>>>(view_of(h), lo, hi, h->K,
+                                                                          h->R, d_alpha, d_gamma);
+    return cuda_check(h, cudaGetLastError(), "export launch");
+}
+
+}  // namespace gz

@@ -1,0 +1,175 @@
+"""GPU path vs the CPU oracle, through the C ABI.
+
+Sketches must match bit for bit (integer XOR arithmetic, no tolerance), the
+component labels exactly, and the per-round Boruvka samples and the spanning
+forest exactly (both are fixed once the sketches are: Fig. cube_code's scan
+order picks the sample, and the forest is the sequential acceptance order).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2203_14927_b300 as gz
+from paper_2203_14927_b300 import streams as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, np.uint32).view(np.int32)).cuda()
+
+
+def _gpu_graph(V, seed, u, v, on_device=True, **cfg):
+    g = gz.Graph(V, seed, **cfg)
+    if on_device:
+        g.edge_update(_dev(u), _dev(v))
+    else:
+        g.edge_update(u, v)
+    g.sync()
+    return g
+
+
+def _assert_same_sketches(g, A, G, lo=0, hi=None):
+    a, gg = g.export_sketch(lo, hi)
+    hi = g.V if hi is None else hi
+    assert np.array_equal(a, A[lo:hi]), "alpha differs"
+    assert np.array_equal(gg, G[lo:hi]), "gamma differs"
+
+
+def _assert_same_query(g, A, G, seed):
+    want = oracle.boruvka(g.V, seed, A, G)
+    g.enable_trace(True)
+    forest, labels, st = g.list_spanning_forest()
+    assert np.array_equal(labels, want["labels"])
+    assert st["rounds"] == want["rounds"]
+    assert st["fails_last"] == want["fails_last"]
+    trace = g.query_trace()
+    assert np.array_equal(trace, want["samples"])
+    assert np.array_equal(forest, want["forest"])
+    labels2, ncc, st2 = g.connected_components()
+    assert np.array_equal(labels2, want["labels"]) and ncc == want["n_components"]
+    return want
+
+
+@pytest.mark.parametrize("kernel", ["batched", "plain"])
+def test_planted_small_config_bit_exact(kernel):
+    # V = 2^10, 8 planted G(n_i, 0.1) components, 20% extra pairs cycled so
+    # that the stream has ~2e5 updates
+    spec = S.PlantedSpec(V=1024, seed=11, n_comp=8, p=0.1, extra=0.2, cycles=74)
+    u, v, comp = S.planted_stream(spec)
+    assert 1.5e5 < len(u) < 2.5e5
+    A, G = oracle.ingest(spec.V, 5, u, v)
+    g = _gpu_graph(spec.V, 5, u, v, kernel=kernel)
+    _assert_same_sketches(g, A, G)
+    want = _assert_same_query(g, A, G, 5)
+    assert np.array_equal(want["labels"], oracle.brute_cc(spec.V, u, v))
+
+
+@pytest.mark.parametrize("V", [2, 3, 77, 1000, 4097])
+def test_ragged_sizes_many_chunks_and_tiles(V):
+    # chunk of 2^10 updates (many chunks + a ragged tail), tiles of 64 records
+    # (heavy nodes split across CTAs), 3 shared-memory rows (deep rows go to
+    # global memory directly), short segments through the direct path
+    n = 5000 if V > 3 else 301
+    u, v = S.random_stream(V, n, seed=V, n_distinct=max(1, n // 3))
+    A, G = oracle.ingest(V, 42, u, v)
+    g = _gpu_graph(V, 42, u, v, chunk_log2=10, tile_records=64, smem_rows=3, small_segment=3)
+    _assert_same_sketches(g, A, G)
+    _assert_same_query(g, A, G, 42)
+
+
+def test_hub_node_split_across_many_tiles():
+    V = 600
+    rng = np.random.default_rng(3)
+    other = rng.integers(1, V, 20000)
+    u = np.zeros(20000, np.uint32)
+    v = other.astype(np.uint32)
+    A, G = oracle.ingest(V, 8, u, v)
+    for tile in (32, 1000, 4096):
+        g = _gpu_graph(V, 8, u, v, tile_records=tile)
+        _assert_same_sketches(g, A, G)
+
+
+def test_kronecker_full_query_parity():
+    spec = S.KronSpec(L=11, seed=4, target_edges=0.45 * 2048 * 2047 / 2, churn=0.1,
+                      n_iso=20, slice_log2=18)
+    u, v = spec.stream()
+    A, G = oracle.ingest(spec.V, 9, u, v)
+    g = _gpu_graph(spec.V, 9, u, v)
+    _assert_same_sketches(g, A, G)
+    want = _assert_same_query(g, A, G, 9)
+    eu, ev = spec.final_edges()
+    assert np.array_equal(want["labels"], oracle.cc_edges(spec.V, eu, ev))
+
+
+def test_host_and_device_inputs_agree():
+    V = 3000
+    u, v = S.random_stream(V, 60000, seed=2)
+    g1 = _gpu_graph(V, 1, u, v, on_device=True)
+    g2 = _gpu_graph(V, 1, u, v, on_device=False, chunk_log2=12)
+    a1, b1 = g1.export_sketch()
+    a2, b2 = g2.export_sketch()
+    assert np.array_equal(a1, a2) and np.array_equal(b1, b2)
+
+
+def test_invalid_batch_is_discarded_whole():
+    V = 100
+    u, v = S.random_stream(V, 1000, seed=5)
+    g = _gpu_graph(V, 3, u, v)
+    before = g.export_sketch()
+    bad_u = np.array([1, 2, 3, 4], np.uint32)
+    bad_v = np.array([2, 3, 3, 5], np.uint32)  # a self loop
+    g.edge_update(_dev(bad_u), _dev(bad_v))
+    with pytest.raises(gz.GzError) as ei:
+        g.sync()
+    assert ei.value.status == gz.GZ_EINVAL
+    g.sync()  # reported once
+    after = g.export_sketch()
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+    g.edge_update(_dev(np.array([5], np.uint32)), _dev(np.array([100], np.uint32)))  # id >= V
+    with pytest.raises(gz.GzError):
+        g.sync()
+    after = g.export_sketch()
+    assert np.array_equal(before[0], after[0])
+
+
+def test_empty_graph_single_edge_and_reset():
+    V = 50
+    g = gz.Graph(V, 1)
+    labels, ncc, st = g.connected_components()
+    assert ncc == V and np.array_equal(labels, np.arange(V))
+    g.edge_update(_dev(np.array([7], np.uint32)), _dev(np.array([3], np.uint32)))
+    forest, labels, st = g.list_spanning_forest()
+    assert forest.tolist() == [[3, 7]] and labels[7] == 3
+    g.reset()
+    labels, ncc, _ = g.connected_components()
+    assert ncc == V
+    a, _ = g.export_sketch()
+    assert not a.any()
+
+
+def test_full_size_kronecker_2p13_sampled_nodes():
+    # V = 2^13 Kronecker stream, ~2e7 updates with 10% churn, in the launch
+    # configuration the benchmark uses; the oracle sketches sampled nodes from
+    # their net neighbour lists (linearity: equal to sketching the stream)
+    spec = S.kron_for_updates(13, 2024, 2.0e7, churn=0.1, chunk_updates=2**22)
+    g = gz.Graph(spec.V, 77)
+    total = 0
+    for c in range(spec.n_chunks):
+        u, v = spec.chunk(c)
+        total += len(u)
+        g.edge_update(_dev(u), _dev(v))
+    g.sync()
+    assert 1.7e7 < total < 2.3e7
+    rng = np.random.default_rng(0)
+    nodes = sorted(set(rng.integers(0, spec.V, 24).tolist()) | {0, 1, 2, 4, spec.V - 1})
+    for x in nodes:
+        A, G = oracle.sketch_node(spec.V, 77, x, spec.node_neighbors(x))
+        a, gg = g.export_sketch(x, x + 1)
+        assert np.array_equal(a[0], A) and np.array_equal(gg[0], G), x
+    labels, ncc, st = g.connected_components()
+    eu, ev = spec.final_edges()
+    want = oracle.cc_edges(spec.V, eu, ev)
+    assert st["fails_last"] == 0 and st["exhausted"] == 0
+    assert np.array_equal(labels, want)
