@@ -1,0 +1,429 @@
+#!/usr/bin/env python
+"""Benchmark of the GraphZeppelin hot path on B300: CubeSketch edge updates/s
+(whole job), HBM roofline of the batched update kernel, and Boruvka CC query
+latency (p50/p99).
+
+One step = zero the sketches, ingest the whole resident stream through
+gz_edge_update (device pointers; the library partitions it into 2^24-update
+chunks), then one gz_connected_components query.  Inputs are a seeded
+Kronecker insert/delete stream generated on the device before timing; every
+input (stream and sketches) is far larger than the 126 MB L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload kron17]
+    python bench.py --impl reference      # the CPU oracle, timed on host cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2203_14927_b300 import streams as S  # noqa: E402
+
+WORKLOADS = {
+    # name: (log2 V, stream updates, churn, seed, description)
+    "kron17": (17, 4.0e9, 0.1, 17, "V=2^17 Graph500-initiator Kronecker stream, ~4e9 updates, 10% churn"),
+    "kron15": (15, 3.0e8, 0.1, 15, "V=2^15 Graph500-initiator Kronecker stream, ~3e8 updates, 10% churn"),
+    "kron13": (13, 2.0e7, 0.1, 13, "V=2^13 Graph500-initiator Kronecker stream, ~2e7 updates, 10% churn"),
+}
+CHUNK_LOG2 = 24
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+
+def oracle_rate(spec: S.KronSpec, seed: int, budget_s: float, max_nodes: int = 64, first: int = 0):
+    """The CPU oracle as it stands (single thread) sketching whole nodes of the
+    same graph from their net neighbour lists; one stream update costs the
+    oracle two node updates, so updates/s = (sum of degrees / 2) / seconds."""
+    import oracle
+
+    rng = np.random.default_rng(1234 + first)
+    nodes = rng.integers(0, spec.V, max_nodes)
+    spent, endpoint_updates, used = 0.0, 0, []
+    for x in nodes:
+        nb = spec.node_neighbors(int(x))
+        t0 = time.perf_counter()
+        oracle.sketch_node(spec.V, seed, int(x), nb)
+        spent += time.perf_counter() - t0
+        endpoint_updates += len(nb)
+        used.append(int(x))
+        if spent >= budget_s:
+            break
+    return endpoint_updates / 2.0 / spent, spent, used, endpoint_updates
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    L, n_upd, churn, seed, desc = WORKLOADS[args.workload]
+    spec = S.kron_for_updates(L, seed, n_upd, churn=churn, chunk_updates=2 ** CHUNK_LOG2)
+    per_step = max(0.5, args.ref_seconds / max(1, args.steps + args.warmup))
+    for w in range(args.warmup):
+        oracle_rate(spec, seed, per_step, first=100 + w)
+    rates, times, nodes_all, eu = [], [], [], 0
+    for s in range(args.steps):
+        r, t, nodes, e = oracle_rate(spec, seed, per_step, first=s)
+        rates.append(r)
+        times.append(t)
+        nodes_all += nodes
+        eu += e
+    value = eu / 2.0 / sum(times)
+    sample = (f"oracle sketch_node over {len(nodes_all)} random nodes of the {args.workload} final graph "
+              f"({eu} endpoint updates = {eu / 2:.0f} stream updates), single thread")
+    out = {
+        "impl": "reference", "metric": "edge_updates_per_sec", "value": value, "unit": "updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded Kronecker graph)",
+        "config": {"workload": f"{args.workload}: {desc}", "V": spec.V},
+        "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle",
+                         "sample": sample, "cpu": cpu_model()},
+        "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU path
+
+
+def generate_on_device(spec, torch, gz):
+    gen = gz.DeviceKronStream(spec)
+    est = spec.target_edges * (1 + 2 * spec.churn)
+    cap = int(est * 1.08) + 4 * spec.slice_len + (1 << 20)
+    U = torch.empty(cap, dtype=torch.int32, device="cuda")
+    Vv = torch.empty(cap, dtype=torch.int32, device="cuda")
+    off = 0
+    for c in range(gen.n_chunks):
+        n = gen.chunk_into(c, U.data_ptr() + 4 * off, Vv.data_ptr() + 4 * off, cap - off)
+        off += n
+    gen.close()
+    return U, Vv, off
+
+
+def run_ours(args, rank: int, world: int):
+    import torch
+
+    import paper_2203_14927_b300 as gz
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+
+    L, n_upd, churn, seed, desc = WORKLOADS[args.workload]
+    seed = seed + 1000 * rank  # independent replicas: each rank its own graph
+    spec = S.kron_for_updates(L, seed, n_upd, churn=churn, chunk_updates=2 ** CHUNK_LOG2)
+    t0 = time.time()
+    U, Vv, total = generate_on_device(spec, torch, gz)
+    torch.cuda.synchronize()
+    log(f"[bench] rank {rank}: generated {total} updates on device in {time.time() - t0:.1f}s")
+    u_all, v_all = U[:total], Vv[:total]
+
+    g = gz.Graph(spec.V, seed=seed, kernel=args.kernel, chunk_log2=CHUNK_LOG2)
+    qtimes = []
+
+    def step():
+        g.reset()
+        g.edge_update(u_all, v_all)
+        labels, ncc, st = g.connected_components()
+        qtimes.append(st["ms"])
+        return ncc, st
+
+    for _ in range(args.warmup):
+        ncc, st = step()
+    log(f"[bench] warmup done: components={ncc} rounds={st['rounds']} fails={st['fails_last']}")
+    qtimes.clear()
+
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g.profile_enable(True)
+    with ClockSampler(dev) as clocks:
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ncc, st = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    prof = g.profile_read()
+    g.profile_enable(False)
+    ms = ev0.elapsed_time(ev1)
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    ms_per_step = ms_max / args.steps
+    step_updates = total
+    value = world * step_updates * args.steps / (ms_max / 1000.0)
+    clk = clocks.summary()
+
+    # --- roofline of the dominant kernel (batched CubeSketch update) ---------
+    peak, peak_kind = measured_peaks()
+    launches = max(prof["batches"], 1)
+    avg_ms = prof["update_ms"] / launches
+    K, R = g.K, g.R
+    upd_per_launch = prof["updates"] / launches
+    # bytes this kernel must move per launch: both records of every update
+    # (2 x u32 read), the row offsets, and a read+write of every (node, k, row)
+    # row of 7 buckets it XORs into HBM (7 x 12 B), plus the rare deep updates
+    bytes_per_launch = (8.0 * upd_per_launch + 4.0 * (spec.V + 1)
+                        + 2 * 84.0 * prof["rows_flushed"] / launches
+                        + 2 * 12.0 * prof["deep_updates"] / launches)
+    achieved = bytes_per_launch / (avg_ms / 1000.0) / 1e9
+    evals_per_launch = upd_per_launch * 2 * 7 * K
+    roofline = {
+        "kernel": "k_batched" if args.kernel == "batched" else "k_plain",
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+        "traffic": None,
+        "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms, "launches": launches,
+        "updates_per_launch": upd_per_launch,
+        "column_evals_per_s": evals_per_launch / (avg_ms / 1000.0),
+        "share_of_step": prof["update_ms"] / ms if ms > 0 else None,
+        "partition_ms_per_launch": prof["partition_ms"] / launches,
+    }
+
+    # --- query latency -----------------------------------------------------------
+    qs = []
+    for _ in range(args.queries):
+        t1 = time.perf_counter()
+        labels, ncc, st = g.connected_components()
+        qs.append((time.perf_counter() - t1) * 1000.0)
+    qs.sort()
+    query = {"p50_ms": float(np.percentile(qs, 50)), "p99_ms": float(np.percentile(qs, 99)),
+             "n": len(qs), "rounds": st["rounds"], "components": ncc, "fails_last": st["fails_last"],
+             "in_step_ms": qtimes}
+
+    # --- end to end through host buffers -------------------------------------
+    e2e = None
+    if not args.no_e2e:
+        n_e2e = min(total, 1 << args.e2e_log2)
+        hu = torch.empty(n_e2e, dtype=torch.int32, pin_memory=True)
+        hv = torch.empty(n_e2e, dtype=torch.int32, pin_memory=True)
+        hu.copy_(u_all[:n_e2e])
+        hv.copy_(v_all[:n_e2e])
+        hu_np, hv_np = hu.numpy(), hv.numpy()
+        ge = gz.Graph(spec.V, seed=seed, kernel=args.kernel, chunk_log2=CHUNK_LOG2)
+        ge.edge_update(hu_np, hv_np)  # warm-up
+        ge.connected_components()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        reps = 2
+        for _ in range(reps):
+            ge.reset()
+            ge.edge_update(hu_np, hv_np)
+            labels, ncc_e, _ = ge.connected_components()
+        te = (time.perf_counter() - t1) / reps
+        ge.close()
+        del hu, hv
+        e2e = {"value": world * n_e2e / te, "unit": "updates/s", "h2d_bytes_per_step": 8 * n_e2e,
+               "d2h_bytes_per_step": 4 * spec.V + 32,
+               "sample": f"first {n_e2e} updates of the same stream from pinned host memory "
+                         f"(2^{int(math.log2(n_e2e))}), reset + gz_edge_update(host) + CC query with "
+                         "labels read back, host wall clock"}
+
+    # --- plain per-update kernel on a prefix of the same stream ---------------
+    plain = None
+    if not args.no_plain and args.kernel == "batched":
+        n_pl = min(total, 1 << args.plain_log2)
+        gp = gz.Graph(spec.V, seed=seed, kernel="plain", chunk_log2=CHUNK_LOG2)
+        gp.edge_update(u_all[:1 << 20], v_all[:1 << 20])
+        torch.cuda.synchronize()
+        gp.reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gp.edge_update(u_all[:n_pl], v_all[:n_pl])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tp = e0.elapsed_time(e1) / 1000.0
+        # same prefix through the batched path for a like-for-like ratio
+        g.reset()
+        e0.record(stream)
+        g.edge_update(u_all[:n_pl], v_all[:n_pl])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tb = e0.elapsed_time(e1) / 1000.0
+        gp.close()
+        plain = {"value": n_pl / tp, "unit": "updates/s", "sample": f"first {n_pl} updates (2^{args.plain_log2})",
+                 "batched_same_prefix": n_pl / tb, "speedup_batched_over_plain": tp / tb}
+
+    # --- CPU oracle baseline ------------------------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        r, spent, nodes, eu = oracle_rate(spec, seed, args.cpu_seconds)
+        cpu = {"value": r, "unit": "updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle sketch_node over {len(nodes)} random nodes of the same graph "
+                         f"({eu} endpoint updates, {spent:.1f} s), single thread",
+               "cpu": cpu_model(), "host_cores": host_cores()}
+
+    if rank == 0:
+        out = {
+            "metric": "edge_updates_per_sec",
+            "value": value,
+            "unit": "updates/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_per_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "u64",
+            "data": "synthetic: seeded Kronecker insert/delete stream generated on device",
+            "config": {
+                "workload": f"{args.workload}: {desc}",
+                "V": spec.V, "K": K, "R": R, "updates_per_step": step_updates,
+                "chunk_updates": 2 ** CHUNK_LOG2, "kernel": args.kernel,
+                "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                "l2": "no flush needed: stream (%.1f GB) and sketches (%.1f GB) exceed the 126 MB L2"
+                      % (8 * total / 1e9, spec.V * K * 84 * R / 1e9),
+                "step": "reset sketches + ingest whole stream + one CC query",
+            },
+            "roofline": roofline,
+            "query_ms": query,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "plain_kernel": plain,
+            "gpu_launches": prof["kernel_launches"],
+            "clocks": clk,
+            "profile": prof,
+        }
+        print(json.dumps(out), flush=True)
+    g.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="kron17")
+    ap.add_argument("--kernel", choices=["batched", "plain"], default="batched")
+    ap.add_argument("--queries", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=40.0)
+    ap.add_argument("--e2e-log2", type=int, default=28)
+    ap.add_argument("--plain-log2", type=int, default=26)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -170,6 +170,25 @@ gz_status gz_export_sketch(gz_handle *h, uint32_t node_lo, uint32_t node_hi,
 gz_status gz_info(gz_handle *h, uint32_t *V, uint32_t *K, uint32_t *R,
                   size_t *node_bytes, void **sketch_device);
 
+/* Device-time profile of ingestion, for measurement.  Times come from CUDA
+ * events recorded on the handle's stream around each launch, summed over the
+ * window since gz_profile_enable(h, 1). */
+typedef struct {
+    uint64_t batches;          /* partition passes (chunks) timed */
+    uint64_t updates;          /* updates in those passes */
+    double partition_ms;       /* validation + histogram, scan, scatter */
+    double update_ms;          /* batched (or plain) sketch-update kernel */
+    uint64_t rows_flushed;     /* (node, k, row) rows the batched kernel XORed into HBM */
+    uint64_t deep_updates;     /* column updates that bypassed shared memory */
+    uint64_t kernel_launches;  /* kernels launched by this handle in the window */
+} gz_profile;
+
+/* Start (enable != 0) or stop a profiling window; starting clears totals. */
+gz_status gz_profile_enable(gz_handle *h, int enable);
+
+/* Synchronise and read the totals of the current window. */
+gz_status gz_profile_read(gz_handle *h, gz_profile *out);
+
 /* Human-readable reason of the last non-OK status (never NULL). */
 const char *gz_last_error(gz_handle *h);
 

@@ -46,6 +46,34 @@ class Config(ctypes.Structure):
     ]
 
 
+class Profile(ctypes.Structure):
+    _fields_ = [
+        ("batches", ctypes.c_uint64),
+        ("updates", ctypes.c_uint64),
+        ("partition_ms", ctypes.c_double),
+        ("update_ms", ctypes.c_double),
+        ("rows_flushed", ctypes.c_uint64),
+        ("deep_updates", ctypes.c_uint64),
+        ("kernel_launches", ctypes.c_uint64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class KronParams(ctypes.Structure):
+    _fields_ = [
+        ("L", ctypes.c_uint32),
+        ("slice_log2", ctypes.c_uint32),
+        ("k_feistel", ctypes.c_uint64 * 4),
+        ("k_kron", ctypes.c_uint64),
+        ("k_churn", ctypes.c_uint64),
+        ("k_iso", ctypes.c_uint64),
+        ("t_iso", ctypes.c_uint64),
+        ("t_churn", ctypes.c_uint64),
+    ]
+
+
 class QueryStats(ctypes.Structure):
     _fields_ = [
         ("rounds", ctypes.c_uint32),
@@ -87,6 +115,13 @@ _SIGNATURES = {
                                         ctypes.c_void_p, ctypes.c_int]),
     "gz_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                ctypes.c_void_p, ctypes.c_void_p]),
+    "gz_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "gz_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gz_gen_kron_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gz_gen_kron_num_chunks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gz_gen_kron_chunk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_uint64, ctypes.c_void_p]),
+    "gz_gen_destroy": (ctypes.c_int, [ctypes.c_void_p]),
 }
 
 
@@ -250,6 +285,14 @@ class Graph:
                                            g.ctypes.data_as(ctypes.c_void_p), 0), "gz_export_sketch")
         return a, g
 
+    def profile_enable(self, on: bool = True):
+        self._check(lib().gz_profile_enable(self._h, 1 if on else 0), "gz_profile_enable")
+
+    def profile_read(self) -> dict:
+        p = Profile()
+        self._check(lib().gz_profile_read(self._h, ctypes.byref(p)), "gz_profile_read")
+        return p.as_dict()
+
     def info(self) -> dict:
         V, K, R = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
         nb = ctypes.c_size_t()
@@ -257,3 +300,58 @@ class Graph:
         self._check(lib().gz_info(self._h, ctypes.byref(V), ctypes.byref(K), ctypes.byref(R),
                                   ctypes.byref(nb), ctypes.byref(ptr)), "gz_info")
         return {"V": V.value, "K": K.value, "R": R.value, "node_bytes": nb.value, "sketch_ptr": ptr.value}
+
+
+class DeviceKronStream:
+    """Device generator of the chunks of a streams.KronSpec (same updates as
+    KronSpec.chunk on the host)."""
+
+    def __init__(self, spec, stream=None):
+        d = spec.device_params()
+        p = KronParams()
+        p.L = d["L"]
+        p.slice_log2 = d["slice_log2"]
+        for i, k in enumerate(d["k_feistel"]):
+            p.k_feistel[i] = k
+        p.k_kron, p.k_churn, p.k_iso = d["k_kron"], d["k_churn"], d["k_iso"]
+        p.t_iso, p.t_churn = d["t_iso"], d["t_churn"]
+        self._table = np.ascontiguousarray(d["table"], np.uint64)
+        self._g = ctypes.c_void_p()
+        s = _current_stream() if stream is None else stream
+        st = lib().gz_gen_kron_create(ctypes.byref(p), self._table.ctypes.data_as(ctypes.c_void_p),
+                                      ctypes.c_void_p(s), ctypes.byref(self._g))
+        if st != GZ_OK:
+            raise GzError(st, "gz_gen_kron_create failed")
+        n = ctypes.c_uint64()
+        lib().gz_gen_kron_num_chunks(self._g, ctypes.byref(n))
+        self.n_chunks = n.value
+        self.spec = spec
+
+    def chunk_into(self, c: int, u_ptr: int, v_ptr: int, capacity: int) -> int:
+        """Write chunk c to device pointers; returns its length."""
+        n = ctypes.c_uint64()
+        st = lib().gz_gen_kron_chunk(self._g, c, ctypes.c_void_p(u_ptr), ctypes.c_void_p(v_ptr), capacity,
+                                     ctypes.byref(n))
+        if st != GZ_OK:
+            raise GzError(st, f"gz_gen_kron_chunk({c}) failed")
+        return n.value
+
+    def chunk(self, c: int):
+        """Chunk c as a pair of int32 CUDA tensors (bit patterns of uint32 ids)."""
+        import torch
+        cap = int(self.spec.slice_len * 2 + 16)
+        u = torch.empty(cap, dtype=torch.int32, device="cuda")
+        v = torch.empty(cap, dtype=torch.int32, device="cuda")
+        n = self.chunk_into(c, u.data_ptr(), v.data_ptr(), cap)
+        return u[:n], v[:n]
+
+    def close(self):
+        if getattr(self, "_g", None) and self._g.value:
+            lib().gz_gen_destroy(self._g)
+            self._g = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -140,6 +140,8 @@ gz_status gz_create(uint32_t V, uint64_t seed, const gz_config* cfg, void* strea
     if (e == cudaSuccess && h->cfg.kernel == GZ_KERNEL_BATCHED)
         e = cudaMalloc(&h->d_records, (size_t)2 * h->chunk * 4);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_flags, 16);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_stats, 2 * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_stats, 0, 2 * sizeof(uint64_t), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, 16, h->stream);
     s = cuda_check(h, e, "gz_create allocation");
     if (s == GZ_OK) s = ingest_setup(h);
@@ -159,10 +161,11 @@ gz_status gz_destroy(gz_handle* h) {
                     h->q_cursor, h->q_members, h->q_roots, h->q_target, h->q_item_base,
                     h->q_item_cnt, h->q_item_comp, h->q_item_lo, h->q_item_hi, h->q_F, h->q_F2,
                     h->q_M, h->q_M2, h->q_flag, h->q_pos, h->q_forest, h->q_ctr, h->q_res,
-                    h->q_partial, h->q_trace};
+                    h->q_partial, h->q_trace, h->d_stats};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);
+    for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
     delete h;
     return GZ_OK;
 }
@@ -284,6 +287,44 @@ gz_status gz_export_sketch(gz_handle* h, uint32_t node_lo, uint32_t node_hi, uin
     }
     if (s != GZ_OK) return s;
     return cuda_check(h, e, "export");
+}
+
+gz_status gz_profile_enable(gz_handle* h, int enable) {
+    if (!h) return GZ_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_stats, 0, 2 * sizeof(uint64_t), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "profile enable");
+    h->prof = enable != 0;
+    h->ev_used = 0;
+    h->prof_batches = h->prof_updates = h->launches = 0;
+    return GZ_OK;
+}
+
+gz_status gz_profile_read(gz_handle* h, gz_profile* out) {
+    if (!h || !out) return GZ_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "profile sync");
+    double part = 0, upd = 0;
+    for (size_t i = 0; i + 2 < h->ev_used; i += 3) {
+        float a = 0, b = 0;
+        e = cudaEventElapsedTime(&a, h->ev_pool[i], h->ev_pool[i + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, h->ev_pool[i + 1], h->ev_pool[i + 2]);
+        if (e != cudaSuccess) return cuda_check(h, e, "cudaEventElapsedTime");
+        part += a;
+        upd += b;
+    }
+    uint64_t st[2] = {0, 0};
+    e = cudaMemcpy(st, h->d_stats, sizeof(st), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_check(h, e, "profile stats");
+    out->batches = h->prof_batches;
+    out->updates = h->prof_updates;
+    out->partition_ms = part;
+    out->update_ms = upd;
+    out->rows_flushed = st[0];
+    out->deep_updates = st[1];
+    out->kernel_launches = h->launches;
+    return GZ_OK;
 }
 
 gz_status gz_info(gz_handle* h, uint32_t* V, uint32_t* K, uint32_t* R, size_t* node_bytes,

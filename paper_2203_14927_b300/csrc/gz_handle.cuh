@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/gz.h"
 #include "gz_internal.cuh"
@@ -52,6 +53,13 @@ struct gz_handle {
     bool trace = false;
     bool trace_valid = false;
 
+    // profiling window (gz_profile_enable / gz_profile_read)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;  // triples: before partition, before update, after update
+    size_t ev_used = 0;
+    uint64_t prof_batches = 0, prof_updates = 0, launches = 0;
+    uint64_t* d_stats = nullptr;  // [0] rows flushed, [1] deep column updates
+
     std::string err;
 };
 
@@ -70,6 +78,9 @@ gz_status export_nested(gz_handle* h, uint32_t lo, uint32_t hi, uint64_t* d_alph
 gz_status query_setup(gz_handle* h);
 gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* forest_uv,
                   size_t* n_edges, uint32_t* n_cc, gz_query_stats* st);
+
+// profiling: record the next event of the current triple (no-op when disabled)
+gz_status prof_event(gz_handle* h);
 
 // single-CTA exclusive scan: out[0..n] with out[n] = total; out2 (optional) = copy of out[0..n)
 void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* out2, uint32_t n, cudaStream_t s);

@@ -112,6 +112,7 @@ struct BatchedArgs {
     const uint32_t* records;
     const uint32_t* flags;
     uint32_t* work;  // tile counter
+    unsigned long long* stats;  // [0] rows flushed, [1] deep column updates
     uint32_t V, K, R, ncol, Rs, tile, small_seg;
 };
 
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
     const uint32_t total = p.offsets[p.V];
     const uint32_t ntiles = (total + p.tile - 1) / p.tile;
     const uint32_t Rs = p.Rs, R = p.R;
+    unsigned long long n_rows = 0, n_deep = 0;
 
     for (;;) {
         __syncthreads();
@@ -199,6 +201,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                                 dG[d * CP + c] ^= g;
                                 md = max(md, d);
                             } else {
+                                ++n_deep;
                                 const uint32_t dd = exact_depth(tw, R);
                                 atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, dd, j)),
                                           (unsigned long long)idx);
@@ -226,7 +229,10 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                         }
                     }
                     __syncthreads();
-                    for (uint32_t i = c; i < p.K; i += CP) maxd[i] = 0;
+                    for (uint32_t i = c; i < p.K; i += CP) {
+                        n_rows += maxd[i] + 1;
+                        maxd[i] = 0;
+                    }
                 }
                 __syncthreads();
             }
@@ -234,6 +240,8 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
             ++x;
         }
     }
+    if (n_rows) atomicAdd(&p.stats[0], n_rows);
+    if (n_deep) atomicAdd(&p.stats[1], n_deep);
 }
 
 // ------------------------------------------------------------------ plain update
@@ -328,15 +336,19 @@ gz_status ingest_setup(gz_handle* h) {
 gz_status ingest_batch(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, uint64_t n) {
     if (n == 0) return GZ_OK;
     cudaStream_t st = h->stream;
+    gz_status ps = prof_event(h);
+    if (ps != GZ_OK) return ps;
     cudaError_t e = cudaMemsetAsync(h->d_flags, 0, 2 * sizeof(uint32_t), st);  // batch flag + work
     if (e != cudaSuccess) return cuda_check(h, e, "memset flags");
     const uint32_t tpb = 256;
     const uint32_t grid = (uint32_t)std::min<uint64_t>((n + tpb - 1) / tpb, (uint64_t)h->sm_count * 8);
     if (h->cfg.kernel == GZ_KERNEL_PLAIN) {
         k_validate_count<<<grid, tpb, 0, st>>>(d_u, d_v, n, h->V, nullptr, h->d_flags);
+        if ((ps = prof_event(h)) != GZ_OK) return ps;
         const uint32_t pg = (uint32_t)std::min<uint64_t>(n, (uint64_t)h->sm_count * 16);
         k_plain<<<pg, h->block, 0, st>>>(d_u, d_v, n, view_of(h), keys_of(h), h->V, h->R, h->ncol,
                                          h->d_flags);
+        h->launches += 2;
     } else {
         e = cudaMemsetAsync(h->d_counts, 0, (size_t)(h->V + 1) * sizeof(uint32_t), st);
         if (e != cudaSuccess) return cuda_check(h, e, "memset counts");
@@ -357,9 +369,28 @@ gz_status ingest_batch(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, u
         a.Rs = h->smem_rows;
         a.tile = h->tile;
         a.small_seg = h->small_seg;
+        a.stats = reinterpret_cast<unsigned long long*>(h->d_stats);
+        if ((ps = prof_event(h)) != GZ_OK) return ps;
         k_batched<<<h->batched_grid, h->block, h->batched_smem, st>>>(a);
+        h->launches += 4;
+    }
+    if ((ps = prof_event(h)) != GZ_OK) return ps;
+    if (h->prof) {
+        h->prof_batches += 1;
+        h->prof_updates += n;
     }
     return cuda_check(h, cudaGetLastError(), "ingest launch");
+}
+
+gz_status prof_event(gz_handle* h) {
+    if (!h->prof) return GZ_OK;
+    if (h->ev_used == h->ev_pool.size()) {
+        cudaEvent_t ev;
+        cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return cuda_check(h, e, "cudaEventCreate");
+        h->ev_pool.push_back(ev);
+    }
+    return cuda_check(h, cudaEventRecord(h->ev_pool[h->ev_used++], h->stream), "cudaEventRecord");
 }
 
 gz_status export_nested(gz_handle* h, uint32_t lo, uint32_t hi, uint64_t* d_alpha, uint32_t* d_gamma) {

@@ -364,6 +364,7 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
     const uint32_t V = h->V, tpb = 256;
     const uint32_t gV = grid_for(h, V, tpb);
     k_q_init<<<gV, tpb, 0, stm>>>(h->q_label, h->q_parent, V);
+    h->launches += 2 + (q.trace ? 1 : 0);  // init, final count (+ trace fill)
     if (q.trace) k_fill64<<<grid_for(h, (uint64_t)h->K * V, tpb), tpb, 0, stm>>>(q.trace, (uint64_t)h->K * V, -4);
     cudaError_t e = cudaMemsetAsync(h->q_ctr, 0, C_N * sizeof(uint32_t), stm);
     if (e != cudaSuccess) return cuda_check(h, e, "memset counters");
@@ -382,6 +383,7 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
         k_q_roots<<<gV, tpb, 0, stm>>>(q);
         k_q_merge_items<<<h->sm_count * 4, 384, 0, stm>>>(q);
         k_q_sample<<<h->sm_count * 16, 256, sample_smem, stm>>>(q);
+        h->launches += 6;
         e = cudaMemcpyAsync(h->h_ctr, h->q_ctr, C_N * sizeof(uint32_t), cudaMemcpyDeviceToHost, stm);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stm);
         if (e != cudaSuccess) return cuda_check(h, e, "query round");
@@ -391,6 +393,7 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
         if (n_ed == 0) break;
         if (r == h->K - 1) exhausted = 1;
         k_q_link<<<grid_for(h, n_roots, tpb), tpb, 0, stm>>>(q);
+        h->launches += 2;  // link, relabel
         if (want_forest) {
             uint32_t *F = h->q_F, *F2 = h->q_F2, *Mx = h->q_M, *Mx2 = h->q_M2;
             const uint32_t gR = grid_for(h, n_roots, tpb);
@@ -408,6 +411,7 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
             launch_scan(h->q_cursor, h->q_pos, nullptr, V, stm);
             k_q_forest_write<<<gV, tpb, 0, stm>>>(q, h->q_cursor, h->q_pos, h->q_forest);
             k_q_forest_advance<<<1, 1, 0, stm>>>(q, h->q_pos);
+            h->launches += J + 6;
         }
         k_q_relabel<<<gV, tpb, 0, stm>>>(q);
     }
