@@ -221,7 +221,22 @@ def run_ours(args, rank: int, world: int):
     log(f"[bench] rank {rank}: generated {total} updates on device in {time.time() - t0:.1f}s")
     u_all, v_all = U[:total], Vv[:total]
 
-    g = gz.Graph(spec.V, seed=seed, kernel=args.kernel, chunk_log2=CHUNK_LOG2)
+    from paper_2203_14927_b300 import autotune
+
+    cfg = dict(autotune.DEFAULT)
+    tuned = None
+    if args.kernel == "batched" and not args.no_tune:
+        ns = min(total, 1 << 27)
+        t0 = time.time()
+        tuned = autotune.tune(spec.V, u_all[:ns], v_all[:ns], seed=seed, use_cache=False, log=log)
+        cfg = dict(tuned["config"])
+        log(f"[bench] autotuned in {time.time() - t0:.1f}s: {cfg} "
+            f"({tuned['rate'] / 1e9:.3f} vs default {tuned['default_rate'] / 1e9:.3f} G/s on the sample)")
+    if args.cfg:
+        cfg.update(json.loads(args.cfg))
+    if args.kernel == "plain":
+        cfg = {"chunk_log2": CHUNK_LOG2}
+    g = gz.Graph(spec.V, seed=seed, kernel=args.kernel, **cfg)
     qtimes = []
 
     def step():
@@ -233,7 +248,7 @@ def run_ours(args, rank: int, world: int):
 
     for _ in range(args.warmup):
         ncc, st = step()
-    log(f"[bench] warmup done: components={ncc} rounds={st['rounds']} fails={st['fails_last']}")
+        log(f"[bench] warmup step: components={ncc} rounds={st['rounds']} fails={st['fails_last']}")
     qtimes.clear()
 
     stream = torch.cuda.current_stream()
@@ -290,7 +305,7 @@ def run_ours(args, rank: int, world: int):
     }
 
     # --- query latency -----------------------------------------------------------
-    qs = []
+    qs = [st["ms"]] if args.queries == 0 else []
     for _ in range(args.queries):
         t1 = time.perf_counter()
         labels, ncc, st = g.connected_components()
@@ -309,7 +324,17 @@ def run_ours(args, rank: int, world: int):
         hu.copy_(u_all[:n_e2e])
         hv.copy_(v_all[:n_e2e])
         hu_np, hv_np = hu.numpy(), hv.numpy()
-        ge = gz.Graph(spec.V, seed=seed, kernel=args.kernel, chunk_log2=CHUNK_LOG2)
+        # raw pinned host -> device copy rate of the same buffers, for context
+        dtmp = torch.empty(n_e2e, dtype=torch.int32, device="cuda")
+        dtmp.copy_(hu, non_blocking=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dtmp.copy_(hu, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        h2d_gbs = 4 * n_e2e / (e0.elapsed_time(e1) / 1000.0) / 1e9
+        del dtmp
+        ge = gz.Graph(spec.V, seed=seed, kernel=args.kernel, **cfg)
         ge.edge_update(hu_np, hv_np)  # warm-up
         ge.connected_components()
         torch.cuda.synchronize()
@@ -323,6 +348,7 @@ def run_ours(args, rank: int, world: int):
         ge.close()
         del hu, hv
         e2e = {"value": world * n_e2e / te, "unit": "updates/s", "h2d_bytes_per_step": 8 * n_e2e,
+               "pinned_h2d_gbs": h2d_gbs,
                "d2h_bytes_per_step": 4 * spec.V + 32,
                "sample": f"first {n_e2e} updates of the same stream from pinned host memory "
                          f"(2^{int(math.log2(n_e2e))}), reset + gz_edge_update(host) + CC query with "
@@ -379,7 +405,10 @@ def run_ours(args, rank: int, world: int):
             "config": {
                 "workload": f"{args.workload}: {desc}",
                 "V": spec.V, "K": K, "R": R, "updates_per_step": step_updates,
-                "chunk_updates": 2 ** CHUNK_LOG2, "kernel": args.kernel,
+                "chunk_updates": 2 ** cfg.get("chunk_log2", CHUNK_LOG2), "kernel": args.kernel,
+                "tuned": cfg if tuned else None,
+                "tune_sample": {"rate": tuned["rate"], "default_rate": tuned["default_rate"],
+                                "candidates": len(tuned["tried"])} if tuned else None,
                 "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                 "l2": "no flush needed: stream (%.1f GB) and sketches (%.1f GB) exceed the 126 MB L2"
                       % (8 * total / 1e9, spec.V * K * 84 * R / 1e9),
@@ -416,6 +445,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--cfg", default="", help="JSON gz_config overrides, e.g. '{\"smem_mode\": 1}'")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

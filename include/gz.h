@@ -63,7 +63,8 @@ typedef struct {
     uint32_t tile_records;  /* records per work tile of the batched kernel (default 1024) */
     uint32_t ctas_per_sm;   /* resident CTAs per SM of the persistent batched kernel (default: max) */
     uint32_t small_segment; /* node segments shorter than this skip shared-memory staging (default 4) */
-    uint32_t reserved[6];
+    uint32_t smem_mode;     /* delta update in shared memory: 0 load-xor-store, 1 shared atomics */
+    uint32_t reserved[5];
 } gz_config;
 
 /* Statistics of the last query. */

@@ -42,7 +42,8 @@ class Config(ctypes.Structure):
         ("tile_records", ctypes.c_uint32),
         ("ctas_per_sm", ctypes.c_uint32),
         ("small_segment", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 6),
+        ("smem_mode", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 5),
     ]
 
 
@@ -160,7 +161,10 @@ def _buffer(x):
             raise TypeError("update tensors must be int32 or uint32")
         x = x.contiguous().reshape(-1)
         return x.data_ptr(), x.numel(), 1 if x.is_cuda else 0, x
-    a = np.ascontiguousarray(x, dtype=np.uint32).reshape(-1)
+    a = np.asarray(x)
+    if a.dtype == np.int32 and a.flags["C_CONTIGUOUS"]:
+        a = a.view(np.uint32)  # same bytes, no copy (keeps pinned memory pinned)
+    a = np.ascontiguousarray(a, dtype=np.uint32).reshape(-1)
     return a.ctypes.data, a.size, 0, a
 
 
@@ -179,7 +183,7 @@ class Graph:
 
     def __init__(self, V: int, seed: int = 0, *, kernel: str = "batched", chunk_log2: int = 0,
                  smem_rows: int = 0, tile_records: int = 0, ctas_per_sm: int = 0,
-                 small_segment: int = 0, stream=None):
+                 small_segment: int = 0, smem_mode: int = 0, stream=None):
         cfg = Config()
         cfg.chunk_log2 = chunk_log2
         cfg.kernel = KERNELS[kernel]
@@ -187,6 +191,7 @@ class Graph:
         cfg.tile_records = tile_records
         cfg.ctas_per_sm = ctas_per_sm
         cfg.small_segment = small_segment
+        cfg.smem_mode = smem_mode
         self._h = ctypes.c_void_p()
         s = _current_stream() if stream is None else stream
         st = lib().gz_create(V, seed & ((1 << 64) - 1), ctypes.byref(cfg), ctypes.c_void_p(s),

@@ -140,6 +140,7 @@ gz_status gz_create(uint32_t V, uint64_t seed, const gz_config* cfg, void* strea
     if (e == cudaSuccess && h->cfg.kernel == GZ_KERNEL_BATCHED)
         e = cudaMalloc(&h->d_records, (size_t)2 * h->chunk * 4);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_flags, 16);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_scan_tmp, ((size_t)(V + 1) / 1024 + 2) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_stats, 2 * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_stats, 0, 2 * sizeof(uint64_t), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, 16, h->stream);
@@ -161,11 +162,16 @@ gz_status gz_destroy(gz_handle* h) {
                     h->q_cursor, h->q_members, h->q_roots, h->q_target, h->q_item_base,
                     h->q_item_cnt, h->q_item_comp, h->q_item_lo, h->q_item_hi, h->q_F, h->q_F2,
                     h->q_M, h->q_M2, h->q_flag, h->q_pos, h->q_forest, h->q_ctr, h->q_res,
-                    h->q_partial, h->q_trace, h->d_stats};
+                    h->q_partial, h->q_trace, h->d_stats, h->d_scan_tmp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);
     for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
+    for (int b = 0; b < 2; ++b) {
+        if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);
+        if (h->ev_free[b]) cudaEventDestroy(h->ev_free[b]);
+    }
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     delete h;
     return GZ_OK;
 }
@@ -176,33 +182,56 @@ gz_status gz_set_stream(gz_handle* h, void* stream) {
     return GZ_OK;
 }
 
+static gz_status host_path_setup(gz_handle* h) {
+    if (h->d_stage) return GZ_OK;
+    cudaError_t e = cudaMalloc(&h->d_stage, (size_t)4 * h->chunk * 4);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaEventCreateWithFlags(&h->ev_copied[b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_free[b], cudaEventDisableTiming);
+    }
+    return cuda_check(h, e, "host staging setup");
+}
+
 gz_status gz_edge_update(gz_handle* h, const uint32_t* u, const uint32_t* v, size_t n, int on_device) {
     if (!h) return GZ_EINVAL;
     if (n == 0) return GZ_OK;
     if (!u || !v) return set_error(h, GZ_EINVAL, "null update arrays");
-    if (!on_device && !h->d_stage) {
-        cudaError_t e = cudaMalloc(&h->d_stage, (size_t)2 * h->chunk * 4);
-        if (e != cudaSuccess) return cuda_check(h, e, "staging allocation");
-    }
-    for (size_t off = 0; off < n; off += h->chunk) {
-        const uint64_t m = std::min<uint64_t>(h->chunk, n - off);
-        const uint32_t *du = u + off, *dv = v + off;
-        if (!on_device) {
-            cudaError_t e = cudaMemcpyAsync(h->d_stage, u + off, m * 4, cudaMemcpyHostToDevice, h->stream);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(h->d_stage + h->chunk, v + off, m * 4, cudaMemcpyHostToDevice, h->stream);
-            if (e != cudaSuccess) return cuda_check(h, e, "update copy");
-            du = h->d_stage;
-            dv = h->d_stage + h->chunk;
+    if (on_device) {
+        for (size_t off = 0; off < n; off += h->chunk) {
+            const uint64_t m = std::min<uint64_t>(h->chunk, n - off);
+            gz_status s = ingest_batch(h, u + off, v + off, m);
+            if (s != GZ_OK) return s;
         }
-        gz_status s = ingest_batch(h, du, dv, m);
+        return GZ_OK;
+    }
+    // Host input: two staging buffers; the copy of chunk i+1 (copy stream)
+    // overlaps the processing of chunk i (handle stream).
+    gz_status s = host_path_setup(h);
+    if (s != GZ_OK) return s;
+    cudaError_t e = cudaSuccess;
+    size_t i = 0;
+    for (size_t off = 0; off < n; off += h->chunk, ++i) {
+        const uint64_t m = std::min<uint64_t>(h->chunk, n - off);
+        const int b = (int)(i & 1);
+        uint32_t* su = h->d_stage + (size_t)b * 2 * h->chunk;
+        uint32_t* sv = su + h->chunk;
+        // buffer b is free once the kernels of its previous chunk (this call
+        // or an earlier one) are done; an event never recorded is complete
+        e = cudaStreamWaitEvent(h->copy_stream, h->ev_free[b], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(su, u + off, m * 4, cudaMemcpyHostToDevice, h->copy_stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sv, v + off, m * 4, cudaMemcpyHostToDevice, h->copy_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_copied[b], h->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0);
+        if (e != cudaSuccess) return cuda_check(h, e, "update copy");
+        s = ingest_batch(h, su, sv, m);
         if (s != GZ_OK) return s;
+        e = cudaEventRecord(h->ev_free[b], h->stream);
+        if (e != cudaSuccess) return cuda_check(h, e, "update event");
     }
-    if (!on_device) {
-        // host buffers may be pageable: do not return before the copies are done
-        cudaError_t e = cudaStreamSynchronize(h->stream);
-        if (e != cudaSuccess) return cuda_check(h, e, "update sync");
-    }
+    // the caller may reuse its host buffers once every copy has landed
+    e = cudaStreamSynchronize(h->copy_stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "update sync");
     return GZ_OK;
 }
 

@@ -19,6 +19,7 @@ struct gz_gen {
     uint32_t* d_cnt = nullptr;  // [2][nb] block counts (inserts, deletes)
     uint32_t* d_off = nullptr;  // [2][nb+1]
     uint32_t* h_tot = nullptr;  // pinned [2]
+    uint32_t* d_scan_tmp = nullptr;
     uint64_t nb = 0;
     cudaStream_t stream = nullptr;
 };
@@ -168,6 +169,7 @@ gz_status gz_gen_kron_create(const gz_kron_params* p, const uint64_t* table, voi
     if (e == cudaSuccess) e = cudaMalloc(&g->d_cnt, 2 * g->nb * 4);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_off, 2 * (g->nb + 1) * 4);
     if (e == cudaSuccess) e = cudaMallocHost(&g->h_tot, 2 * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_scan_tmp, (g->nb / 1024 + 2) * 4);
     if (e != cudaSuccess) {
         gz_gen_destroy(g);
         return e == cudaErrorMemoryAllocation ? GZ_ENOMEM : GZ_ECUDA;
@@ -209,8 +211,8 @@ gz_status gz_gen_kron_chunk(gz_gen* g, uint64_t c, uint32_t* u, uint32_t* v, uin
     cudaStream_t s = g->stream;
     const uint32_t nb = (uint32_t)g->nb;
     k_gen_count<<<nb, kThreads, 0, s>>>(a, g->d_cnt, g->d_cnt + nb);
-    gz::launch_scan(g->d_cnt, g->d_off, nullptr, nb, s);
-    gz::launch_scan(g->d_cnt + nb, g->d_off + nb + 1, nullptr, nb, s);
+    gz::launch_scan(g->d_cnt, g->d_off, nullptr, nb, s, g->d_scan_tmp);
+    gz::launch_scan(g->d_cnt + nb, g->d_off + nb + 1, nullptr, nb, s, g->d_scan_tmp);
     cudaError_t e = cudaMemcpyAsync(&g->h_tot[0], g->d_off + nb, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&g->h_tot[1], g->d_off + nb + 1 + nb, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -231,6 +233,7 @@ gz_status gz_gen_destroy(gz_gen* g) {
     if (g->d_cnt) cudaFree(g->d_cnt);
     if (g->d_off) cudaFree(g->d_off);
     if (g->h_tot) cudaFreeHost(g->h_tot);
+    if (g->d_scan_tmp) cudaFree(g->d_scan_tmp);
     delete g;
     return GZ_OK;
 }

@@ -32,8 +32,11 @@ struct gz_handle {
     uint32_t* d_offsets = nullptr; // V+1
     uint32_t* d_cursor = nullptr;  // V
     uint32_t* d_records = nullptr; // 2*chunk
-    uint32_t* d_stage = nullptr;   // 2*chunk, host-input staging (lazy)
-    uint32_t* d_flags = nullptr;   // [0] batch invalid, [1] sticky invalid, [2] work counter
+    uint32_t* d_stage = nullptr;   // 2 buffers x (u, v) x chunk, host-input staging (lazy)
+    cudaStream_t copy_stream = nullptr;  // H2D copies of host input (lazy)
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+    uint32_t* d_flags = nullptr;   // [0] batch invalid, [1] work counter, [2] sticky invalid
+    uint32_t* d_scan_tmp = nullptr; // ceil((V+1)/1024) tile sums of the scans
     uint32_t block = 0;            // columns padded to a warp multiple
     uint32_t smem_rows = 0, tile = 0, small_seg = 0, batched_grid = 0;
     size_t batched_smem = 0;
@@ -82,7 +85,9 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
 // profiling: record the next event of the current triple (no-op when disabled)
 gz_status prof_event(gz_handle* h);
 
-// single-CTA exclusive scan: out[0..n] with out[n] = total; out2 (optional) = copy of out[0..n)
-void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* out2, uint32_t n, cudaStream_t s);
+// exclusive scan: out[0..n] with out[n] = total; out2 (optional) = copy of out[0..n);
+// tile_scratch holds ceil(n / 1024) u32
+void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* out2, uint32_t n, cudaStream_t s,
+                 uint32_t* tile_scratch);
 
 }  // namespace gz

@@ -48,46 +48,98 @@ __global__ void k_validate_count(const uint32_t* __restrict__ u, const uint32_t*
     }
 }
 
-// Exclusive scan of n counts by one CTA: out[i] = sum in[0..i), out[n] = total;
-// out2 (optional) receives out[0..n) as well (the scatter cursors).
-__global__ void __launch_bounds__(1024) k_scan(const uint32_t* __restrict__ in,
-                                               uint32_t* __restrict__ out,
-                                               uint32_t* __restrict__ out2, uint32_t n) {
-    __shared__ uint32_t warp_sum[32];
-    const uint32_t T = blockDim.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const uint32_t per = (n + T - 1) / T;
-    const uint32_t lo = min(tid * per, n), hi = min(lo + per, n);
-    uint32_t s = 0;
-    for (uint32_t i = lo; i < hi; ++i) s += in[i];
-    uint32_t x = s;
+// Exclusive scan of n counts: out[i] = sum in[0..i), out[n] = total; out2
+// (optional) receives out[0..n) as well (the scatter cursors).  Two launches:
+// per-tile sums, then every tile adds the sums of the tiles before it and
+// scans its own 1024 entries (coalesced loads, warp-shuffle scan).
+constexpr uint32_t kScanTile = 1024;
+
+__device__ __forceinline__ uint32_t block_scan_excl_1024(uint32_t x, uint32_t* sh, uint32_t* total) {
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t s = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= (uint32_t)o) x += y;
+        const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= (uint32_t)o) s += y;
     }
-    if (lane == 31) warp_sum[w] = x;
+    if (lane == 31) sh[w] = s;
     __syncthreads();
     if (w == 0) {
-        uint32_t ws = lane < T / 32 ? warp_sum[lane] : 0;
+        uint32_t t = sh[lane];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, ws, o);
-            if (lane >= (uint32_t)o) ws += y;
+            const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= (uint32_t)o) t += y;
         }
-        warp_sum[lane] = ws;
+        sh[lane] = t;
     }
     __syncthreads();
-    uint32_t excl = x - s + (w ? warp_sum[w - 1] : 0);
-    for (uint32_t i = lo; i < hi; ++i) {
-        out[i] = excl;
-        if (out2) out2[i] = excl;
-        excl += in[i];
-    }
-    if (tid == T - 1) out[n] = excl;
+    const uint32_t r = s - x + (w ? sh[w - 1] : 0);
+    *total = sh[31];
+    __syncthreads();
+    return r;
 }
 
-void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* out2, uint32_t n, cudaStream_t s) {
-    k_scan<<<1, 1024, 0, s>>>(in, out, out2, n);
+__global__ void __launch_bounds__(kScanTile) k_scan_sums(const uint32_t* __restrict__ in, uint32_t n,
+                                                        uint32_t* __restrict__ tile_sum) {
+    __shared__ uint32_t sh[32];
+    const uint32_t i = blockIdx.x * kScanTile + threadIdx.x;
+    uint32_t x = i < n ? in[i] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t t = sh[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) tile_sum[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kScanTile) k_scan_tiles(const uint32_t* __restrict__ in, uint32_t n,
+                                                         const uint32_t* __restrict__ tile_sum,
+                                                         uint32_t* __restrict__ out,
+                                                         uint32_t* __restrict__ out2) {
+    __shared__ uint32_t sh[32];
+    __shared__ uint32_t s_base;
+    // prefix of the tile sums before this tile
+    uint32_t acc = 0;
+    for (uint32_t t = threadIdx.x; t < blockIdx.x; t += kScanTile) acc += tile_sum[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t t = sh[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) s_base = t;
+    }
+    __syncthreads();
+    const uint32_t base = s_base;
+    __syncthreads();
+    const uint32_t i = blockIdx.x * kScanTile + threadIdx.x;
+    const uint32_t x = i < n ? in[i] : 0;
+    uint32_t total;
+    const uint32_t e = base + block_scan_excl_1024(x, sh, &total);
+    if (i < n) {
+        out[i] = e;
+        if (out2) out2[i] = e;
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = base + total;
+}
+
+// tile sums live after the n+1 outputs' worth of scratch the caller provides
+void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* out2, uint32_t n, cudaStream_t s,
+                 uint32_t* tile_scratch) {
+    const uint32_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 0) {
+        cudaMemsetAsync(out, 0, sizeof(uint32_t), s);
+        return;
+    }
+    k_scan_sums<<<tiles, kScanTile, 0, s>>>(in, n, tile_scratch);
+    k_scan_tiles<<<tiles, kScanTile, 0, s>>>(in, n, tile_scratch, out, out2);
 }
 
 // Scatter: record of update (a,b) in a's segment is b and in b's segment is a.
@@ -116,37 +168,103 @@ struct BatchedArgs {
     uint32_t V, K, R, ncol, Rs, tile, small_seg;
 };
 
-// One CTA = 32*ceil(7K/32) threads; thread c owns CubeSketch column c = 7k + j.
-// Dynamic shared memory: delta alpha[Rs][CP] u64, staged indices [tile] u64,
-// delta gamma[Rs][CP] u32, per-k deepest touched row [K] u32.  With the
-// [row][column] layout a warp's 32 lanes hit 32 distinct banks whatever rows
-// their updates land in.
+// The two hashes of one column written on 32-bit words, with every part that
+// depends only on the column's keys folded into per-thread constants.  They
+// compute exactly `depth_word` and `checksum` of gz_internal.cuh.
+namespace fm {
+constexpr uint32_t C1_LO = 0xED558CCDu, C1_HI = 0xFF51AFD7u;  // MurmurHash3 fmix64 multipliers
+constexpr uint32_t C2_LO = 0x1A85EC53u, C2_HI = 0xC4CEB9FEu;
+}  // namespace fm
+
+struct ColKey {
+    uint32_t a_lo, a_hi;
+    uint64_t b;
+    uint32_t kfold;  // c_lo ^ (c_hi >> 1): the key's share of the first xor-shift
+    uint32_t c_hi;
+    uint32_t k2;     // c_hi * C1_LO: the key's share of the first product when idx < 2^32
+};
+
+__device__ __forceinline__ ColKey make_colkey(uint64_t a, uint64_t b, uint64_t c) {
+    ColKey k;
+    k.a_lo = (uint32_t)a;
+    k.a_hi = (uint32_t)(a >> 32);
+    k.b = b;
+    const uint32_t c_lo = (uint32_t)c, c_hi = (uint32_t)(c >> 32);
+    k.kfold = c_lo ^ (c_hi >> 1);
+    k.c_hi = c_hi;
+    k.k2 = c_hi * fm::C1_LO;
+    return k;
+}
+
+// high word of a*idx + b (mod 2^64); kWide: idx may reach 2^32 (V > 2^16)
+template <bool kWide>
+__device__ __forceinline__ uint32_t depth_hi(const ColKey& k, uint32_t x_lo, uint32_t x_hi) {
+    const uint64_t p = (uint64_t)k.a_lo * x_lo + k.b;
+    uint32_t hi = (uint32_t)(p >> 32) + k.a_hi * x_lo;
+    if (kWide) hi += k.a_lo * x_hi;
+    return hi;
+}
+
+// hi32(fmix64(idx ^ c)); fold = idx_lo ^ (idx_hi >> 1), precomputed per record
+template <bool kWide>
+__device__ __forceinline__ uint32_t checksum_w(const ColKey& k, uint32_t x_hi, uint32_t fold) {
+    const uint32_t lo1 = fold ^ k.kfold;  // low word after x ^= c; x ^= x >> 33
+    uint32_t lo2, hi2;
+    if (kWide) {
+        const uint32_t hi1 = x_hi ^ k.c_hi;
+        const uint64_t q = (uint64_t)lo1 * fm::C1_LO;
+        lo2 = (uint32_t)q;
+        hi2 = (uint32_t)(q >> 32) + lo1 * fm::C1_HI + hi1 * fm::C1_LO;
+    } else {
+        const uint64_t q = (uint64_t)lo1 * fm::C1_LO + ((uint64_t)k.k2 << 32);
+        lo2 = (uint32_t)q;
+        hi2 = (uint32_t)(q >> 32) + lo1 * fm::C1_HI;
+    }
+    const uint32_t lo3 = lo2 ^ (hi2 >> 1);
+    return __umulhi(lo3, fm::C2_LO) + lo3 * fm::C2_HI + hi2 * fm::C2_LO;
+}
+
+// One CTA = 32*ceil(7K/32) threads; thread c owns CubeSketch column c = 7k + j
+// (one "Graph Worker" per column; no two threads write one bucket).
+// Dynamic shared memory:
+//   delta alpha  [Rs][CP] u64 (kAtomic: two u32 planes lo[Rs][CP], hi[Rs][CP])
+//   delta gamma  [Rs][CP] u32
+//   staged records [tile] (kWide: uint4 {idx_lo, idx_hi, fold, 0}; else u32 idx)
+//   per-k deepest touched row [K] u32
+// With the [row][column] layout the 32 lanes of a warp hit 32 distinct banks
+// whatever rows their updates land in.  kAtomic uses shared-memory atomics for
+// the XORs, so an update never waits on a shared-memory load.
+template <bool kAtomic, bool kWide>
 __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
     extern __shared__ __align__(16) uint64_t smem[];
     __shared__ uint32_t s_tile, s_node;
     if (p.flags[0]) return;
     const uint32_t CP = blockDim.x, c = threadIdx.x;
-    uint64_t* dA = smem;
-    uint64_t* sidx = dA + (size_t)p.Rs * CP;
-    uint32_t* dG = reinterpret_cast<uint32_t*>(sidx + p.tile);
-    uint32_t* maxd = dG + (size_t)p.Rs * CP;
+    const uint32_t Rs = p.Rs, R = p.R, RC = Rs * CP;
+    uint64_t* dA = smem;                                 // kAtomic == false
+    uint32_t* dAlo = reinterpret_cast<uint32_t*>(smem);  // kAtomic == true
+    uint32_t* dAhi = dAlo + RC;
+    uint32_t* dG = reinterpret_cast<uint32_t*>(smem + RC);
+    uint32_t* stage = dG + RC;  // 16-byte aligned: RC*12 bytes, RC a multiple of 32
+    uint4* stage4 = reinterpret_cast<uint4*>(stage);
+    uint32_t* maxd = stage + (kWide ? 4u : 1u) * p.tile;
 
     const bool active = c < p.ncol;
     const uint32_t k = c / GZ_COLS, j = c - k * GZ_COLS;
-    uint64_t ka = 0, kb = 0, kc = 0;
-    if (active) {
-        ka = p.keys.a[c];
-        kb = p.keys.b[c];
-        kc = p.keys.c[c];
-    }
-    for (uint32_t i = c; i < p.Rs * CP; i += CP) {
-        dA[i] = 0;
+    ColKey key{};
+    if (active) key = make_colkey(p.keys.a[c], p.keys.b[c], p.keys.c[c]);
+    for (uint32_t i = c; i < RC; i += CP) {
+        if (kAtomic) {
+            dAlo[i] = 0;
+            dAhi[i] = 0;
+        } else {
+            dA[i] = 0;
+        }
         dG[i] = 0;
     }
     for (uint32_t i = c; i < p.K; i += CP) maxd[i] = 0;
     const uint32_t total = p.offsets[p.V];
     const uint32_t ntiles = (total + p.tile - 1) / p.tile;
-    const uint32_t Rs = p.Rs, R = p.R;
     unsigned long long n_rows = 0, n_deep = 0;
 
     for (;;) {
@@ -174,13 +292,22 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
             const uint32_t seg_end = min(p.offsets[x + 1], hi);
             const uint32_t nseg = seg_end - pos;
             if (nseg > 0) {
-                for (uint32_t i = c; i < nseg; i += CP) sidx[i] = edge_index(x, p.records[pos + i], p.V);
+                for (uint32_t i = c; i < nseg; i += CP) {
+                    const uint64_t idx = edge_index(x, p.records[pos + i], p.V);
+                    if (kWide) {
+                        const uint32_t ilo = (uint32_t)idx, ihi = (uint32_t)(idx >> 32);
+                        stage4[i] = make_uint4(ilo, ihi, ilo ^ (ihi >> 1), 0u);
+                    } else {
+                        stage[i] = (uint32_t)idx;
+                    }
+                }
                 __syncthreads();
                 if (nseg < p.small_seg) {
                     // short segment: straight to global memory
                     if (active) {
+                        const uint64_t ka = p.keys.a[c], kb = p.keys.b[c], kc = p.keys.c[c];
                         for (uint32_t i = 0; i < nseg; ++i) {
-                            const uint64_t idx = sidx[i];
+                            const uint64_t idx = kWide ? ((uint64_t)stage4[i].y << 32 | stage4[i].x) : stage[i];
                             const uint32_t d = exact_depth(depth_word(ka, kb, idx), R);
                             atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, d, j)),
                                       (unsigned long long)idx);
@@ -192,17 +319,35 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                     if (active) {
 #pragma unroll 4
                         for (uint32_t i = 0; i < nseg; ++i) {
-                            const uint64_t idx = sidx[i];
-                            const uint64_t tw = depth_word(ka, kb, idx);
-                            const uint32_t d = __clz(static_cast<uint32_t>(tw >> 32));
-                            const uint32_t g = checksum(kc, idx);
+                            uint32_t xlo, xhi, fold;
+                            if (kWide) {
+                                const uint4 r = stage4[i];
+                                xlo = r.x;
+                                xhi = r.y;
+                                fold = r.z;
+                            } else {
+                                xlo = stage[i];
+                                xhi = 0;
+                                fold = xlo;
+                            }
+                            const uint32_t th = depth_hi<kWide>(key, xlo, xhi);
+                            const uint32_t d = __clz(th);
+                            const uint32_t g = checksum_w<kWide>(key, xhi, fold);
                             if (d < Rs) {
-                                dA[d * CP + c] ^= idx;
-                                dG[d * CP + c] ^= g;
+                                const uint32_t slot = d * CP + c;
+                                if (kAtomic) {
+                                    atomicXor(dAlo + slot, xlo);
+                                    if (kWide) atomicXor(dAhi + slot, xhi);
+                                    atomicXor(dG + slot, g);
+                                } else {
+                                    dA[slot] ^= ((uint64_t)xhi << 32) | xlo;
+                                    dG[slot] ^= g;
+                                }
                                 md = max(md, d);
                             } else {
                                 ++n_deep;
-                                const uint32_t dd = exact_depth(tw, R);
+                                const uint64_t idx = ((uint64_t)xhi << 32) | xlo;
+                                const uint32_t dd = exact_depth(depth_word(p.keys.a[c], p.keys.b[c], idx), R);
                                 atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, dd, j)),
                                           (unsigned long long)idx);
                                 atomicXor(p.s.gamma(x, k, dd, j), g);
@@ -217,13 +362,23 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                         const uint32_t row = rem / GZ_COLS, jj = rem - row * GZ_COLS;
                         if (row <= maxd[kk]) {
                             const uint32_t slot = row * CP + kk * GZ_COLS + jj;
-                            const uint64_t a = dA[slot];
+                            uint64_t a;
+                            if (kAtomic) {
+                                a = ((uint64_t)dAhi[slot] << 32) | dAlo[slot];
+                            } else {
+                                a = dA[slot];
+                            }
                             const uint32_t g = dG[slot];
                             if (a | g) {
                                 atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, kk, row, jj)),
                                           (unsigned long long)a);
                                 atomicXor(p.s.gamma(x, kk, row, jj), g);
-                                dA[slot] = 0;
+                                if (kAtomic) {
+                                    dAlo[slot] = 0;
+                                    dAhi[slot] = 0;
+                                } else {
+                                    dA[slot] = 0;
+                                }
                                 dG[slot] = 0;
                             }
                         }
@@ -242,6 +397,13 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
     }
     if (n_rows) atomicAdd(&p.stats[0], n_rows);
     if (n_deep) atomicAdd(&p.stats[1], n_deep);
+}
+
+using BatchedFn = void (*)(BatchedArgs);
+
+static BatchedFn batched_fn(uint32_t mode, bool wide) {
+    if (mode) return wide ? k_batched<true, true> : k_batched<true, false>;
+    return wide ? k_batched<false, true> : k_batched<false, false>;
 }
 
 // ------------------------------------------------------------------ plain update
@@ -318,14 +480,17 @@ gz_status ingest_setup(gz_handle* h) {
     rs = std::min<uint32_t>(rs, 32);
     rs = std::min<uint32_t>(rs, h->R);
     h->smem_rows = rs;
-    h->tile = h->cfg.tile_records ? h->cfg.tile_records : 1024;
+    h->tile = h->cfg.tile_records ? h->cfg.tile_records : 512;
     h->small_seg = h->cfg.small_segment ? h->cfg.small_segment : 4;
-    h->batched_smem = (size_t)rs * h->block * 12 + (size_t)h->tile * 8 + (size_t)h->K * 4;
-    cudaError_t e = cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const bool wide = (uint64_t)h->V * h->V > (1ull << 32);
+    h->batched_smem = (size_t)rs * h->block * 12 + (size_t)h->tile * (wide ? 16 : 4) + (size_t)h->K * 4;
+    if (h->cfg.smem_mode > 1) return set_error(h, GZ_EINVAL, "smem_mode must be 0 or 1");
+    const void* fn = (const void*)batched_fn(h->cfg.smem_mode, wide);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)h->batched_smem);
     if (e != cudaSuccess) return cuda_check(h, e, "cudaFuncSetAttribute(k_batched)");
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batched, (int)h->block, h->batched_smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, (int)h->block, h->batched_smem);
     if (e != cudaSuccess) return cuda_check(h, e, "occupancy(k_batched)");
     if (nb < 1) return set_error(h, GZ_EINVAL, "batched kernel does not fit on an SM");
     uint32_t per_sm = h->cfg.ctas_per_sm ? std::min<uint32_t>(h->cfg.ctas_per_sm, nb) : nb;
@@ -353,7 +518,7 @@ gz_status ingest_batch(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, u
         e = cudaMemsetAsync(h->d_counts, 0, (size_t)(h->V + 1) * sizeof(uint32_t), st);
         if (e != cudaSuccess) return cuda_check(h, e, "memset counts");
         k_validate_count<<<grid, tpb, 0, st>>>(d_u, d_v, n, h->V, h->d_counts, h->d_flags);
-        launch_scan(h->d_counts, h->d_offsets, h->d_cursor, h->V, st);
+        launch_scan(h->d_counts, h->d_offsets, h->d_cursor, h->V, st, h->d_scan_tmp);
         k_scatter<<<grid, tpb, 0, st>>>(d_u, d_v, n, h->d_cursor, h->d_records, h->d_flags);
         BatchedArgs a;
         a.s = view_of(h);
@@ -371,8 +536,9 @@ gz_status ingest_batch(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, u
         a.small_seg = h->small_seg;
         a.stats = reinterpret_cast<unsigned long long*>(h->d_stats);
         if ((ps = prof_event(h)) != GZ_OK) return ps;
-        k_batched<<<h->batched_grid, h->block, h->batched_smem, st>>>(a);
-        h->launches += 4;
+        const bool wide = (uint64_t)h->V * h->V > (1ull << 32);
+        batched_fn(h->cfg.smem_mode, wide)<<<h->batched_grid, h->block, h->batched_smem, st>>>(a);
+        h->launches += 5;
     }
     if ((ps = prof_event(h)) != GZ_OK) return ps;
     if (h->prof) {

@@ -378,12 +378,12 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
         if (e == cudaSuccess) e = cudaMemsetAsync(h->q_ctr, 0, 4 * sizeof(uint32_t), stm);  // roots..fails
         if (e != cudaSuccess) return cuda_check(h, e, "memset round");
         k_q_count<<<gV, tpb, 0, stm>>>(q);
-        launch_scan(h->q_count, h->q_off, h->q_cursor, V, stm);
+        launch_scan(h->q_count, h->q_off, h->q_cursor, V, stm, h->d_scan_tmp);
         k_q_group<<<gV, tpb, 0, stm>>>(q);
         k_q_roots<<<gV, tpb, 0, stm>>>(q);
         k_q_merge_items<<<h->sm_count * 4, 384, 0, stm>>>(q);
         k_q_sample<<<h->sm_count * 16, 256, sample_smem, stm>>>(q);
-        h->launches += 6;
+        h->launches += 7;
         e = cudaMemcpyAsync(h->h_ctr, h->q_ctr, C_N * sizeof(uint32_t), cudaMemcpyDeviceToHost, stm);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stm);
         if (e != cudaSuccess) return cuda_check(h, e, "query round");
@@ -408,10 +408,10 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
             k_q_fj_mark<<<gR, tpb, 0, stm>>>(q, F, Mx, h->q_flag);
             // q_cursor is free again: reuse it for the accept flags
             k_q_accept<<<gV, tpb, 0, stm>>>(q, h->q_flag, h->q_cursor);
-            launch_scan(h->q_cursor, h->q_pos, nullptr, V, stm);
+            launch_scan(h->q_cursor, h->q_pos, nullptr, V, stm, h->d_scan_tmp);
             k_q_forest_write<<<gV, tpb, 0, stm>>>(q, h->q_cursor, h->q_pos, h->q_forest);
             k_q_forest_advance<<<1, 1, 0, stm>>>(q, h->q_pos);
-            h->launches += J + 6;
+            h->launches += J + 7;
         }
         k_q_relabel<<<gV, tpb, 0, stm>>>(q);
     }

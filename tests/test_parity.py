@@ -66,15 +66,17 @@ def test_planted_small_config_bit_exact(kernel):
     assert np.array_equal(want["labels"], oracle.brute_cc(spec.V, u, v))
 
 
+@pytest.mark.parametrize("smem_mode", [0, 1])
 @pytest.mark.parametrize("V", [2, 3, 77, 1000, 4097])
-def test_ragged_sizes_many_chunks_and_tiles(V):
+def test_ragged_sizes_many_chunks_and_tiles(V, smem_mode):
     # chunk of 2^10 updates (many chunks + a ragged tail), tiles of 64 records
     # (heavy nodes split across CTAs), 3 shared-memory rows (deep rows go to
     # global memory directly), short segments through the direct path
     n = 5000 if V > 3 else 301
     u, v = S.random_stream(V, n, seed=V, n_distinct=max(1, n // 3))
     A, G = oracle.ingest(V, 42, u, v)
-    g = _gpu_graph(V, 42, u, v, chunk_log2=10, tile_records=64, smem_rows=3, small_segment=3)
+    g = _gpu_graph(V, 42, u, v, chunk_log2=10, tile_records=64, smem_rows=3, small_segment=3,
+                   smem_mode=smem_mode)
     _assert_same_sketches(g, A, G)
     _assert_same_query(g, A, G, 42)
 
@@ -104,13 +106,33 @@ def test_kronecker_full_query_parity():
 
 
 def test_host_and_device_inputs_agree():
+    # host input goes through two staging buffers on a copy stream (15 chunks
+    # of 2^12 updates here, so both buffers are reused several times), and a
+    # second call must not overwrite a buffer the first call's kernels read
     V = 3000
     u, v = S.random_stream(V, 60000, seed=2)
     g1 = _gpu_graph(V, 1, u, v, on_device=True)
-    g2 = _gpu_graph(V, 1, u, v, on_device=False, chunk_log2=12)
+    g2 = gz.Graph(V, 1, chunk_log2=12)
+    half = len(u) // 2
+    g2.edge_update(u[:half], v[:half])
+    g2.edge_update(u[half:], v[half:])
+    g2.sync()
     a1, b1 = g1.export_sketch()
     a2, b2 = g2.export_sketch()
     assert np.array_equal(a1, a2) and np.array_equal(b1, b2)
+
+
+@pytest.mark.parametrize("smem_mode", [0, 1])
+def test_smem_modes_bit_exact_kronecker(smem_mode):
+    spec = S.KronSpec(L=12, seed=8, target_edges=0.4 * 4096 * 4095 / 2, churn=0.1, n_iso=30,
+                      slice_log2=20)
+    u, v = spec.stream()
+    g = _gpu_graph(spec.V, 3, u, v, smem_mode=smem_mode, chunk_log2=20)
+    rng = np.random.default_rng(smem_mode)
+    for x in sorted(set(rng.integers(0, spec.V, 12).tolist()) | {0, 1}):
+        A, G = oracle.sketch_node(spec.V, 3, x, spec.node_neighbors(x))
+        a, gg = g.export_sketch(x, x + 1)
+        assert np.array_equal(a[0], A) and np.array_equal(gg[0], G), x
 
 
 def test_invalid_batch_is_discarded_whole():
