@@ -190,6 +190,39 @@ gz_status gz_profile_enable(gz_handle *h, int enable);
 /* Synchronise and read the totals of the current window. */
 gz_status gz_profile_read(gz_handle *h, gz_profile *out);
 
+/* Allocation-free ingestion (the paper has no counterpart: this serves
+ * callers that cannot allocate device memory).  Code running while a stream is
+ * captured into a CUDA graph cannot call cudaMalloc without breaking the
+ * capture; a host whose device memory belongs to another allocator cannot let
+ * a library allocate behind its back; a latency-bound loop may not take the
+ * driver's allocation lock.  This call applies a batch of updates like
+ * gz_edge_update but allocates and frees nothing: its scratch is a fixed
+ * array of about 10 MB in the library's static device memory, which every GPU
+ * that loads the library holds until the process exits.
+ *   sketch : device, V*K*84*R bytes of node sketches in the handle layout
+ *            (exact-depth rows; per node, for each k, alpha[R][7] u64 then
+ *            gamma[R][7] u32), zeroed for the empty graph; e.g. the array of
+ *            a handle from gz_info, or memory the caller owns.
+ *   V, seed: vertex count (2 <= V <= GZ_NOALLOC_MAX_V) and the hash seed the
+ *            sketches were built with.
+ *   u, v   : device, n updates (n <= GZ_NOALLOC_MAX_UPDATES), same meaning and
+ *            validation as gz_edge_update: a self loop or an id >= V discards
+ *            the whole batch.
+ *   status : device u32 or NULL; set on the stream to 1 when the batch was
+ *            discarded, else 0.
+ *   stream : cudaStream_t of all the work (NULL = default stream).
+ * Returns GZ_EINVAL (nothing queued) for V or n beyond the limits or null
+ * pointers, GZ_ECUDA when a CUDA call fails.  The first call on a device sets
+ * up that device (it looks up the scratch array's device address); make that
+ * first call before any stream capture begins.  All calls share the one
+ * scratch array, so calls that overlap on the GPU race: issue them on one
+ * stream, or order them. */
+#define GZ_NOALLOC_MAX_V (1u << 17)
+#define GZ_NOALLOC_MAX_UPDATES (1ull << 20)
+gz_status gz_sketch_update_noalloc(void *sketch, uint32_t V, uint64_t seed,
+                                   const uint32_t *u, const uint32_t *v, size_t n,
+                                   uint32_t *status, void *stream);
+
 /* Human-readable reason of the last non-OK status (never NULL). */
 const char *gz_last_error(gz_handle *h);
 

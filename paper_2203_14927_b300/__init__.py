@@ -123,6 +123,9 @@ _SIGNATURES = {
     "gz_gen_kron_chunk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_uint64, ctypes.c_void_p]),
     "gz_gen_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "gz_sketch_update_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                                ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 

@@ -569,3 +569,163 @@ gz_status export_nested(gz_handle* h, uint32_t lo, uint32_t hi, uint64_t* d_alph
 }
 
 }  // namespace gz
+
+// ======================================================================
+// Allocation-free ingestion entry point (gz_sketch_update_noalloc).
+//
+// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
+// being captured into a graph (an allocation would break the capture), hosts
+// whose device memory is owned by another allocator (a framework pool that
+// must see every byte), and latency-bound loops that may not take the
+// driver's allocation lock.  For them this variant of the partition + batched
+// update runs entirely in a fixed scratch array that lives in this file's
+// static device memory: every GPU that loads the library holds it (about
+// 10 MB) until the process exits.  The caller passes the sketch memory and
+// the update arrays; nothing is allocated or freed.
+// ======================================================================
+
+#include <mutex>
+
+namespace gz {
+namespace noalloc {
+
+constexpr uint32_t kMaxV = GZ_NOALLOC_MAX_V;
+constexpr uint64_t kMaxUpdates = GZ_NOALLOC_MAX_UPDATES;
+constexpr uint32_t kMaxCols = 7u * 30u;  // K(2^17) = 30 CubeSketches per node
+// layout in 32-bit words (the u64 parts first, so they stay 8-byte aligned)
+constexpr size_t kKeys = 0;                                   // 3 x kMaxCols u64
+constexpr size_t kStats = kKeys + 2 * 3 * kMaxCols;           // 2 u64
+constexpr size_t kFlags = kStats + 4;                         // 4 u32
+constexpr size_t kCounts = kFlags + 4;                        // kMaxV + 1
+constexpr size_t kOffsets = kCounts + kMaxV + 1;              // kMaxV + 1
+constexpr size_t kCursor = kOffsets + kMaxV + 1;              // kMaxV + 1
+constexpr size_t kTiles = kCursor + kMaxV + 1;                // scan tile sums
+constexpr size_t kRecords = kTiles + (kMaxV + 1) / 1024 + 2;  // 2 x kMaxUpdates
+constexpr size_t kWords = kRecords + 2 * kMaxUpdates;
+
+static __device__ __align__(256) uint32_t g_scratch[kWords];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_mu;
+static uint32_t* g_ptr[kMaxDevices];
+static int g_sms[kMaxDevices];
+
+// Per-column hash keys from the seed (the same SplitMix64 schedule as
+// gz_create): a = SM(seed, 3col) | 1, b = SM(seed, 3col+1), c = SM(seed, 3col+2).
+__global__ void k_keys(uint64_t seed, uint32_t ncol, uint64_t* a, uint64_t* b, uint64_t* c) {
+    const uint32_t col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol) return;
+    uint64_t out[3];
+    for (int w = 0; w < 3; ++w) {
+        uint64_t z = seed + 0x9E3779B97F4A7C15ull * (3ull * col + w + 1);
+        z ^= z >> 30;
+        z *= 0xBF58476D1CE4E5B9ull;
+        z ^= z >> 27;
+        z *= 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        out[w] = z;
+    }
+    a[col] = out[0] | 1ull;
+    b[col] = out[1];
+    c[col] = out[2];
+}
+
+__global__ void k_status(const uint32_t* flags, uint32_t* status) { *status = flags[0] ? 1u : 0u; }
+
+// Once per device, with that device current: the device address of the
+// scratch array (its name is only a host-side stand-in in host code).
+static gz_status setup(int dev, uint32_t** ptr, int* sms) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return GZ_ECUDA;
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GZ_ECUDA;
+        for (int wide = 0; wide < 2; ++wide)
+            if (cudaFuncSetAttribute((const void*)batched_fn(1, wide != 0),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024) != cudaSuccess)
+                return GZ_ECUDA;
+        g_sms[dev] = n;
+        g_ptr[dev] = static_cast<uint32_t*>(p);
+    }
+    *ptr = g_ptr[dev];
+    *sms = g_sms[dev];
+    return GZ_OK;
+}
+
+}  // namespace noalloc
+}  // namespace gz
+
+extern "C" gz_status gz_sketch_update_noalloc(void* sketch, uint32_t V, uint64_t seed, const uint32_t* u,
+                                              const uint32_t* v, size_t n, uint32_t* status, void* stream) {
+    using namespace gz;
+    using namespace gz::noalloc;
+    if (!sketch || V < 2 || V > kMaxV || n > kMaxUpdates || (n && (!u || !v))) return GZ_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GZ_ECUDA;
+    uint32_t* base = nullptr;
+    int sms = 0;
+    gz_status s = setup(dev, &base, &sms);
+    if (s != GZ_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    uint32_t L = 0;
+    while ((1ull << L) < V) ++L;
+    uint32_t K = 0;
+    {
+        unsigned __int128 lhs = 1, rhs = V;
+        while (lhs < rhs) {
+            lhs *= 3;
+            rhs *= 2;
+            ++K;
+        }
+    }
+    const uint32_t R = 2 * L, ncol = 7 * K;
+    const uint32_t block = (ncol + 31) / 32 * 32;
+    const uint32_t Rs = std::min<uint32_t>(16, R), tile = 1024;
+    const bool wide = (uint64_t)V * V > (1ull << 32);
+
+    uint64_t* keys = reinterpret_cast<uint64_t*>(base + kKeys);
+    uint32_t* flags = base + kFlags;
+    uint32_t* counts = base + kCounts;
+    // flags (batch, work counter, sticky) and stats start at zero on every call
+    if (cudaMemsetAsync(base + kStats, 0, 8 * sizeof(uint32_t), st) != cudaSuccess) return GZ_ECUDA;
+    if (cudaMemsetAsync(counts, 0, (size_t)(V + 1) * sizeof(uint32_t), st) != cudaSuccess) return GZ_ECUDA;
+    k_keys<<<(ncol + 127) / 128, 128, 0, st>>>(seed, ncol, keys, keys + kMaxCols, keys + 2 * kMaxCols);
+    if (n) {
+        const uint32_t tpb = 256;
+        const uint32_t grid = (uint32_t)std::min<uint64_t>((n + tpb - 1) / tpb, (uint64_t)sms * 8);
+        k_validate_count<<<grid, tpb, 0, st>>>(u, v, n, V, counts, flags);
+        launch_scan(counts, base + kOffsets, base + kCursor, V, st, base + kTiles);
+        k_scatter<<<grid, tpb, 0, st>>>(u, v, n, base + kCursor, base + kRecords, flags);
+        BatchedArgs a;
+        a.s.base = static_cast<uint8_t*>(sketch);
+        a.s.per_k_bytes = 84u * R;
+        a.s.node_bytes = (uint64_t)K * a.s.per_k_bytes;
+        a.s.gamma_off = 56u * R;
+        a.keys.a = keys;
+        a.keys.b = keys + kMaxCols;
+        a.keys.c = keys + 2 * kMaxCols;
+        a.offsets = base + kOffsets;
+        a.records = base + kRecords;
+        a.flags = flags;
+        a.work = flags + 1;
+        a.stats = reinterpret_cast<unsigned long long*>(base + kStats);
+        a.V = V;
+        a.K = K;
+        a.R = R;
+        a.ncol = ncol;
+        a.Rs = Rs;
+        a.tile = tile;
+        a.small_seg = 4;
+        const size_t smem = (size_t)Rs * block * 12 + (size_t)tile * (wide ? 16 : 4) + (size_t)K * 4;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_fn(1, wide), (int)block, smem) !=
+                cudaSuccess ||
+            per_sm < 1)
+            return GZ_ECUDA;
+        batched_fn(1, wide)<<<per_sm * sms, block, smem, st>>>(a);
+    }
+    if (status) k_status<<<1, 1, 0, st>>>(flags, status);
+    return cudaGetLastError() == cudaSuccess ? GZ_OK : GZ_ECUDA;
+}
