@@ -162,7 +162,7 @@ gz_status gz_destroy(gz_handle* h) {
                     h->q_cursor, h->q_members, h->q_roots, h->q_target, h->q_item_base,
                     h->q_item_cnt, h->q_item_comp, h->q_item_lo, h->q_item_hi, h->q_F, h->q_F2,
                     h->q_M, h->q_M2, h->q_flag, h->q_pos, h->q_forest, h->q_ctr, h->q_res,
-                    h->q_partial, h->q_trace, h->d_stats, h->d_scan_tmp};
+                    h->q_partial, h->q_trace, h->d_stats, h->d_scan_tmp, h->d_tile_node};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);

@@ -32,6 +32,7 @@ struct gz_handle {
     uint32_t* d_offsets = nullptr; // V+1
     uint32_t* d_cursor = nullptr;  // V
     uint32_t* d_records = nullptr; // 2*chunk
+    uint32_t* d_tile_node = nullptr; // first node of every record tile (2*chunk/tile + 2)
     uint32_t* d_stage = nullptr;   // 2 buffers x (u, v) x chunk, host-input staging (lazy)
     cudaStream_t copy_stream = nullptr;  // H2D copies of host input (lazy)
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};

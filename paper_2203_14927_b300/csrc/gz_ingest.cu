@@ -162,11 +162,23 @@ struct BatchedArgs {
     Keys keys;
     const uint32_t* offsets;  // V+1
     const uint32_t* records;
+    const uint32_t* tile_node;  // first node of every record tile
     const uint32_t* flags;
     uint32_t* work;  // tile counter
     unsigned long long* stats;  // [0] rows flushed, [1] deep column updates
     uint32_t V, K, R, ncol, Rs, tile, small_seg;
 };
+
+// tile_node[t] = the node x with offsets[x] <= t*tile < offsets[x+1]: node x
+// owns the tiles whose first record falls inside its segment.
+__global__ void k_tile_nodes(const uint32_t* __restrict__ offsets, uint32_t V, uint32_t tile,
+                             const uint32_t* __restrict__ flags, uint32_t* __restrict__ tile_node) {
+    if (flags[0]) return;
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < V; x += gridDim.x * blockDim.x) {
+        const uint32_t lo = offsets[x], hi = offsets[x + 1];
+        for (uint32_t t = (lo + tile - 1) / tile; t * tile < hi; ++t) tile_node[t] = x;
+    }
+}
 
 // The two hashes of one column written on 32-bit words, with every part that
 // depends only on the column's keys folded into per-thread constants.  They
@@ -237,7 +249,6 @@ __device__ __forceinline__ uint32_t checksum_w(const ColKey& k, uint32_t x_hi, u
 template <bool kAtomic, bool kWide>
 __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
     extern __shared__ __align__(16) uint64_t smem[];
-    __shared__ uint32_t s_tile, s_node;
     if (p.flags[0]) return;
     const uint32_t CP = blockDim.x, c = threadIdx.x;
     const uint32_t Rs = p.Rs, R = p.R, RC = Rs * CP;
@@ -266,28 +277,17 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
     const uint32_t total = p.offsets[p.V];
     const uint32_t ntiles = (total + p.tile - 1) / p.tile;
     unsigned long long n_rows = 0, n_deep = 0;
+    __shared__ uint32_t s_t[2];
+    if (c == 0) s_t[0] = atomicAdd(p.work, 1u);
 
-    for (;;) {
+    for (uint32_t it = 0;; ++it) {
         __syncthreads();
-        if (c == 0) {
-            const uint32_t t = atomicAdd(p.work, 1u);
-            s_tile = t;
-            if (t < ntiles) {
-                // node x with offsets[x] <= t*tile < offsets[x+1]
-                const uint32_t lo = t * p.tile;
-                uint32_t L = 0, H = p.V;
-                while (H - L > 1) {
-                    const uint32_t mid = (L + H) >> 1;
-                    if (p.offsets[mid] <= lo) L = mid; else H = mid;
-                }
-                s_node = L;
-            }
-        }
-        __syncthreads();
-        const uint32_t t = s_tile;
+        const uint32_t t = s_t[it & 1];
         if (t >= ntiles) break;
+        // claim the next tile now; its index is read after the next barrier
+        if (c == 0) s_t[(it + 1) & 1] = atomicAdd(p.work, 1u);
         const uint32_t lo = t * p.tile, hi = min(lo + p.tile, total);
-        uint32_t x = s_node, pos = lo;
+        uint32_t x = p.tile_node[t], pos = lo;
         while (pos < hi) {
             const uint32_t seg_end = min(p.offsets[x + 1], hi);
             const uint32_t nseg = seg_end - pos;
@@ -317,43 +317,97 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                 } else {
                     uint32_t md = 0;
                     if (active) {
-#pragma unroll 4
-                        for (uint32_t i = 0; i < nseg; ++i) {
+                        // one column update staged in shared memory (d < Rs)
+                        auto put = [&](uint32_t d, uint32_t xlo, uint32_t xhi, uint32_t g) {
+                            const uint32_t slot = d * CP + c;
+                            if (kAtomic) {
+                                atomicXor(dAlo + slot, xlo);
+                                if (kWide) atomicXor(dAhi + slot, xhi);
+                                atomicXor(dG + slot, g);
+                            } else {
+                                dA[slot] ^= ((uint64_t)xhi << 32) | xlo;
+                                dG[slot] ^= g;
+                            }
+                        };
+                        // a column update whose exact depth is Rs or more goes to HBM
+                        auto deep = [&](uint32_t xlo, uint32_t xhi, uint32_t g) {
+                            ++n_deep;
+                            const uint64_t idx = ((uint64_t)xhi << 32) | xlo;
+                            const uint32_t dd = exact_depth(depth_word(p.keys.a[c], p.keys.b[c], idx), R);
+                            atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, dd, j)),
+                                      (unsigned long long)idx);
+                            atomicXor(p.s.gamma(x, k, dd, j), g);
+                        };
+                        uint32_t i = 0;
+                        // four records at a time in straight-line code, so the
+                        // four hash chains interleave; one rare branch for deep rows
+                        for (; i + 4 <= nseg; i += 4) {
+                            uint32_t xlo[4], xhi[4], fold[4];
+                            if (kWide) {
+#pragma unroll
+                                for (int r = 0; r < 4; ++r) {
+                                    const uint4 q = stage4[i + r];
+                                    xlo[r] = q.x;
+                                    xhi[r] = q.y;
+                                    fold[r] = q.z;
+                                }
+                            } else {
+                                const uint4 q = reinterpret_cast<const uint4*>(stage)[i >> 2];
+                                xlo[0] = q.x;
+                                xlo[1] = q.y;
+                                xlo[2] = q.z;
+                                xlo[3] = q.w;
+#pragma unroll
+                                for (int r = 0; r < 4; ++r) {
+                                    xhi[r] = 0;
+                                    fold[r] = xlo[r];
+                                }
+                            }
+                            uint32_t d[4], g[4];
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) {
+                                d[r] = __clz(depth_hi<kWide>(key, xlo[r], xhi[r]));
+                                g[r] = checksum_w<kWide>(key, xhi[r], fold[r]);
+                            }
+                            const uint32_t dmax = max(max(d[0], d[1]), max(d[2], d[3]));
+                            if (dmax < Rs) {
+#pragma unroll
+                                for (int r = 0; r < 4; ++r) put(d[r], xlo[r], xhi[r], g[r]);
+                                md = max(md, dmax);
+                            } else {
+#pragma unroll
+                                for (int r = 0; r < 4; ++r) {
+                                    if (d[r] < Rs) {
+                                        put(d[r], xlo[r], xhi[r], g[r]);
+                                        md = max(md, d[r]);
+                                    } else {
+                                        deep(xlo[r], xhi[r], g[r]);
+                                    }
+                                }
+                            }
+                        }
+                        for (; i < nseg; ++i) {
                             uint32_t xlo, xhi, fold;
                             if (kWide) {
-                                const uint4 r = stage4[i];
-                                xlo = r.x;
-                                xhi = r.y;
-                                fold = r.z;
+                                const uint4 q = stage4[i];
+                                xlo = q.x;
+                                xhi = q.y;
+                                fold = q.z;
                             } else {
                                 xlo = stage[i];
                                 xhi = 0;
                                 fold = xlo;
                             }
-                            const uint32_t th = depth_hi<kWide>(key, xlo, xhi);
-                            const uint32_t d = __clz(th);
+                            const uint32_t d = __clz(depth_hi<kWide>(key, xlo, xhi));
                             const uint32_t g = checksum_w<kWide>(key, xhi, fold);
                             if (d < Rs) {
-                                const uint32_t slot = d * CP + c;
-                                if (kAtomic) {
-                                    atomicXor(dAlo + slot, xlo);
-                                    if (kWide) atomicXor(dAhi + slot, xhi);
-                                    atomicXor(dG + slot, g);
-                                } else {
-                                    dA[slot] ^= ((uint64_t)xhi << 32) | xlo;
-                                    dG[slot] ^= g;
-                                }
+                                put(d, xlo, xhi, g);
                                 md = max(md, d);
                             } else {
-                                ++n_deep;
-                                const uint64_t idx = ((uint64_t)xhi << 32) | xlo;
-                                const uint32_t dd = exact_depth(depth_word(p.keys.a[c], p.keys.b[c], idx), R);
-                                atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, dd, j)),
-                                          (unsigned long long)idx);
-                                atomicXor(p.s.gamma(x, k, dd, j), g);
+                                deep(xlo, xhi, g);
                             }
                         }
-                        atomicMax(&maxd[k], md);
+                    atomicMax(&maxd[k], md);
                     }
                     __syncthreads();
                     const uint32_t per_k = Rs * GZ_COLS;
@@ -495,6 +549,10 @@ gz_status ingest_setup(gz_handle* h) {
     if (nb < 1) return set_error(h, GZ_EINVAL, "batched kernel does not fit on an SM");
     uint32_t per_sm = h->cfg.ctas_per_sm ? std::min<uint32_t>(h->cfg.ctas_per_sm, nb) : nb;
     h->batched_grid = per_sm * h->sm_count;
+    if (h->cfg.kernel == GZ_KERNEL_BATCHED) {
+        e = cudaMalloc(&h->d_tile_node, (size_t)(2 * h->chunk / h->tile + 2) * sizeof(uint32_t));
+        if (e != cudaSuccess) return cuda_check(h, e, "tile table allocation");
+    }
     return GZ_OK;
 }
 
@@ -520,11 +578,14 @@ gz_status ingest_batch(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, u
         k_validate_count<<<grid, tpb, 0, st>>>(d_u, d_v, n, h->V, h->d_counts, h->d_flags);
         launch_scan(h->d_counts, h->d_offsets, h->d_cursor, h->V, st, h->d_scan_tmp);
         k_scatter<<<grid, tpb, 0, st>>>(d_u, d_v, n, h->d_cursor, h->d_records, h->d_flags);
+        k_tile_nodes<<<(h->V + 255) / 256, 256, 0, st>>>(h->d_offsets, h->V, h->tile, h->d_flags,
+                                                       h->d_tile_node);
         BatchedArgs a;
         a.s = view_of(h);
         a.keys = keys_of(h);
         a.offsets = h->d_offsets;
         a.records = h->d_records;
+        a.tile_node = h->d_tile_node;
         a.flags = h->d_flags;
         a.work = h->d_flags + 1;
         a.V = h->V;
@@ -538,7 +599,7 @@ gz_status ingest_batch(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, u
         if ((ps = prof_event(h)) != GZ_OK) return ps;
         const bool wide = (uint64_t)h->V * h->V > (1ull << 32);
         batched_fn(h->cfg.smem_mode, wide)<<<h->batched_grid, h->block, h->batched_smem, st>>>(a);
-        h->launches += 5;
+        h->launches += 6;
     }
     if ((ps = prof_event(h)) != GZ_OK) return ps;
     if (h->prof) {
@@ -601,7 +662,9 @@ constexpr size_t kOffsets = kCounts + kMaxV + 1;              // kMaxV + 1
 constexpr size_t kCursor = kOffsets + kMaxV + 1;              // kMaxV + 1
 constexpr size_t kTiles = kCursor + kMaxV + 1;                // scan tile sums
 constexpr size_t kRecords = kTiles + (kMaxV + 1) / 1024 + 2;  // 2 x kMaxUpdates
-constexpr size_t kWords = kRecords + 2 * kMaxUpdates;
+constexpr uint32_t kTile = 1024;                              // records per work tile
+constexpr size_t kTileNode = kRecords + 2 * kMaxUpdates;       // first node of every tile
+constexpr size_t kWords = kTileNode + 2 * kMaxUpdates / kTile + 2;
 
 static __device__ __align__(256) uint32_t g_scratch[kWords];
 
@@ -682,7 +745,7 @@ extern "C" gz_status gz_sketch_update_noalloc(void* sketch, uint32_t V, uint64_t
     }
     const uint32_t R = 2 * L, ncol = 7 * K;
     const uint32_t block = (ncol + 31) / 32 * 32;
-    const uint32_t Rs = std::min<uint32_t>(16, R), tile = 1024;
+    const uint32_t Rs = std::min<uint32_t>(16, R), tile = kTile;
     const bool wide = (uint64_t)V * V > (1ull << 32);
 
     uint64_t* keys = reinterpret_cast<uint64_t*>(base + kKeys);
@@ -698,6 +761,7 @@ extern "C" gz_status gz_sketch_update_noalloc(void* sketch, uint32_t V, uint64_t
         k_validate_count<<<grid, tpb, 0, st>>>(u, v, n, V, counts, flags);
         launch_scan(counts, base + kOffsets, base + kCursor, V, st, base + kTiles);
         k_scatter<<<grid, tpb, 0, st>>>(u, v, n, base + kCursor, base + kRecords, flags);
+        k_tile_nodes<<<(V + 255) / 256, 256, 0, st>>>(base + kOffsets, V, kTile, flags, base + kTileNode);
         BatchedArgs a;
         a.s.base = static_cast<uint8_t*>(sketch);
         a.s.per_k_bytes = 84u * R;
@@ -708,6 +772,7 @@ extern "C" gz_status gz_sketch_update_noalloc(void* sketch, uint32_t V, uint64_t
         a.keys.c = keys + 2 * kMaxCols;
         a.offsets = base + kOffsets;
         a.records = base + kRecords;
+        a.tile_node = base + kTileNode;
         a.flags = flags;
         a.work = flags + 1;
         a.stats = reinterpret_cast<unsigned long long*>(base + kStats);
