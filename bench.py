@@ -183,6 +183,25 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------------------- ranks
+
+
+def max_over_ranks(ms: float, dist=None, device="cpu") -> float:
+    """Slowest rank's time: the whole job finishes when the last replica does."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(updates_per_rank_step: int, steps: int, world: int, ms_max: float) -> float:
+    """Updates of all ranks over the slowest rank's time (weak scaling: every
+    rank ingests its own graph of the same size)."""
+    return world * updates_per_rank_step * steps / (ms_max / 1000.0)
+
+
 # ----------------------------------------------------------------------------- GPU path
 
 
@@ -268,14 +287,10 @@ def run_ours(args, rank: int, world: int):
     prof = g.profile_read()
     g.profile_enable(False)
     ms = ev0.elapsed_time(ev1)
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist, "cuda")
     ms_per_step = ms_max / args.steps
     step_updates = total
-    value = world * step_updates * args.steps / (ms_max / 1000.0)
+    value = whole_job_rate(step_updates, args.steps, world, ms_max)
     clk = clocks.summary()
 
     # --- roofline of the dominant kernel (batched CubeSketch update) ---------
@@ -284,25 +299,41 @@ def run_ours(args, rank: int, world: int):
     avg_ms = prof["update_ms"] / launches
     K, R = g.K, g.R
     upd_per_launch = prof["updates"] / launches
-    # bytes this kernel must move per launch: both records of every update
-    # (2 x u32 read), the row offsets, and a read+write of every (node, k, row)
-    # row of 7 buckets it XORs into HBM (7 x 12 B), plus the rare deep updates
-    bytes_per_launch = (8.0 * upd_per_launch + 4.0 * (spec.V + 1)
-                        + 2 * 84.0 * prof["rows_flushed"] / launches
-                        + 2 * 12.0 * prof["deep_updates"] / launches)
-    achieved = bytes_per_launch / (avg_ms / 1000.0) / 1e9
-    evals_per_launch = upd_per_launch * 2 * 7 * K
-    roofline = {
+    sec = avg_ms / 1000.0
+    s_total = spec.V * K * 84 * R
+    wide = spec.V * spec.V > (1 << 32)
+    col_updates = upd_per_launch * 2 * 7 * K
+    # HBM, by the method's bytes per chunk: the kernel's two records per update
+    # and one read + write of every node sketch (SURVEY 8(d) amortised RMW)
+    hbm_bytes = 8.0 * upd_per_launch + 2.0 * s_total
+    hbm = {"bound": "hbm", "achieved": hbm_bytes / sec / 1e9, "peak": peak, "unit": "GB/s",
+           "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+           "bytes_per_launch": hbm_bytes}
+    hbm["frac"] = hbm["achieved"] / peak
+    # integer issue: 16 (V > 2^16) or 14 32-bit operations per column update
+    ops = col_updates * (16 if wide else 14)
+    issue_peak = 148 * 4 * 32 * 2.032e9 / 1e12
+    alu = {"bound": "alu", "achieved": ops / sec / 1e12, "peak": issue_peak, "unit": "Tops/s",
+           "peak_source": "148 SMs x 4 schedulers x 32 lanes x 2.032 GHz (recipe unit counts and max clock)",
+           "ops_per_launch": ops, "ops_per_column_update": 16 if wide else 14}
+    alu["frac"] = alu["achieved"] / issue_peak
+    imads = col_updates * (5 if wide else 4)
+    imad_peak = 148 * 4 * 16 * 2.032e9 / 1e12
+    imad = {"bound": "alu (integer multiply-add pipe)", "achieved": imads / sec / 1e12, "peak": imad_peak,
+            "unit": "T IMAD/s", "peak_source": "148 SMs x 4 x 16-lane fmaheavy pipes x 2.032 GHz",
+            "imad_per_column_update": 5 if wide else 4}
+    imad["frac"] = imad["achieved"] / imad_peak
+    binding = max((hbm, alu, imad), key=lambda r: r["frac"])
+    roofline = dict(binding)
+    roofline.update({
         "kernel": "k_batched" if args.kernel == "batched" else "k_plain",
-        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-        "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
         "traffic": None,
-        "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms, "launches": launches,
-        "updates_per_launch": upd_per_launch,
-        "column_evals_per_s": evals_per_launch / (avg_ms / 1000.0),
+        "avg_launch_ms": avg_ms, "launches": launches, "updates_per_launch": upd_per_launch,
+        "column_updates_per_s": col_updates / sec,
         "share_of_step": prof["update_ms"] / ms if ms > 0 else None,
         "partition_ms_per_launch": prof["partition_ms"] / launches,
-    }
+        "all": {"hbm": hbm, "alu_issue": alu, "imad_pipe": imad},
+    })
 
     # --- query latency -----------------------------------------------------------
     qs = [st["ms"]] if args.queries == 0 else []
@@ -429,13 +460,208 @@ def run_ours(args, rank: int, world: int):
         dist.destroy_process_group()
 
 
+def run_serve(args, rank: int, world: int):
+    """Serving: many independent graphs resident on one GPU (gz_server)."""
+    import torch
+
+    import paper_2203_14927_b300 as gz
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rng = np.random.default_rng(2026)
+    n_graphs = args.serve_graphs
+    t0 = time.time()
+    graphs = []
+    for i in range(n_graphs):
+        e = int(rng.integers(10, 17))
+        V = 1 << e
+        n_upd = int(4 * V * e)
+        seed = 9000 + i
+        if i % 2 == 0:
+            spec = S.kron_for_updates(e, seed, n_upd, churn=0.1, chunk_updates=2 ** 22, n_iso=8)
+            U, Vv, tot = generate_on_device(spec, torch, gz)
+            u = U[:tot].cpu().numpy().view(np.uint32).copy()
+            v = Vv[:tot].cpu().numpy().view(np.uint32).copy()
+            del U, Vv
+            kind = "kronecker"
+        else:
+            u, v, _ = S.planted_sparse_stream(V, seed, n_upd)
+            kind = "planted"
+        cuts, pos = [], 0
+        while pos < len(u):
+            pos += int(2 ** rng.uniform(16, 20))
+            cuts.append(min(pos, len(u)))
+        graphs.append({"V": V, "seed": seed, "u": u, "v": v, "cuts": cuts, "kind": kind})
+    total_updates = sum(len(g["u"]) for g in graphs)
+    sizes = []
+    import ctypes
+    for g in graphs:
+        b = ctypes.c_size_t()
+        gz.lib().gz_memory_bytes(g["V"], None, ctypes.byref(b))
+        sizes.append(b.value)
+    log(f"[serve] {n_graphs} graphs, {total_updates} updates, sketches+scratch {sum(sizes) / 1e9:.1f} GB, "
+        f"generated in {time.time() - t0:.1f}s")
+
+    def schedule(window):
+        """Poisson arrivals: each graph's update chunks spread over `window`
+        seconds, a query after about one chunk in three and after the last."""
+        r = np.random.default_rng(77)
+        events = []
+        for gi, g in enumerate(graphs):
+            rate = len(g["cuts"]) / window
+            t, lo = 0.0, 0
+            for hi in g["cuts"]:
+                t += r.exponential(1.0 / rate)
+                events.append((t, gi, "u", lo, hi))
+                lo = hi
+                if r.random() < 1.0 / 3.0:
+                    events.append((t + 1e-9, gi, "q", 0, 0))
+            events.append((t + 2e-9, gi, "q", 0, 0))
+            events.append((t + 3e-9, gi, "close", 0, 0))
+        events.sort(key=lambda x: x[0])
+        return events
+
+    def serve(events, slots, one_at_a_time=False, paced=False):
+        srv = gz.Server(hbm_budget=int(args.serve_budget_gb * 1e9), slots=slots, max_batch=8)
+        gids = [srv.add_graph(g["V"], g["seed"]) for g in graphs]
+        torch.cuda.synchronize()
+
+        def submit(ev):
+            _, gi, kind, lo, hi = ev
+            g = graphs[gi]
+            if kind == "u":
+                srv.submit_update(gids[gi], g["u"][lo:hi], g["v"][lo:hi])
+            elif kind == "q":
+                srv.submit_query(gids[gi])
+            else:
+                srv.close_graph(gids[gi])
+
+        start = time.perf_counter()
+        if one_at_a_time:
+            for gi in range(len(graphs)):
+                for ev in events:
+                    if ev[1] == gi:
+                        submit(ev)
+                srv.drain()
+        else:
+            for ev in events:
+                if paced:
+                    now = time.perf_counter() - start
+                    if ev[0] > now:
+                        time.sleep(ev[0] - now)
+                submit(ev)
+            srv.drain()
+        elapsed = time.perf_counter() - start
+        done = srv.poll(1 << 20)
+        st = srv.stats()
+        err = srv.last_error()
+        srv.close()
+        bad = sum(1 for c in done if c["status"] not in (gz.GZ_OK, gz.GZ_ESKETCH_FAIL))
+        q = sorted(c["done_ms"] - c["submit_ms"] for c in done if c["kind"] == 1)
+        return {"elapsed_s": elapsed, "updates_per_s": total_updates / elapsed,
+                "query_p50_ms": float(np.percentile(q, 50)), "query_p99_ms": float(np.percentile(q, 99)),
+                "queries": len(q), "requests": len(done), "errors": bad, "last_error": err,
+                "peak_resident_gb": st["peak_resident_bytes"] / 1e9}
+
+    events0 = schedule(1.0)
+    mixed = serve(events0, args.serve_slots)  # all requests at once, arrival order
+    seq = serve(events0, 1, one_at_a_time=True)
+    window = max(1.0, total_updates / (0.5 * mixed["updates_per_s"]))
+    paced = serve(schedule(window), args.serve_slots, paced=True)
+    out = {
+        "metric": "serve_aggregate_updates_per_sec", "value": mixed["updates_per_s"], "unit": "updates/s",
+        "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": mixed["elapsed_s"] * 1000.0,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic: 64 seeded graphs, half Kronecker (device generator), half planted G(n,p)",
+        "config": {"workload": "serve: 64 graphs, V = 2^U{10..16}, update chunks 2^U(16,20) and CC queries "
+                               "as Poisson arrivals", "graphs": n_graphs, "total_updates": total_updates,
+                   "footprint_gb": sum(sizes) / 1e9, "budget_gb": args.serve_budget_gb,
+                   "slots": args.serve_slots, "paced_window_s": window},
+        "query_ms": {"p50_ms": paced["query_p50_ms"], "p99_ms": paced["query_p99_ms"], "n": paced["queries"],
+                     "offered_load": "half of the measured capacity, Poisson arrivals"},
+        "capacity_mixed": mixed, "capacity_one_at_a_time": seq, "paced": paced,
+        "speedup_vs_one_at_a_time": seq["elapsed_s"] / mixed["elapsed_s"],
+    }
+    print(json.dumps(out), flush=True)
+
+
+def _truth(spec):
+    from oracle.kron_cc import kron_components
+    return kron_components(spec)
+
+
+def run_failures(args, rank: int, world: int):
+    """Sketch-failure rate: for each seed, ingest a V = 2^17 Kronecker stream
+    and query; compare the labels with the exact components of the net graph
+    (oracle, on the host cores, in a spawn-started pool)."""
+    import multiprocessing as mp
+
+    if rank != 0:
+        return
+    L, n_upd, churn, _, desc = WORKLOADS[args.fail_workload]
+    seeds = [100 + i for i in range(args.seeds)]
+    specs = [S.kron_for_updates(L, sd, n_upd, churn=churn, chunk_updates=2 ** CHUNK_LOG2) for sd in seeds]
+    pool = mp.get_context("spawn").Pool(min(len(specs), max(1, host_cores() - 2)))
+    truth_async = [pool.apply_async(_truth, (sp,)) for sp in specs]
+
+    import torch
+
+    import paper_2203_14927_b300 as gz
+    from paper_2203_14927_b300 import autotune
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cfg = dict(autotune.DEFAULT)
+    if args.cfg:
+        cfg.update(json.loads(args.cfg))
+    rows = []
+    for sd, sp in zip(seeds, specs):
+        U, Vv, tot = generate_on_device(sp, torch, gz)
+        g = gz.Graph(sp.V, seed=sd, **cfg)
+        g.edge_update(U[:tot], Vv[:tot])
+        t0 = time.perf_counter()
+        labels, ncc, st = g.connected_components()
+        qms = (time.perf_counter() - t0) * 1000.0
+        g.close()
+        del U, Vv
+        rows.append({"seed": sd, "updates": tot, "components": ncc, "rounds": st["rounds"],
+                     "fails_last": st["fails_last"], "fails_total": st["fails_total"],
+                     "exhausted": st["exhausted"], "query_ms": qms, "labels": labels})
+        log(f"[failures] seed {sd}: {tot} updates, {ncc} components, rounds {st['rounds']}, "
+            f"FAIL results {st['fails_total']}")
+    wrong = 0
+    for r, fut in zip(rows, truth_async):
+        want = fut.get()
+        r["correct"] = bool(np.array_equal(r.pop("labels"), want))
+        r["true_components"] = int(len(np.unique(want)))
+        wrong += not r["correct"]
+    pool.close()
+    out = {
+        "metric": "sketch_failure_rate", "value": wrong / len(rows), "unit": "wrong queries / queries",
+        "n_gpus": 1, "steps": len(rows), "warmup": 0, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic: seeded Kronecker streams generated on device",
+        "config": {"workload": f"{args.fail_workload}: {desc}", "seeds": seeds,
+                   "truth": "exact components of the net graph (oracle, hub-core shortcut checked against "
+                            "union-find in tests)"},
+        "fail_results_total": sum(r["fails_total"] for r in rows),
+        "queries_with_fail_in_last_round": sum(1 for r in rows if r["fails_last"]),
+        "per_seed": rows,
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="kron17")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve", "failures"], default="kron17")
+    ap.add_argument("--seeds", type=int, default=20)
+    ap.add_argument("--fail-workload", choices=sorted(WORKLOADS), default="kron17")
+    ap.add_argument("--serve-graphs", type=int, default=64)
+    ap.add_argument("--serve-budget-gb", type=float, default=24.0)
+    ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--kernel", choices=["batched", "plain"], default="batched")
     ap.add_argument("--queries", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -451,7 +677,13 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
+        if args.workload in ("serve", "failures"):
+            args.workload = "kron17"
         run_reference(args, rank, world)
+    elif args.workload == "serve":
+        run_serve(args, rank, world)
+    elif args.workload == "failures":
+        run_failures(args, rank, world)
     else:
         run_ours(args, rank, world)
 

@@ -64,7 +64,9 @@ typedef struct {
     uint32_t ctas_per_sm;   /* resident CTAs per SM of the persistent batched kernel (default: max) */
     uint32_t small_segment; /* node segments shorter than this skip shared-memory staging (default 4) */
     uint32_t smem_mode;     /* delta update in shared memory: 0 load-xor-store, 1 shared atomics */
-    uint32_t reserved[5];
+    uint32_t no_graph;      /* 1: launch a chunk's kernels one by one instead of replaying the
+                               CUDA graph captured for the handle (default 0: graph) */
+    uint32_t reserved[4];
 } gz_config;
 
 /* Statistics of the last query. */
@@ -190,6 +192,88 @@ gz_status gz_profile_enable(gz_handle *h, int enable);
 /* Synchronise and read the totals of the current window. */
 gz_status gz_profile_read(gz_handle *h, gz_profile *out);
 
+/* ------------------------------------------------------------------ serving
+ * Many independent graphs on one GPU.  The paper serves one graph and lets a
+ * query wait for the buffered updates before it (Section 6.6, "Connectivity
+ * Queries are Fast"); a server holds many graphs' node sketches resident and
+ * keeps the GPU busy across them:
+ *   - admission by memory: a graph takes device memory (its sketches and
+ *     scratch, gz_memory_bytes plus query scratch) when its first request is
+ *     served, and only while the running total stays within hbm_budget;
+ *     otherwise it waits; a closed graph gives its memory back when its last
+ *     request is done;
+ *   - continuous batching: `slots` workers, each a host thread with its own
+ *     CUDA stream, repeatedly take the resident (or admissible) graph whose
+ *     oldest pending request is oldest and serve its pending requests in
+ *     order; requests that arrive while others run join the queue and are
+ *     picked up as soon as a slot and memory free up, and the work of
+ *     different graphs overlaps on the device;
+ *   - a graph is served by one worker at a time, so each graph sees its
+ *     requests in submission order and gets exactly the result it would get
+ *     alone.
+ * Times are host-clock milliseconds since the server started. */
+typedef struct gz_server gz_server;
+
+typedef struct {
+    uint64_t hbm_budget; /* device bytes the server may hold for graphs (0 = 80% of free memory) */
+    uint32_t slots;      /* worker threads / CUDA streams (0 = 4) */
+    uint32_t max_batch;  /* most requests one worker takes from a graph at a time (0 = 64) */
+    uint32_t reserved[6];
+} gz_server_config;
+
+typedef struct {
+    uint64_t req_id;
+    uint32_t graph;
+    uint32_t kind;         /* 0 update batch, 1 connected-components query */
+    int32_t status;        /* gz_status of the request */
+    uint32_t n_components; /* queries: number of components */
+    uint64_t n_updates;    /* update batches: updates applied */
+    double submit_ms, start_ms, done_ms;
+} gz_completion;
+
+typedef struct {
+    uint64_t resident_bytes, peak_resident_bytes, budget_bytes;
+    uint32_t graphs, resident_graphs, waiting_graphs, pending_requests;
+    uint64_t completed_requests;
+} gz_server_stats;
+
+/* Start a server on the current device (cfg may be NULL). */
+gz_status gz_server_create(const gz_server_config *cfg, gz_server **out);
+
+/* Finish every accepted request, then stop the workers and free everything. */
+gz_status gz_server_destroy(gz_server *s);
+
+/* Register a graph (no device memory is taken yet).  cfg may be NULL. */
+gz_status gz_server_add_graph(gz_server *s, uint32_t V, uint64_t seed, const gz_config *cfg,
+                              uint32_t *graph);
+
+/* Queue an update batch (host arrays, copied by the call; same meaning as
+ * gz_edge_update).  *req_id identifies its completion. */
+gz_status gz_server_submit_update(gz_server *s, uint32_t graph, const uint32_t *u,
+                                  const uint32_t *v, size_t n, uint64_t *req_id);
+
+/* Queue a connected-components query; labels (host, V entries, or NULL) is
+ * written before the completion is reported and must stay valid until then. */
+gz_status gz_server_submit_query(gz_server *s, uint32_t graph, uint32_t *labels,
+                                 uint64_t *req_id);
+
+/* No more requests for this graph: its memory is released once its queue is
+ * empty. */
+gz_status gz_server_close_graph(gz_server *s, uint32_t graph);
+
+/* Move up to max completions into out (oldest first); waits up to wait_ms
+ * milliseconds for the first one (0 = do not wait). */
+gz_status gz_server_poll(gz_server *s, gz_completion *out, size_t max, size_t *n, int wait_ms);
+
+/* Wait until every submitted request has completed. */
+gz_status gz_server_drain(gz_server *s);
+
+gz_status gz_server_stats_read(gz_server *s, gz_server_stats *out);
+
+/* Reason of the most recent failed request ("" if none); valid until the next
+ * call of this function by the same thread. */
+const char *gz_server_last_error(gz_server *s);
+
 /* Allocation-free ingestion (the paper has no counterpart: this serves
  * callers that cannot allocate device memory).  Code running while a stream is
  * captured into a CUDA graph cannot call cudaMalloc without breaking the
@@ -223,7 +307,8 @@ gz_status gz_sketch_update_noalloc(void *sketch, uint32_t V, uint64_t seed,
                                    const uint32_t *u, const uint32_t *v, size_t n,
                                    uint32_t *status, void *stream);
 
-/* Human-readable reason of the last non-OK status (never NULL). */
+/* Human-readable reason of the last non-OK status of h (never NULL); with
+ * h == NULL, the reason the calling thread's last gz_create failed. */
 const char *gz_last_error(gz_handle *h);
 
 /* Library version string. */

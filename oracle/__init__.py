@@ -51,6 +51,10 @@ def lib():
         L.gzo_splitmix64_at.argtypes = [u64, u64]
         L.gzo_fmix64.restype = u64
         L.gzo_fmix64.argtypes = [u64]
+        L.gzo_fmix32.restype = u32
+        L.gzo_fmix32.argtypes = [u32]
+        L.gzo_fold.restype = u32
+        L.gzo_fold.argtypes = [u64]
         L.gzo_h1.restype = u64
         L.gzo_h1.argtypes = [u64, u64, u64]
         L.gzo_h2.restype = u32
@@ -103,6 +107,14 @@ def splitmix64_at(seed: int, n: int) -> int:
 
 def fmix64(x: int) -> int:
     return int(lib().gzo_fmix64(x))
+
+
+def fmix32(x: int) -> int:
+    return int(lib().gzo_fmix32(x))
+
+
+def fold(x: int) -> int:
+    return int(lib().gzo_fold(x))
 
 
 def h1(a: int, b: int, x: int) -> int:

@@ -28,8 +28,10 @@
  *              family of Dietzfelbinger (STACS 1996); bit i of h1 is bit 63-i
  *              of the product, so "h1(x) = 0 mod 2^i" tests the TOP i bits.
  *              Bit order of col_hash in Fig. cube_code: bit 0 first.
- *   h2         h2(x) = high 32 bits of fmix64(x XOR c), fmix64 being the
- *              64-bit finalizer of MurmurHash3 (Appleby, 2011).
+ *   h2         h2(x) = fmix32(fold(x) XOR lo32(c)), fmix32 being the 32-bit
+ *              finalizer of MurmurHash3 (Appleby, 2011) and
+ *              fold(x) = lo32(x) XOR lo32(hi32(x) * 0x9E3779B9), the identity
+ *              for x < 2^32.
  *   rows       the update loop of Fig. cube_code also stops at row R.
  *   query      Fig. cube_code's scan (columns ascending, rows ascending); a
  *              bucket is taken when gamma == h2(alpha) AND alpha decodes to
@@ -70,6 +72,24 @@ uint64_t gzo_fmix64(uint64_t x)
     return x;
 }
 
+/* MurmurHash3's 32-bit finalizer (Appleby 2011). */
+uint32_t gzo_fmix32(uint32_t h)
+{
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+/* 32-bit fold of an edge index: lo32(x) ^ lo32(hi32(x) * 0x9E3779B9). */
+uint32_t gzo_fold(uint64_t x)
+{
+    uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
+    return lo ^ (uint32_t)(hi * 0x9E3779B9u);
+}
+
 static uint64_t bitreverse64(uint64_t x)
 {
     uint64_t r = 0;
@@ -86,10 +106,10 @@ uint64_t gzo_h1(uint64_t a, uint64_t b, uint64_t x)
     return bitreverse64(a * x + b);
 }
 
-/* checksum of Fig. cube_code: h2(x) = hi32(fmix64(x ^ c)). */
+/* checksum of Fig. cube_code: h2(x) = fmix32(fold(x) ^ lo32(c)). */
 uint32_t gzo_h2(uint64_t c, uint64_t x)
 {
-    return (uint32_t)(gzo_fmix64(x ^ c) >> 32);
+    return gzo_fmix32(gzo_fold(x) ^ (uint32_t)c);
 }
 
 /* ---------------------------------------------------------------- geometry */

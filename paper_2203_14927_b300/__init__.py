@@ -43,7 +43,8 @@ class Config(ctypes.Structure):
         ("ctas_per_sm", ctypes.c_uint32),
         ("small_segment", ctypes.c_uint32),
         ("smem_mode", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 5),
+        ("no_graph", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 4),
     ]
 
 
@@ -123,6 +124,20 @@ _SIGNATURES = {
     "gz_gen_kron_chunk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_uint64, ctypes.c_void_p]),
     "gz_gen_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "gz_server_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gz_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "gz_server_add_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
+    "gz_server_submit_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "gz_server_submit_query": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
+                                              ctypes.c_void_p]),
+    "gz_server_close_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    "gz_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                      ctypes.c_int]),
+    "gz_server_drain": (ctypes.c_int, [ctypes.c_void_p]),
+    "gz_server_stats_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gz_server_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "gz_sketch_update_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                                 ctypes.c_void_p, ctypes.c_void_p]),
@@ -186,7 +201,7 @@ class Graph:
 
     def __init__(self, V: int, seed: int = 0, *, kernel: str = "batched", chunk_log2: int = 0,
                  smem_rows: int = 0, tile_records: int = 0, ctas_per_sm: int = 0,
-                 small_segment: int = 0, smem_mode: int = 0, stream=None):
+                 small_segment: int = 0, smem_mode: int = 0, no_graph: int = 0, stream=None):
         cfg = Config()
         cfg.chunk_log2 = chunk_log2
         cfg.kernel = KERNELS[kernel]
@@ -195,12 +210,13 @@ class Graph:
         cfg.ctas_per_sm = ctas_per_sm
         cfg.small_segment = small_segment
         cfg.smem_mode = smem_mode
+        cfg.no_graph = no_graph
         self._h = ctypes.c_void_p()
         s = _current_stream() if stream is None else stream
         st = lib().gz_create(V, seed & ((1 << 64) - 1), ctypes.byref(cfg), ctypes.c_void_p(s),
                              ctypes.byref(self._h))
         if st != GZ_OK:
-            raise GzError(st, f"gz_create(V={V}) failed")
+            raise GzError(st, f"gz_create(V={V}) failed: {lib().gz_last_error(None).decode()}")
         self.V = V
         self.seed = seed
         self.K, self.R = geometry(V)
@@ -357,6 +373,108 @@ class DeviceKronStream:
         if getattr(self, "_g", None) and self._g.value:
             lib().gz_gen_destroy(self._g)
             self._g = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("slots", ctypes.c_uint32), ("max_batch", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 6)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("req_id", ctypes.c_uint64), ("graph", ctypes.c_uint32), ("kind", ctypes.c_uint32),
+                ("status", ctypes.c_int32), ("n_components", ctypes.c_uint32), ("n_updates", ctypes.c_uint64),
+                ("submit_ms", ctypes.c_double), ("start_ms", ctypes.c_double), ("done_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("resident_bytes", ctypes.c_uint64), ("peak_resident_bytes", ctypes.c_uint64),
+                ("budget_bytes", ctypes.c_uint64), ("graphs", ctypes.c_uint32),
+                ("resident_graphs", ctypes.c_uint32), ("waiting_graphs", ctypes.c_uint32),
+                ("pending_requests", ctypes.c_uint32), ("completed_requests", ctypes.c_uint64)]
+
+
+class Server:
+    """Many graphs resident on the current device (gz_server_* in include/gz.h):
+    admission by an HBM budget, `slots` concurrent workers (streams)."""
+
+    def __init__(self, hbm_budget: int = 0, slots: int = 0, max_batch: int = 0):
+        cfg = ServerConfig()
+        cfg.hbm_budget, cfg.slots, cfg.max_batch = hbm_budget, slots, max_batch
+        self._s = ctypes.c_void_p()
+        st = lib().gz_server_create(ctypes.byref(cfg), ctypes.byref(self._s))
+        if st != GZ_OK:
+            raise GzError(st, "gz_server_create failed")
+        self._labels = {}
+        self._V = {}
+
+    def add_graph(self, V: int, seed: int = 0, **cfg) -> int:
+        c = Config()
+        for k, val in cfg.items():
+            setattr(c, k, KERNELS[val] if k == "kernel" else val)
+        gid = ctypes.c_uint32()
+        st = lib().gz_server_add_graph(self._s, V, seed & ((1 << 64) - 1), ctypes.byref(c), ctypes.byref(gid))
+        if st != GZ_OK:
+            raise GzError(st, f"gz_server_add_graph(V={V}) failed")
+        self._V[gid.value] = V
+        return gid.value
+
+    def submit_update(self, graph: int, u, v) -> int:
+        u = np.ascontiguousarray(u, np.uint32)
+        v = np.ascontiguousarray(v, np.uint32)
+        rid = ctypes.c_uint64()
+        st = lib().gz_server_submit_update(self._s, graph, u.ctypes.data_as(ctypes.c_void_p),
+                                           v.ctypes.data_as(ctypes.c_void_p), len(u), ctypes.byref(rid))
+        if st != GZ_OK:
+            raise GzError(st, "gz_server_submit_update failed")
+        return rid.value
+
+    def submit_query(self, graph: int) -> int:
+        labels = np.zeros(self._V[graph], np.uint32)
+        rid = ctypes.c_uint64()
+        st = lib().gz_server_submit_query(self._s, graph, labels.ctypes.data_as(ctypes.c_void_p),
+                                          ctypes.byref(rid))
+        if st != GZ_OK:
+            raise GzError(st, "gz_server_submit_query failed")
+        self._labels[rid.value] = labels
+        return rid.value
+
+    def close_graph(self, graph: int):
+        lib().gz_server_close_graph(self._s, graph)
+
+    def poll(self, max_n: int = 4096, wait_ms: int = 0) -> list:
+        buf = (Completion * max_n)()
+        n = ctypes.c_size_t()
+        lib().gz_server_poll(self._s, buf, max_n, ctypes.byref(n), wait_ms)
+        out = []
+        for i in range(n.value):
+            c = buf[i]
+            d = {f: getattr(c, f) for f, _ in Completion._fields_}
+            if c.kind == 1:
+                d["labels"] = self._labels.pop(c.req_id, None)
+            out.append(d)
+        return out
+
+    def drain(self):
+        lib().gz_server_drain(self._s)
+
+    def last_error(self) -> str:
+        return lib().gz_server_last_error(self._s).decode()
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        lib().gz_server_stats_read(self._s, ctypes.byref(st))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_s", None) and self._s.value:
+            lib().gz_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
 
     def __del__(self):
         try:

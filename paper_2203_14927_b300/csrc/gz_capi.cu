@@ -65,8 +65,11 @@ extern "C" {
 
 const char* gz_version(void) { return "gz-b300 0.1 (sm_103a)"; }
 
+// reason of the calling thread's last failed gz_create (no handle exists then)
+static thread_local std::string g_create_err = "no failed gz_create on this thread";
+
 const char* gz_last_error(gz_handle* h) {
-    if (!h) return "null handle";
+    if (!h) return g_create_err.c_str();
     return h->err.c_str();
 }
 
@@ -128,25 +131,35 @@ gz_status gz_create(uint32_t V, uint64_t seed, const gz_config* cfg, void* strea
         hk[ncol + col] = splitmix_nth(seed, 3 * col + 1);
         hk[2 * ncol + col] = splitmix_nth(seed, 3 * col + 2);
     }
+    // Stream-ordered allocations: creating or destroying a handle never
+    // synchronises the whole device (cudaFree would), so a server can admit
+    // and release graphs while other graphs' work runs.
     const size_t sk = (size_t)V * h->node_bytes;
-    e = cudaMalloc(&h->d_sketch, sk);
+    cudaStream_t as = h->stream;
+    e = cudaMallocAsync(&h->d_sketch, sk, as);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_sketch, 0, sk, h->stream);
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_keys, 3 * ncol * sizeof(uint64_t));
-    if (e == cudaSuccess) e = cudaMemcpy(h->d_keys, hk, 3 * ncol * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMallocAsync(&h->d_keys, 3 * ncol * sizeof(uint64_t), as);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->d_keys, hk, 3 * ncol * sizeof(uint64_t), cudaMemcpyHostToDevice, as);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(as);  // hk is freed below
     delete[] hk;
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_counts, (size_t)(V + 1) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_offsets, (size_t)(V + 1) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_cursor, (size_t)(V + 1) * 4);
+    if (e == cudaSuccess) e = cudaMallocAsync(&h->d_counts, (size_t)(V + 1) * 4, as);
+    if (e == cudaSuccess) e = cudaMallocAsync(&h->d_offsets, (size_t)(V + 1) * 4, as);
+    if (e == cudaSuccess) e = cudaMallocAsync(&h->d_cursor, (size_t)(V + 1) * 4, as);
     if (e == cudaSuccess && h->cfg.kernel == GZ_KERNEL_BATCHED)
-        e = cudaMalloc(&h->d_records, (size_t)2 * h->chunk * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_flags, 16);
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_scan_tmp, ((size_t)(V + 1) / 1024 + 2) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_stats, 2 * sizeof(uint64_t));
+        e = cudaMallocAsync(&h->d_records, (size_t)2 * h->chunk * 4, as);
+    if (e == cudaSuccess) e = cudaMallocAsync(&h->d_flags, 16, as);
+    if (e == cudaSuccess) e = cudaMallocAsync(&h->d_scan_tmp, ((size_t)(V + 1) / 1024 + 2) * 4, as);
+    if (e == cudaSuccess) e = cudaMallocAsync(&h->d_stats, 2 * sizeof(uint64_t), as);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_stats, 0, 2 * sizeof(uint64_t), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, 16, h->stream);
     s = cuda_check(h, e, "gz_create allocation");
     if (s == GZ_OK) s = ingest_setup(h);
+    // allocations are stream-ordered: complete them before the handle is
+    // used from any other stream
+    if (s == GZ_OK) s = cuda_check(h, cudaStreamSynchronize(h->stream), "gz_create sync");
     if (s != GZ_OK) {
+        g_create_err = h->err;
         gz_destroy(h);
         return s;
     }
@@ -164,14 +177,18 @@ gz_status gz_destroy(gz_handle* h) {
                     h->q_M, h->q_M2, h->q_flag, h->q_pos, h->q_forest, h->q_ctr, h->q_res,
                     h->q_partial, h->q_trace, h->d_stats, h->d_scan_tmp, h->d_tile_node};
     for (void* p : ptrs)
-        if (p) cudaFree(p);
-    if (h->h_ctr) cudaFreeHost(h->h_ctr);
+        if (p) cudaFreeAsync(p, h->stream);
+    delete[] h->h_ctr;
     for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
     for (int b = 0; b < 2; ++b) {
         if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);
         if (h->ev_free[b]) cudaEventDestroy(h->ev_free[b]);
     }
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    for (int i = 0; i < 3; ++i)
+        if (h->cap_ev[i]) cudaEventDestroy(h->cap_ev[i]);
     delete h;
     return GZ_OK;
 }
@@ -184,7 +201,8 @@ gz_status gz_set_stream(gz_handle* h, void* stream) {
 
 static gz_status host_path_setup(gz_handle* h) {
     if (h->d_stage) return GZ_OK;
-    cudaError_t e = cudaMalloc(&h->d_stage, (size_t)4 * h->chunk * 4);
+    cudaError_t e = cudaMallocAsync(&h->d_stage, (size_t)4 * h->chunk * 4, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // the copy stream uses it
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
         e = cudaEventCreateWithFlags(&h->ev_copied[b], cudaEventDisableTiming);
@@ -299,8 +317,8 @@ gz_status gz_export_sketch(gz_handle* h, uint32_t node_lo, uint32_t node_hi, uin
     uint64_t* da = alpha;
     uint32_t* dg = gamma;
     if (!on_device) {
-        cudaError_t e = cudaMalloc(&da, n * 8);
-        if (e == cudaSuccess) e = cudaMalloc(&dg, n * 4);
+        cudaError_t e = cudaMallocAsync(&da, n * 8, h->stream);
+        if (e == cudaSuccess) e = cudaMallocAsync(&dg, n * 4, h->stream);
         if (e != cudaSuccess) return cuda_check(h, e, "export scratch");
     }
     s = export_nested(h, node_lo, node_hi, da, dg);
@@ -311,8 +329,8 @@ gz_status gz_export_sketch(gz_handle* h, uint32_t node_lo, uint32_t node_hi, uin
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (!on_device) {
-        cudaFree(da);
-        cudaFree(dg);
+        cudaFreeAsync(da, h->stream);
+        cudaFreeAsync(dg, h->stream);
     }
     if (s != GZ_OK) return s;
     return cuda_check(h, e, "export");

@@ -57,6 +57,14 @@ struct gz_handle {
     bool trace = false;
     bool trace_valid = false;
 
+    // per-chunk ingest pipeline captured once as a CUDA graph
+    bool graph_ready = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaGraphNode_t node_validate = nullptr, node_scatter = nullptr;
+    cudaGraphNode_t node_ev[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t cap_ev[3] = {nullptr, nullptr, nullptr};
+
     // profiling window (gz_profile_enable / gz_profile_read)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;  // triples: before partition, before update, after update

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "gz_handle.cuh"
 #include "gz_internal.cuh"
@@ -180,20 +181,13 @@ __global__ void k_tile_nodes(const uint32_t* __restrict__ offsets, uint32_t V, u
     }
 }
 
-// The two hashes of one column written on 32-bit words, with every part that
-// depends only on the column's keys folded into per-thread constants.  They
-// compute exactly `depth_word` and `checksum` of gz_internal.cuh.
-namespace fm {
-constexpr uint32_t C1_LO = 0xED558CCDu, C1_HI = 0xFF51AFD7u;  // MurmurHash3 fmix64 multipliers
-constexpr uint32_t C2_LO = 0x1A85EC53u, C2_HI = 0xC4CEB9FEu;
-}  // namespace fm
-
+// The two hashes of one column on 32-bit words, with the key parts held in
+// registers.  They compute exactly `depth_word` and `checksum` of
+// gz_internal.cuh.
 struct ColKey {
     uint32_t a_lo, a_hi;
     uint64_t b;
-    uint32_t kfold;  // c_lo ^ (c_hi >> 1): the key's share of the first xor-shift
-    uint32_t c_hi;
-    uint32_t k2;     // c_hi * C1_LO: the key's share of the first product when idx < 2^32
+    uint32_t c_lo;  // checksum key
 };
 
 __device__ __forceinline__ ColKey make_colkey(uint64_t a, uint64_t b, uint64_t c) {
@@ -201,10 +195,7 @@ __device__ __forceinline__ ColKey make_colkey(uint64_t a, uint64_t b, uint64_t c
     k.a_lo = (uint32_t)a;
     k.a_hi = (uint32_t)(a >> 32);
     k.b = b;
-    const uint32_t c_lo = (uint32_t)c, c_hi = (uint32_t)(c >> 32);
-    k.kfold = c_lo ^ (c_hi >> 1);
-    k.c_hi = c_hi;
-    k.k2 = c_hi * fm::C1_LO;
+    k.c_lo = (uint32_t)c;
     return k;
 }
 
@@ -217,51 +208,57 @@ __device__ __forceinline__ uint32_t depth_hi(const ColKey& k, uint32_t x_lo, uin
     return hi;
 }
 
-// hi32(fmix64(idx ^ c)); fold = idx_lo ^ (idx_hi >> 1), precomputed per record
-template <bool kWide>
-__device__ __forceinline__ uint32_t checksum_w(const ColKey& k, uint32_t x_hi, uint32_t fold) {
-    const uint32_t lo1 = fold ^ k.kfold;  // low word after x ^= c; x ^= x >> 33
-    uint32_t lo2, hi2;
-    if (kWide) {
-        const uint32_t hi1 = x_hi ^ k.c_hi;
-        const uint64_t q = (uint64_t)lo1 * fm::C1_LO;
-        lo2 = (uint32_t)q;
-        hi2 = (uint32_t)(q >> 32) + lo1 * fm::C1_HI + hi1 * fm::C1_LO;
-    } else {
-        const uint64_t q = (uint64_t)lo1 * fm::C1_LO + ((uint64_t)k.k2 << 32);
-        lo2 = (uint32_t)q;
-        hi2 = (uint32_t)(q >> 32) + lo1 * fm::C1_HI;
-    }
-    const uint32_t lo3 = lo2 ^ (hi2 >> 1);
-    return __umulhi(lo3, fm::C2_LO) + lo3 * fm::C2_HI + hi2 * fm::C2_LO;
+// checksum of a staged record; fold = fold32(idx), computed once per record
+__device__ __forceinline__ uint32_t checksum_w(const ColKey& k, uint32_t fold) {
+    return fmix32(fold ^ k.c_lo);
+}
+
+// cp.async (16-byte granules, L2 only): global -> shared without a register
+// round trip; bytes past src_bytes are zero-filled and not read.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, uint32_t src_bytes) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 // One CTA = 32*ceil(7K/32) threads; thread c owns CubeSketch column c = 7k + j
 // (one "Graph Worker" per column; no two threads write one bucket).
 // Dynamic shared memory:
-//   delta alpha  [Rs][CP] u64 (kAtomic: two u32 planes lo[Rs][CP], hi[Rs][CP])
-//   delta gamma  [Rs][CP] u32
-//   staged records [tile] (kWide: uint4 {idx_lo, idx_hi, fold, 0}; else u32 idx)
+//   delta planes: kAtomic: alpha lo, alpha hi, gamma (u32 each, RC = Rs*CP
+//                 slots); else alpha (u64) and gamma (u32).  Slot of (row d,
+//                 column c) = (c/32)*Rs*32 + d*32 + c%32: a warp's 32 lanes
+//                 hit 32 distinct banks whatever rows they update, and a row
+//                 step is a shift, not a multiply.
+//   raw records  [2][tile] u32, filled by cp.async one tile ahead
+//   staged records [tile] (kWide: uint4 {idx_lo, idx_hi, fold32(idx), 0}; else u32 idx)
 //   per-k deepest touched row [K] u32
-// With the [row][column] layout the 32 lanes of a warp hit 32 distinct banks
-// whatever rows their updates land in.  kAtomic uses shared-memory atomics for
-// the XORs, so an update never waits on a shared-memory load.
+// Tiles (equal record counts) are claimed from an atomic counter one tile
+// ahead, so the next tile's records and first node are fetched while the
+// current tile is being hashed.
 template <bool kAtomic, bool kWide>
 __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
     extern __shared__ __align__(16) uint64_t smem[];
     if (p.flags[0]) return;
     const uint32_t CP = blockDim.x, c = threadIdx.x;
-    const uint32_t Rs = p.Rs, R = p.R, RC = Rs * CP;
+    const uint32_t Rs = p.Rs, R = p.R, RC = Rs * CP, T = p.tile;
     uint64_t* dA = smem;                                 // kAtomic == false
     uint32_t* dAlo = reinterpret_cast<uint32_t*>(smem);  // kAtomic == true
     uint32_t* dAhi = dAlo + RC;
     uint32_t* dG = reinterpret_cast<uint32_t*>(smem + RC);
-    uint32_t* stage = dG + RC;  // 16-byte aligned: RC*12 bytes, RC a multiple of 32
+    uint32_t* raw = dG + RC;  // [2][T], 16-byte aligned (RC multiple of 32, T multiple of 4)
+    uint32_t* stage = raw + 2 * T;
     uint4* stage4 = reinterpret_cast<uint4*>(stage);
-    uint32_t* maxd = stage + (kWide ? 4u : 1u) * p.tile;
+    uint32_t* maxd = stage + (kWide ? 4u : 1u) * T;
 
     const bool active = c < p.ncol;
     const uint32_t k = c / GZ_COLS, j = c - k * GZ_COLS;
+    // slot of (row 0, column c); row d adds d*32
+    const uint32_t cbase = (c >> 5) * Rs * 32 + (c & 31);
     ColKey key{};
     if (active) key = make_colkey(p.keys.a[c], p.keys.b[c], p.keys.c[c]);
     for (uint32_t i = c; i < RC; i += CP) {
@@ -275,28 +272,63 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
     }
     for (uint32_t i = c; i < p.K; i += CP) maxd[i] = 0;
     const uint32_t total = p.offsets[p.V];
-    const uint32_t ntiles = (total + p.tile - 1) / p.tile;
+    const uint32_t ntiles = (total + T - 1) / T;
     unsigned long long n_rows = 0, n_deep = 0;
-    __shared__ uint32_t s_t[2];
-    if (c == 0) s_t[0] = atomicAdd(p.work, 1u);
 
+    // records of tile t -> raw[buf]: 16-byte granules, the tail zero-filled
+    auto fetch = [&](uint32_t t, uint32_t buf) {
+        const uint32_t lo = t * T;
+        const uint32_t bytes = (min(lo + T, total) - lo) * 4u;
+        for (uint32_t q = c; q * 16 < T * 4; q += CP) {
+            const uint32_t off = q * 16;
+            const uint32_t n = off < bytes ? min(16u, bytes - off) : 0u;
+            cp_async16(raw + buf * T + q * 4, p.records + lo + (n ? q * 4 : 0), n);
+        }
+        cp_async_commit();
+    };
+
+    // Dynamic tiles with a lookahead of one: while tile t is processed, the
+    // records of the next tile (already claimed) stream in with cp.async and
+    // thread 0 claims the tile after that; its index is stored at the end of
+    // the tile, so the atomic's latency hides behind the tile's work.
+    __shared__ uint32_t s_t[3];
+    if (c == 0) {
+        s_t[0] = atomicAdd(p.work, 1u);
+        s_t[1] = atomicAdd(p.work, 1u);
+    }
+    __syncthreads();
+    uint32_t x_next = 0;
+    if (s_t[0] < ntiles) {
+        fetch(s_t[0], 0);
+        x_next = p.tile_node[s_t[0]];
+    }
     for (uint32_t it = 0;; ++it) {
-        __syncthreads();
-        const uint32_t t = s_t[it & 1];
+        const uint32_t t = s_t[it % 3];
         if (t >= ntiles) break;
-        // claim the next tile now; its index is read after the next barrier
-        if (c == 0) s_t[(it + 1) & 1] = atomicAdd(p.work, 1u);
-        const uint32_t lo = t * p.tile, hi = min(lo + p.tile, total);
-        uint32_t x = p.tile_node[t], pos = lo;
+        const uint32_t buf = it & 1;
+        const uint32_t x_first = x_next;
+        const uint32_t tn = s_t[(it + 1) % 3];
+        uint32_t claimed = 0;
+        if (c == 0) claimed = atomicAdd(p.work, 1u);
+        if (tn < ntiles) {
+            fetch(tn, buf ^ 1);
+            x_next = p.tile_node[tn];
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();  // raw[buf] complete and visible
+        const uint32_t* rb = raw + buf * T;
+        const uint32_t lo = t * T, hi = min(lo + T, total);
+        uint32_t x = x_first, pos = lo;
         while (pos < hi) {
             const uint32_t seg_end = min(p.offsets[x + 1], hi);
             const uint32_t nseg = seg_end - pos;
             if (nseg > 0) {
                 for (uint32_t i = c; i < nseg; i += CP) {
-                    const uint64_t idx = edge_index(x, p.records[pos + i], p.V);
+                    const uint64_t idx = edge_index(x, rb[pos - lo + i], p.V);
                     if (kWide) {
-                        const uint32_t ilo = (uint32_t)idx, ihi = (uint32_t)(idx >> 32);
-                        stage4[i] = make_uint4(ilo, ihi, ilo ^ (ihi >> 1), 0u);
+                        stage4[i] = make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), fold32(idx), 0u);
                     } else {
                         stage[i] = (uint32_t)idx;
                     }
@@ -319,7 +351,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                     if (active) {
                         // one column update staged in shared memory (d < Rs)
                         auto put = [&](uint32_t d, uint32_t xlo, uint32_t xhi, uint32_t g) {
-                            const uint32_t slot = d * CP + c;
+                            const uint32_t slot = cbase + (d << 5);
                             if (kAtomic) {
                                 atomicXor(dAlo + slot, xlo);
                                 if (kWide) atomicXor(dAhi + slot, xhi);
@@ -367,7 +399,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
 #pragma unroll
                             for (int r = 0; r < 4; ++r) {
                                 d[r] = __clz(depth_hi<kWide>(key, xlo[r], xhi[r]));
-                                g[r] = checksum_w<kWide>(key, xhi[r], fold[r]);
+                                g[r] = checksum_w(key, fold[r]);
                             }
                             const uint32_t dmax = max(max(d[0], d[1]), max(d[2], d[3]));
                             if (dmax < Rs) {
@@ -399,7 +431,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                                 fold = xlo;
                             }
                             const uint32_t d = __clz(depth_hi<kWide>(key, xlo, xhi));
-                            const uint32_t g = checksum_w<kWide>(key, xhi, fold);
+                            const uint32_t g = checksum_w(key, fold);
                             if (d < Rs) {
                                 put(d, xlo, xhi, g);
                                 md = max(md, d);
@@ -407,7 +439,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                                 deep(xlo, xhi, g);
                             }
                         }
-                    atomicMax(&maxd[k], md);
+                        atomicMax(&maxd[k], md);
                     }
                     __syncthreads();
                     const uint32_t per_k = Rs * GZ_COLS;
@@ -415,7 +447,8 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                         const uint32_t kk = q / per_k, rem = q - kk * per_k;
                         const uint32_t row = rem / GZ_COLS, jj = rem - row * GZ_COLS;
                         if (row <= maxd[kk]) {
-                            const uint32_t slot = row * CP + kk * GZ_COLS + jj;
+                            const uint32_t col = kk * GZ_COLS + jj;
+                            const uint32_t slot = (col >> 5) * Rs * 32 + (row << 5) + (col & 31);
                             uint64_t a;
                             if (kAtomic) {
                                 a = ((uint64_t)dAhi[slot] << 32) | dAlo[slot];
@@ -448,7 +481,10 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
             pos = seg_end;
             ++x;
         }
+        if (c == 0) s_t[(it + 2) % 3] = claimed;
+        __syncthreads();
     }
+    cp_async_wait<0>();
     if (n_rows) atomicAdd(&p.stats[0], n_rows);
     if (n_deep) atomicAdd(&p.stats[1], n_deep);
 }
@@ -458,6 +494,23 @@ using BatchedFn = void (*)(BatchedArgs);
 static BatchedFn batched_fn(uint32_t mode, bool wide) {
     if (mode) return wide ? k_batched<true, true> : k_batched<true, false>;
     return wide ? k_batched<false, true> : k_batched<false, false>;
+}
+
+// Raise the dynamic shared-memory cap of every batched-kernel variant to the
+// device's opt-in maximum (idempotent; safe to call from any thread).
+static cudaError_t set_smem_cap(int device) {
+    int cap = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    for (int mode = 0; mode < 2 && e == cudaSuccess; ++mode)
+        for (int wide = 0; wide < 2 && e == cudaSuccess; ++wide) {
+            const void* fn = (const void*)batched_fn(mode, wide != 0);
+            cudaFuncAttributes fa;
+            e = cudaFuncGetAttributes(&fa, fn);  // the kernel's static shared memory counts too
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         cap - (int)fa.sharedSizeBytes);
+        }
+    return e;
 }
 
 // ------------------------------------------------------------------ plain update
@@ -537,11 +590,14 @@ gz_status ingest_setup(gz_handle* h) {
     h->tile = h->cfg.tile_records ? h->cfg.tile_records : 512;
     h->small_seg = h->cfg.small_segment ? h->cfg.small_segment : 4;
     const bool wide = (uint64_t)h->V * h->V > (1ull << 32);
-    h->batched_smem = (size_t)rs * h->block * 12 + (size_t)h->tile * (wide ? 16 : 4) + (size_t)h->K * 4;
+    if (h->tile % 4 != 0) return set_error(h, GZ_EINVAL, "tile_records must be a multiple of 4");
+    h->batched_smem = (size_t)rs * h->block * 12 + (size_t)h->tile * (8 + (wide ? 16 : 4)) + (size_t)h->K * 4;
     if (h->cfg.smem_mode > 1) return set_error(h, GZ_EINVAL, "smem_mode must be 0 or 1");
     const void* fn = (const void*)batched_fn(h->cfg.smem_mode, wide);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)h->batched_smem);
+    // The dynamic shared-memory cap is one process-wide setting per kernel, so
+    // every caller sets the same value (the device's opt-in maximum); a
+    // per-handle value would let handles of different sizes break each other.
+    cudaError_t e = set_smem_cap(h->device);
     if (e != cudaSuccess) return cuda_check(h, e, "cudaFuncSetAttribute(k_batched)");
     int nb = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, (int)h->block, h->batched_smem);
@@ -550,58 +606,171 @@ gz_status ingest_setup(gz_handle* h) {
     uint32_t per_sm = h->cfg.ctas_per_sm ? std::min<uint32_t>(h->cfg.ctas_per_sm, nb) : nb;
     h->batched_grid = per_sm * h->sm_count;
     if (h->cfg.kernel == GZ_KERNEL_BATCHED) {
-        e = cudaMalloc(&h->d_tile_node, (size_t)(2 * h->chunk / h->tile + 2) * sizeof(uint32_t));
+        e = cudaMallocAsync(&h->d_tile_node, (size_t)(2 * h->chunk / h->tile + 2) * sizeof(uint32_t),
+                            h->stream);
         if (e != cudaSuccess) return cuda_check(h, e, "tile table allocation");
     }
     return GZ_OK;
 }
 
+static BatchedArgs batched_args(gz_handle* h) {
+    BatchedArgs a;
+    a.s = view_of(h);
+    a.keys = keys_of(h);
+    a.offsets = h->d_offsets;
+    a.records = h->d_records;
+    a.tile_node = h->d_tile_node;
+    a.flags = h->d_flags;
+    a.work = h->d_flags + 1;
+    a.V = h->V;
+    a.K = h->K;
+    a.R = h->R;
+    a.ncol = h->ncol;
+    a.Rs = h->smem_rows;
+    a.tile = h->tile;
+    a.small_seg = h->small_seg;
+    a.stats = reinterpret_cast<unsigned long long*>(h->d_stats);
+    return a;
+}
+
+// The batched pipeline of one chunk on stream st: validation + histogram,
+// scan, scatter, tile table, persistent update.  ev (may hold nulls) are
+// recorded before the partition, before the update and after it.
+static void enqueue_batched(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, uint64_t n,
+                            uint32_t grid, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1, cudaEvent_t ev2,
+                            bool capturing = false) {
+    // under stream capture only an "external" record becomes an event-record node
+    auto record = [&](cudaEvent_t ev) {
+        if (capturing) cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+        else cudaEventRecord(ev, st);
+    };
+    if (ev0) record(ev0);
+    cudaMemsetAsync(h->d_flags, 0, 2 * sizeof(uint32_t), st);  // batch flag + work
+    cudaMemsetAsync(h->d_counts, 0, (size_t)(h->V + 1) * sizeof(uint32_t), st);
+    k_validate_count<<<grid, 256, 0, st>>>(d_u, d_v, n, h->V, h->d_counts, h->d_flags);
+    launch_scan(h->d_counts, h->d_offsets, h->d_cursor, h->V, st, h->d_scan_tmp);
+    k_scatter<<<grid, 256, 0, st>>>(d_u, d_v, n, h->d_cursor, h->d_records, h->d_flags);
+    k_tile_nodes<<<(h->V + 255) / 256, 256, 0, st>>>(h->d_offsets, h->V, h->tile, h->d_flags, h->d_tile_node);
+    if (ev1) record(ev1);
+    const bool wide = (uint64_t)h->V * h->V > (1ull << 32);
+    batched_fn(h->cfg.smem_mode, wide)<<<h->batched_grid, h->block, h->batched_smem, st>>>(batched_args(h));
+    if (ev2) record(ev2);
+}
+
+// Capture the pipeline once on a private stream (thread-local capture mode,
+// so other threads' CUDA calls are unaffected); the input pointers and count
+// are rewritten per launch in the validation and scatter nodes, the three
+// event-record nodes are re-pointed when profiling.
+static gz_status capture_graph(gz_handle* h) {
+    cudaStream_t cap = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->cap_ev[i]);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        if (cap) cudaStreamDestroy(cap);
+        return cuda_check(h, e, "graph capture begin");
+    }
+    enqueue_batched(h, h->d_records, h->d_records, 0, (uint32_t)h->sm_count * 8, cap, h->cap_ev[0], h->cap_ev[1],
+                    h->cap_ev[2], true);
+    e = cudaStreamEndCapture(cap, &h->graph);
+    cudaStreamDestroy(cap);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph_exec, h->graph, 0);
+    if (e != cudaSuccess) return cuda_check(h, e, "graph capture");
+    size_t nn = 0;
+    e = cudaGraphGetNodes(h->graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (e == cudaSuccess) e = cudaGraphGetNodes(h->graph, nodes.data(), &nn);
+    if (e != cudaSuccess) return cuda_check(h, e, "graph nodes");
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess) continue;
+        if (ty == cudaGraphNodeTypeKernel) {
+            cudaKernelNodeParams kp;
+            if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
+            if (kp.func == (void*)k_validate_count) h->node_validate = nd;
+            if (kp.func == (void*)k_scatter) h->node_scatter = nd;
+        } else if (ty == cudaGraphNodeTypeEventRecord) {
+            cudaEvent_t ev;
+            if (cudaGraphEventRecordNodeGetEvent(nd, &ev) != cudaSuccess) continue;
+            for (int i = 0; i < 3; ++i)
+                if (ev == h->cap_ev[i]) h->node_ev[i] = nd;
+        }
+    }
+    if (!h->node_validate || !h->node_scatter || !h->node_ev[0] || !h->node_ev[1] || !h->node_ev[2])
+        return set_error(h, GZ_ECUDA, "captured ingest graph lacks an expected node");
+    h->graph_ready = true;
+    return GZ_OK;
+}
+
+static gz_status launch_graph(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, uint64_t n) {
+    if (!h->graph_ready) {
+        gz_status s = capture_graph(h);
+        if (s != GZ_OK) return s;
+    }
+    cudaKernelNodeParams kp;
+    cudaError_t e = cudaGraphKernelNodeGetParams(h->node_validate, &kp);
+    const uint32_t V = h->V;
+    uint32_t* counts = h->d_counts;
+    uint32_t* flags = h->d_flags;
+    void* va[] = {(void*)&d_u, (void*)&d_v, (void*)&n, (void*)&V, (void*)&counts, (void*)&flags};
+    kp.kernelParams = va;
+    kp.extra = nullptr;
+    if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(h->graph_exec, h->node_validate, &kp);
+    uint32_t* cursor = h->d_cursor;
+    uint32_t* records = h->d_records;
+    void* sa[] = {(void*)&d_u, (void*)&d_v, (void*)&n, (void*)&cursor, (void*)&records, (void*)&flags};
+    cudaKernelNodeParams kq;
+    if (e == cudaSuccess) e = cudaGraphKernelNodeGetParams(h->node_scatter, &kq);
+    kq.kernelParams = sa;
+    kq.extra = nullptr;
+    if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(h->graph_exec, h->node_scatter, &kq);
+    if (e != cudaSuccess) return cuda_check(h, e, "graph parameters");
+    for (int i = 0; i < 3; ++i) {
+        cudaEvent_t ev = h->cap_ev[i];
+        if (h->prof) {
+            if (h->ev_used == h->ev_pool.size()) {
+                cudaEvent_t nev;
+                e = cudaEventCreate(&nev);
+                if (e != cudaSuccess) return cuda_check(h, e, "cudaEventCreate");
+                h->ev_pool.push_back(nev);
+            }
+            ev = h->ev_pool[h->ev_used++];
+        }
+        e = cudaGraphExecEventRecordNodeSetEvent(h->graph_exec, h->node_ev[i], ev);
+        if (e != cudaSuccess) return cuda_check(h, e, "graph event");
+    }
+    return cuda_check(h, cudaGraphLaunch(h->graph_exec, h->stream), "cudaGraphLaunch");
+}
+
 gz_status ingest_batch(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, uint64_t n) {
     if (n == 0) return GZ_OK;
     cudaStream_t st = h->stream;
-    gz_status ps = prof_event(h);
-    if (ps != GZ_OK) return ps;
-    cudaError_t e = cudaMemsetAsync(h->d_flags, 0, 2 * sizeof(uint32_t), st);  // batch flag + work
-    if (e != cudaSuccess) return cuda_check(h, e, "memset flags");
-    const uint32_t tpb = 256;
-    const uint32_t grid = (uint32_t)std::min<uint64_t>((n + tpb - 1) / tpb, (uint64_t)h->sm_count * 8);
+    gz_status ps;
     if (h->cfg.kernel == GZ_KERNEL_PLAIN) {
-        k_validate_count<<<grid, tpb, 0, st>>>(d_u, d_v, n, h->V, nullptr, h->d_flags);
+        if ((ps = prof_event(h)) != GZ_OK) return ps;
+        cudaError_t e = cudaMemsetAsync(h->d_flags, 0, 2 * sizeof(uint32_t), st);
+        if (e != cudaSuccess) return cuda_check(h, e, "memset flags");
+        const uint32_t grid = (uint32_t)std::min<uint64_t>((n + 255) / 256, (uint64_t)h->sm_count * 8);
+        k_validate_count<<<grid, 256, 0, st>>>(d_u, d_v, n, h->V, nullptr, h->d_flags);
         if ((ps = prof_event(h)) != GZ_OK) return ps;
         const uint32_t pg = (uint32_t)std::min<uint64_t>(n, (uint64_t)h->sm_count * 16);
         k_plain<<<pg, h->block, 0, st>>>(d_u, d_v, n, view_of(h), keys_of(h), h->V, h->R, h->ncol,
                                          h->d_flags);
         h->launches += 2;
-    } else {
-        e = cudaMemsetAsync(h->d_counts, 0, (size_t)(h->V + 1) * sizeof(uint32_t), st);
-        if (e != cudaSuccess) return cuda_check(h, e, "memset counts");
-        k_validate_count<<<grid, tpb, 0, st>>>(d_u, d_v, n, h->V, h->d_counts, h->d_flags);
-        launch_scan(h->d_counts, h->d_offsets, h->d_cursor, h->V, st, h->d_scan_tmp);
-        k_scatter<<<grid, tpb, 0, st>>>(d_u, d_v, n, h->d_cursor, h->d_records, h->d_flags);
-        k_tile_nodes<<<(h->V + 255) / 256, 256, 0, st>>>(h->d_offsets, h->V, h->tile, h->d_flags,
-                                                       h->d_tile_node);
-        BatchedArgs a;
-        a.s = view_of(h);
-        a.keys = keys_of(h);
-        a.offsets = h->d_offsets;
-        a.records = h->d_records;
-        a.tile_node = h->d_tile_node;
-        a.flags = h->d_flags;
-        a.work = h->d_flags + 1;
-        a.V = h->V;
-        a.K = h->K;
-        a.R = h->R;
-        a.ncol = h->ncol;
-        a.Rs = h->smem_rows;
-        a.tile = h->tile;
-        a.small_seg = h->small_seg;
-        a.stats = reinterpret_cast<unsigned long long*>(h->d_stats);
         if ((ps = prof_event(h)) != GZ_OK) return ps;
-        const bool wide = (uint64_t)h->V * h->V > (1ull << 32);
-        batched_fn(h->cfg.smem_mode, wide)<<<h->batched_grid, h->block, h->batched_smem, st>>>(a);
-        h->launches += 6;
+    } else if (!h->cfg.no_graph) {
+        if ((ps = launch_graph(h, d_u, d_v, n)) != GZ_OK) return ps;
+        h->launches += 7;
+    } else {
+        cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+        for (int i = 0; i < 3 && h->prof; ++i) {
+            if ((ps = prof_event(h)) != GZ_OK) return ps;
+            ev[i] = h->ev_pool[h->ev_used - 1];
+        }
+        const uint32_t grid = (uint32_t)std::min<uint64_t>((n + 255) / 256, (uint64_t)h->sm_count * 8);
+        enqueue_batched(h, d_u, d_v, n, grid, st, ev[0], ev[1], ev[2]);
+        h->launches += 7;
     }
-    if ((ps = prof_event(h)) != GZ_OK) return ps;
     if (h->prof) {
         h->prof_batches += 1;
         h->prof_updates += n;
@@ -653,18 +822,21 @@ namespace noalloc {
 constexpr uint32_t kMaxV = GZ_NOALLOC_MAX_V;
 constexpr uint64_t kMaxUpdates = GZ_NOALLOC_MAX_UPDATES;
 constexpr uint32_t kMaxCols = 7u * 30u;  // K(2^17) = 30 CubeSketches per node
-// layout in 32-bit words (the u64 parts first, so they stay 8-byte aligned)
-constexpr size_t kKeys = 0;                                   // 3 x kMaxCols u64
-constexpr size_t kStats = kKeys + 2 * 3 * kMaxCols;           // 2 u64
-constexpr size_t kFlags = kStats + 4;                         // 4 u32
-constexpr size_t kCounts = kFlags + 4;                        // kMaxV + 1
-constexpr size_t kOffsets = kCounts + kMaxV + 1;              // kMaxV + 1
-constexpr size_t kCursor = kOffsets + kMaxV + 1;              // kMaxV + 1
-constexpr size_t kTiles = kCursor + kMaxV + 1;                // scan tile sums
-constexpr size_t kRecords = kTiles + (kMaxV + 1) / 1024 + 2;  // 2 x kMaxUpdates
-constexpr uint32_t kTile = 1024;                              // records per work tile
-constexpr size_t kTileNode = kRecords + 2 * kMaxUpdates;       // first node of every tile
+// layout in 32-bit words; every region starts on a 256-byte boundary (the
+// records are read with 16-byte cp.async copies)
+constexpr size_t up64(size_t w) { return (w + 63) / 64 * 64; }
+constexpr size_t kKeys = 0;                                         // 3 x kMaxCols u64
+constexpr size_t kStats = up64(kKeys + 2 * 3 * kMaxCols);           // 2 u64
+constexpr size_t kFlags = kStats + 4;                               // 4 u32
+constexpr size_t kCounts = up64(kFlags + 4);                        // kMaxV + 1
+constexpr size_t kOffsets = up64(kCounts + kMaxV + 1);              // kMaxV + 1
+constexpr size_t kCursor = up64(kOffsets + kMaxV + 1);              // kMaxV + 1
+constexpr size_t kTiles = up64(kCursor + kMaxV + 1);                // scan tile sums
+constexpr size_t kRecords = up64(kTiles + (kMaxV + 1) / 1024 + 2);  // 2 x kMaxUpdates
+constexpr uint32_t kTile = 1024;                                    // records per work tile
+constexpr size_t kTileNode = up64(kRecords + 2 * kMaxUpdates);       // first node of every tile
 constexpr size_t kWords = kTileNode + 2 * kMaxUpdates / kTile + 2;
+static_assert(kRecords % 4 == 0 && kFlags == kStats + 4, "scratch layout");
 
 static __device__ __align__(256) uint32_t g_scratch[kWords];
 
@@ -704,10 +876,7 @@ static gz_status setup(int dev, uint32_t** ptr, int* sms) {
         if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return GZ_ECUDA;
         int n = 0;
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GZ_ECUDA;
-        for (int wide = 0; wide < 2; ++wide)
-            if (cudaFuncSetAttribute((const void*)batched_fn(1, wide != 0),
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024) != cudaSuccess)
-                return GZ_ECUDA;
+        if (set_smem_cap(dev) != cudaSuccess) return GZ_ECUDA;
         g_sms[dev] = n;
         g_ptr[dev] = static_cast<uint32_t*>(p);
     }
@@ -783,7 +952,7 @@ extern "C" gz_status gz_sketch_update_noalloc(void* sketch, uint32_t V, uint64_t
         a.Rs = Rs;
         a.tile = tile;
         a.small_seg = 4;
-        const size_t smem = (size_t)Rs * block * 12 + (size_t)tile * (wide ? 16 : 4) + (size_t)K * 4;
+        const size_t smem = (size_t)Rs * block * 12 + (size_t)tile * (8 + (wide ? 16 : 4)) + (size_t)K * 4;
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_fn(1, wide), (int)block, smem) !=
                 cudaSuccess ||

@@ -49,16 +49,25 @@ struct Keys {
     const uint64_t* c;
 };
 
-// Checksum h2 (Fig. cube_code): high word of MurmurHash3's 64-bit finalizer
-// (Appleby 2011) applied to idx XOR c.  The last xor-shift of the finalizer does
-// not change the high word, so it is skipped.
+// MurmurHash3's 32-bit finalizer (Appleby 2011).
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// 32-bit fold of an edge index: lo32 ^ lo32(hi32 * 0x9E3779B9) (the identity
+// below 2^32).
+__device__ __forceinline__ uint32_t fold32(uint64_t idx) {
+    return static_cast<uint32_t>(idx) ^ (static_cast<uint32_t>(idx >> 32) * 0x9E3779B9u);
+}
+
+// Checksum h2 (Fig. cube_code): fmix32(fold(idx) ^ lo32(c)).
 __device__ __forceinline__ uint32_t checksum(uint64_t c, uint64_t idx) {
-    uint64_t x = idx ^ c;
-    x ^= x >> 33;
-    x *= 0xFF51AFD7ED558CCDull;
-    x ^= x >> 33;
-    x *= 0xC4CEB9FE1A85EC53ull;
-    return static_cast<uint32_t>(x >> 32);
+    return fmix32(fold32(idx) ^ static_cast<uint32_t>(c));
 }
 
 // Depth hash: t = a*idx + b (mod 2^64), Dietzfelbinger's multiply-add-shift

@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <new>
 #include <vector>
 
 #include "gz_handle.cuh"
@@ -296,7 +297,7 @@ gz_status query_setup(gz_handle* h) {
     const size_t V = h->V;
     h->q_M_members = 64;
     h->q_items_cap = (uint32_t)(2 * V / h->q_M_members + 2);
-    auto alloc32 = [&](uint32_t** p, size_t n) { return cudaMalloc(p, n * sizeof(uint32_t)); };
+    auto alloc32 = [&](uint32_t** p, size_t n) { return cudaMallocAsync(p, n * sizeof(uint32_t), h->stream); };
     cudaError_t e = cudaSuccess;
     uint32_t** arrs[] = {&h->q_label, &h->q_parent, &h->q_members, &h->q_roots, &h->q_target,
                          &h->q_item_base, &h->q_item_cnt, &h->q_F, &h->q_F2, &h->q_M, &h->q_M2,
@@ -311,9 +312,13 @@ gz_status query_setup(gz_handle* h) {
     if (e == cudaSuccess) e = alloc32(&h->q_item_hi, h->q_items_cap);
     if (e == cudaSuccess) e = alloc32(&h->q_forest, 2 * V);
     if (e == cudaSuccess) e = alloc32(&h->q_ctr, C_N);
-    if (e == cudaSuccess) e = cudaMalloc(&h->q_res, V * sizeof(int64_t));
-    if (e == cudaSuccess) e = cudaMalloc(&h->q_partial, (size_t)h->q_items_cap * h->per_k_bytes);
-    if (e == cudaSuccess) e = cudaMallocHost(&h->h_ctr, C_N * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMallocAsync(&h->q_res, V * sizeof(int64_t), h->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&h->q_partial, (size_t)h->q_items_cap * h->per_k_bytes, h->stream);
+    if (e == cudaSuccess) {
+        h->h_ctr = new (std::nothrow) uint32_t[C_N];
+        if (!h->h_ctr) return set_error(h, GZ_ENOMEM, "query counters");
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_check(h, e, "query scratch allocation");
     h->query_ready = true;
     return GZ_OK;
@@ -329,7 +334,7 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
     gz_status s = query_setup(h);
     if (s != GZ_OK) return s;
     if (h->trace && !h->q_trace) {
-        cudaError_t e = cudaMalloc(&h->q_trace, (size_t)h->K * h->V * sizeof(int64_t));
+        cudaError_t e = cudaMallocAsync(&h->q_trace, (size_t)h->K * h->V * sizeof(int64_t), h->stream);
         if (e != cudaSuccess) return cuda_check(h, e, "trace allocation");
     }
     cudaStream_t stm = h->stream;

@@ -1,0 +1,413 @@
+// gz_server.cu -- serving many independent graphs on one GPU (host code only;
+// the device work is the library's ingestion and query kernels).
+//
+// State: every graph has a FIFO of requests and is WAITING (no device memory),
+// RESIDENT (a gz_handle holds its sketches) or RELEASED.  `slots` worker
+// threads, each with its own CUDA stream, loop: pick the graph whose oldest
+// pending request is oldest among the graphs that are resident and idle or
+// that fit in the remaining memory budget, mark it busy, take up to
+// max_batch of its requests, serve them in order on the worker's stream
+// (creating the handle first if the graph is not resident), report the
+// completions, and release the graph's memory if it was closed and drained.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/gz.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t id;
+    uint32_t kind;  // 0 update, 1 query
+    std::vector<uint32_t> u, v;
+    uint32_t* labels = nullptr;
+    double submit_ms = 0;
+};
+
+enum GraphState { WAITING = 0, RESIDENT = 1, RELEASED = 2 };
+
+struct Graph {
+    uint32_t V = 0;
+    uint64_t seed = 0;
+    gz_config cfg{};
+    bool has_cfg = false;
+    uint64_t bytes = 0;
+    GraphState state = WAITING;
+    bool busy = false, closed = false;
+    gz_handle* h = nullptr;
+    std::deque<Request> queue;
+};
+
+}  // namespace
+
+struct gz_server {
+    gz_server_config cfg{};
+    int device = 0;
+    Clock::time_point t0;
+    std::mutex mu;
+    std::condition_variable work_cv, done_cv;
+    std::vector<std::unique_ptr<Graph>> graphs;
+    std::deque<gz_completion> completions;
+    std::vector<std::thread> workers;
+    std::vector<cudaStream_t> streams;
+    uint64_t next_req = 1;
+    uint64_t resident_bytes = 0, peak_bytes = 0, completed = 0;
+    uint64_t outstanding = 0;  // submitted, not completed
+    uint32_t busy_workers = 0;
+    bool stop = false;
+    std::string last_err;
+
+    double now_ms() const {
+        return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+uint64_t graph_bytes(uint32_t V, const gz_config* cfg) {
+    size_t b = 0;
+    gz_memory_bytes(V, cfg, &b);
+    // query scratch (labels, parents, members, ... and partial XORs) and the
+    // host-input staging buffers
+    uint32_t K = 0, R = 0;
+    gz_geometry(V, &K, &R);
+    const uint32_t cl = cfg && cfg->chunk_log2 ? cfg->chunk_log2 : 24;
+    return b + (uint64_t)V * 96 + (2ull * V / 64 + 2) * 84ull * R + (4ull << cl) * 4;
+}
+
+// pick under the lock: a resident idle graph or an admissible waiting one,
+// whichever has the oldest pending request
+Graph* pick(gz_server* s, uint32_t* gid) {
+    Graph* best = nullptr;
+    double best_t = 0;
+    for (size_t i = 0; i < s->graphs.size(); ++i) {
+        Graph* g = s->graphs[i].get();
+        if (g->busy || g->queue.empty() || g->state == RELEASED) continue;
+        if (g->state == WAITING && s->resident_bytes + g->bytes > s->cfg.hbm_budget) continue;
+        const double t = g->queue.front().submit_ms;
+        if (!best || t < best_t) {
+            best = g;
+            best_t = t;
+            *gid = (uint32_t)i;
+        }
+    }
+    return best;
+}
+
+void worker_main(gz_server* s, int slot) {
+    cudaSetDevice(s->device);
+    cudaStream_t stream = s->streams[slot];
+    for (;;) {
+        uint32_t gid = 0;
+        Graph* g = nullptr;
+        std::vector<Request> batch;
+        bool admit = false;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            for (;;) {
+                g = pick(s, &gid);
+                if (g || s->stop) break;
+                s->work_cv.wait(lk);
+            }
+            if (!g) return;  // stopping and nothing left to do
+            g->busy = true;
+            ++s->busy_workers;
+            if (g->state == WAITING) {
+                admit = true;
+                g->state = RESIDENT;  // memory is reserved now, taken below
+                s->resident_bytes += g->bytes;
+                s->peak_bytes = std::max(s->peak_bytes, s->resident_bytes);
+            }
+            const uint32_t take = std::min<size_t>(g->queue.size(), s->cfg.max_batch);
+            for (uint32_t i = 0; i < take; ++i) {
+                batch.push_back(std::move(g->queue.front()));
+                g->queue.pop_front();
+            }
+        }
+        gz_status create_st = GZ_OK;
+        if (admit) {
+            create_st = gz_create(g->V, g->seed, g->has_cfg ? &g->cfg : nullptr, stream, &g->h);
+            if (create_st != GZ_OK) g->h = nullptr;
+        } else if (g->h) {
+            gz_set_stream(g->h, stream);  // the previous worker synchronised before releasing it
+        }
+        std::vector<gz_completion> done;
+        done.reserve(batch.size());
+        std::string err;
+        // updates are queued back to back; the completion time of a run of
+        // updates is taken when the stream next synchronises (a query, or
+        // the end of the batch)
+        size_t unsynced = 0;
+        auto settle = [&](gz_status st) {
+            const double t = s->now_ms();
+            for (size_t i = done.size() - unsynced; i < done.size(); ++i) {
+                done[i].done_ms = t;
+                if (done[i].status == GZ_OK) done[i].status = st;
+            }
+            unsynced = 0;
+        };
+        for (Request& r : batch) {
+            gz_completion c{};
+            c.req_id = r.id;
+            c.graph = gid;
+            c.kind = r.kind;
+            c.submit_ms = r.submit_ms;
+            c.start_ms = s->now_ms();
+            gz_status st = create_st;
+            if (st == GZ_OK && !g->h) st = GZ_ENOMEM;
+            if (st == GZ_OK && r.kind == 0) {
+                st = gz_edge_update(g->h, r.u.data(), r.v.data(), r.u.size(), 0);
+                c.n_updates = r.u.size();
+                c.status = st;
+                done.push_back(c);
+                ++unsynced;
+            } else {
+                if (st == GZ_OK) {
+                    settle(gz_sync(g->h));
+                    uint32_t ncc = 0;
+                    st = gz_connected_components(g->h, r.labels, &ncc, nullptr);
+                    c.n_components = ncc;
+                }
+                c.status = st;
+                c.done_ms = s->now_ms();
+                done.push_back(c);
+            }
+            if (st != GZ_OK && st != GZ_ESKETCH_FAIL && err.empty())
+                err = "graph " + std::to_string(gid) + ": " + (g->h ? gz_last_error(g->h) : "no handle");
+            std::vector<uint32_t>().swap(r.u);
+            std::vector<uint32_t>().swap(r.v);
+        }
+        if (g->h) settle(gz_sync(g->h));
+        else settle(GZ_OK);
+        gz_handle* to_free = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            for (const gz_completion& c : done) s->completions.push_back(c);
+            if (!err.empty()) s->last_err = err;
+            s->completed += done.size();
+            s->outstanding -= done.size();
+            g->busy = false;
+            --s->busy_workers;
+            if (create_st != GZ_OK) {
+                // the graph cannot be admitted: its queued requests fail too
+                for (Request& r : g->queue) {
+                    gz_completion c{};
+                    c.req_id = r.id;
+                    c.graph = gid;
+                    c.kind = r.kind;
+                    c.status = create_st;
+                    c.submit_ms = r.submit_ms;
+                    c.start_ms = c.done_ms = s->now_ms();
+                    s->completions.push_back(c);
+                    ++s->completed;
+                    --s->outstanding;
+                }
+                g->queue.clear();
+            }
+            if ((g->closed && g->queue.empty()) || create_st != GZ_OK) {
+                if (g->state == RESIDENT) s->resident_bytes -= g->bytes;
+                g->state = RELEASED;
+                to_free = g->h;
+                g->h = nullptr;
+            }
+        }
+        if (to_free) gz_destroy(to_free);
+        s->work_cv.notify_all();
+        s->done_cv.notify_all();
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+gz_status gz_server_create(const gz_server_config* cfg, gz_server** out) {
+    if (!out) return GZ_EINVAL;
+    *out = nullptr;
+    gz_server* s = new (std::nothrow) gz_server();
+    if (!s) return GZ_ENOMEM;
+    if (cfg) s->cfg = *cfg;
+    if (s->cfg.slots == 0) s->cfg.slots = 4;
+    if (s->cfg.max_batch == 0) s->cfg.max_batch = 64;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        return GZ_ECUDA;
+    }
+    if (s->cfg.hbm_budget == 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            delete s;
+            return GZ_ECUDA;
+        }
+        s->cfg.hbm_budget = (uint64_t)(0.8 * fr);
+    }
+    s->t0 = Clock::now();
+    for (uint32_t i = 0; i < s->cfg.slots; ++i) {
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+            delete s;
+            return GZ_ECUDA;
+        }
+        s->streams.push_back(st);
+    }
+    for (uint32_t i = 0; i < s->cfg.slots; ++i) s->workers.emplace_back(worker_main, s, (int)i);
+    *out = s;
+    return GZ_OK;
+}
+
+gz_status gz_server_destroy(gz_server* s) {
+    if (!s) return GZ_EINVAL;
+    gz_server_drain(s);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->work_cv.notify_all();
+    for (std::thread& t : s->workers) t.join();
+    for (auto& g : s->graphs)
+        if (g->h) gz_destroy(g->h);
+    for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+    delete s;
+    return GZ_OK;
+}
+
+gz_status gz_server_add_graph(gz_server* s, uint32_t V, uint64_t seed, const gz_config* cfg, uint32_t* graph) {
+    if (!s || !graph) return GZ_EINVAL;
+    uint32_t K, R;
+    if (gz_geometry(V, &K, &R) != GZ_OK) return GZ_EINVAL;
+    std::unique_ptr<Graph> g(new (std::nothrow) Graph());
+    if (!g) return GZ_ENOMEM;
+    g->V = V;
+    g->seed = seed;
+    if (cfg) g->cfg = *cfg;
+    // serving requests are small batches: partition buffers for 2^20 updates
+    // unless the caller chose otherwise (larger batches are split by the call)
+    if (g->cfg.chunk_log2 == 0) g->cfg.chunk_log2 = 20;
+    g->has_cfg = true;
+    g->bytes = graph_bytes(V, &g->cfg);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (g->bytes > s->cfg.hbm_budget) return GZ_ENOMEM;
+    *graph = (uint32_t)s->graphs.size();
+    s->graphs.push_back(std::move(g));
+    return GZ_OK;
+}
+
+static gz_status submit(gz_server* s, uint32_t graph, Request&& r, uint64_t* req_id) {
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (graph >= s->graphs.size()) return GZ_EINVAL;
+        Graph* g = s->graphs[graph].get();
+        if (g->closed || g->state == RELEASED) return GZ_EINVAL;
+        r.id = s->next_req++;
+        r.submit_ms = s->now_ms();
+        if (req_id) *req_id = r.id;
+        g->queue.push_back(std::move(r));
+        ++s->outstanding;
+    }
+    s->work_cv.notify_all();
+    return GZ_OK;
+}
+
+gz_status gz_server_submit_update(gz_server* s, uint32_t graph, const uint32_t* u, const uint32_t* v, size_t n,
+                                  uint64_t* req_id) {
+    if (!s || (n && (!u || !v))) return GZ_EINVAL;
+    Request r;
+    r.kind = 0;
+    try {
+        r.u.assign(u, u + n);
+        r.v.assign(v, v + n);
+    } catch (...) {
+        return GZ_ENOMEM;
+    }
+    return submit(s, graph, std::move(r), req_id);
+}
+
+gz_status gz_server_submit_query(gz_server* s, uint32_t graph, uint32_t* labels, uint64_t* req_id) {
+    if (!s) return GZ_EINVAL;
+    Request r;
+    r.kind = 1;
+    r.labels = labels;
+    return submit(s, graph, std::move(r), req_id);
+}
+
+gz_status gz_server_close_graph(gz_server* s, uint32_t graph) {
+    if (!s) return GZ_EINVAL;
+    gz_handle* to_free = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (graph >= s->graphs.size()) return GZ_EINVAL;
+        Graph* g = s->graphs[graph].get();
+        g->closed = true;
+        if (!g->busy && g->queue.empty() && g->state != RELEASED) {
+            if (g->state == RESIDENT) s->resident_bytes -= g->bytes;
+            g->state = RELEASED;
+            to_free = g->h;
+            g->h = nullptr;
+        }
+    }
+    if (to_free) gz_destroy(to_free);
+    s->work_cv.notify_all();
+    return GZ_OK;
+}
+
+gz_status gz_server_poll(gz_server* s, gz_completion* out, size_t max, size_t* n, int wait_ms) {
+    if (!s || !n || (max && !out)) return GZ_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (s->completions.empty() && wait_ms > 0)
+        s->done_cv.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return !s->completions.empty(); });
+    size_t k = 0;
+    while (k < max && !s->completions.empty()) {
+        out[k++] = s->completions.front();
+        s->completions.pop_front();
+    }
+    *n = k;
+    return GZ_OK;
+}
+
+gz_status gz_server_drain(gz_server* s) {
+    if (!s) return GZ_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->done_cv.wait(lk, [&] { return s->outstanding == 0; });
+    return GZ_OK;
+}
+
+const char* gz_server_last_error(gz_server* s) {
+    if (!s) return "null server";
+    std::lock_guard<std::mutex> lk(s->mu);
+    thread_local std::string copy;
+    copy = s->last_err;
+    return copy.c_str();
+}
+
+gz_status gz_server_stats_read(gz_server* s, gz_server_stats* out) {
+    if (!s || !out) return GZ_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->resident_bytes = s->resident_bytes;
+    out->peak_resident_bytes = s->peak_bytes;
+    out->budget_bytes = s->cfg.hbm_budget;
+    out->graphs = (uint32_t)s->graphs.size();
+    for (auto& g : s->graphs) {
+        out->resident_graphs += g->state == RESIDENT;
+        out->waiting_graphs += g->state == WAITING && !g->queue.empty();
+        out->pending_requests += (uint32_t)g->queue.size();
+    }
+    out->completed_requests = s->completed;
+    return GZ_OK;
+}
+
+}  // extern "C"

@@ -345,6 +345,39 @@ def planted_stream(spec: PlantedSpec):
     return u2.astype(np.uint32), v2.astype(np.uint32), comp
 
 
+def planted_sparse_stream(V: int, seed: int, n_updates: int, n_comp: int = 8, churn: float = 0.1):
+    """Planted components at any scale: the final edges are uniform random
+    pairs inside n_comp equal-ish components (G(n_i, p) with p set by the
+    update budget), churn pairs are uniform over all pairs (inserted, later
+    deleted); seeded shuffle.  Returns (u, v) uint32 and the component map."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    comp = rng.integers(0, n_comp, V)
+    n_final = int(n_updates / (1 + 2 * churn))
+    n_churn = int(n_final * churn)
+    fu, fv = [], []
+    for c in range(n_comp):
+        nodes = np.nonzero(comp == c)[0]
+        if len(nodes) < 2:
+            continue
+        m = int(n_final * len(nodes) / V * 1.05) + 1
+        a = nodes[rng.integers(0, len(nodes), m)]
+        b = nodes[rng.integers(0, len(nodes), m)]
+        keep = a != b
+        fu.append(np.minimum(a, b)[keep])
+        fv.append(np.maximum(a, b)[keep])
+    fu = np.concatenate(fu).astype(np.uint64)
+    fv = np.concatenate(fv).astype(np.uint64)
+    idx = np.unique(fu * np.uint64(V) + fv)[:n_final]
+    a = rng.integers(0, V, n_churn).astype(np.uint64)
+    b = rng.integers(0, V, n_churn).astype(np.uint64)
+    keep = a != b
+    cidx = np.unique(np.minimum(a, b)[keep] * np.uint64(V) + np.maximum(a, b)[keep])
+    cidx = np.setdiff1d(cidx, idx, assume_unique=True)
+    all_idx = np.concatenate([idx, cidx, cidx])
+    all_idx = all_idx[rng.permutation(len(all_idx))]
+    return ((all_idx // np.uint64(V)).astype(np.uint32), (all_idx % np.uint64(V)).astype(np.uint32), comp)
+
+
 def random_stream(V: int, n: int, seed: int, n_distinct: int | None = None):
     """n updates over `n_distinct` random pairs (repeats toggle), any V >= 2."""
     rng = np.random.Generator(np.random.PCG64(seed))

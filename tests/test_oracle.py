@@ -2,7 +2,7 @@
 
 Each test checks the oracle against something other than itself: values the
 paper prints (Table tab:size, the "one-tenth of sketch size" buffer), the
-published SplitMix64 outputs, the set definition of a bucket (Eq. 1-2) against
+published SplitMix64 outputs, the finalizers' invertibility, the set definition of a bucket (Eq. 1-2) against
 the update loop (Fig. cube_code), linearity (Definition def:l0), Lemma
 goodcheck, the membership law behind Lemma goodset, and brute-force connected
 components checked in turn against scipy's graph routine.
@@ -43,26 +43,49 @@ def test_splitmix64_published_outputs():
     assert got == want
 
 
-def test_fmix64_is_a_bijection_with_zero_fixed_point():
-    # every step of MurmurHash3's finalizer is invertible (xorshift by >= 32
-    # bits and multiplication by an odd constant), and 0 maps to 0
-    assert oracle.fmix64(0) == 0
+def test_fmix32_is_a_bijection_with_zero_fixed_point():
+    # every step of MurmurHash3's 32-bit finalizer is invertible (xorshift and
+    # multiplication by an odd constant), and 0 maps to 0
+    assert oracle.fmix32(0) == 0
     rng = np.random.default_rng(5)
-    xs = [int(x) for x in rng.integers(0, 2**63, 2000, dtype=np.int64)]
-    inv1 = pow(0xFF51AFD7ED558CCD, -1, 2**64)
-    inv2 = pow(0xC4CEB9FE1A85EC53, -1, 2**64)
+    inv1 = pow(0x85EBCA6B, -1, 2**32)
+    inv2 = pow(0xC2B2AE35, -1, 2**32)
 
-    def unxs33(y):
-        return y ^ (y >> 33)
+    def unxs16(y):
+        return y ^ (y >> 16)
 
-    for x in xs:
-        y = oracle.fmix64(x)
-        y = unxs33(y)
-        y = (y * inv2) % 2**64
-        y = unxs33(y)
-        y = (y * inv1) % 2**64
-        y = unxs33(y)
+    def unxs13(y):
+        return y ^ (y >> 13) ^ (y >> 26)
+
+    for x in (int(t) for t in rng.integers(0, 2**32, 3000, dtype=np.uint64)):
+        y = unxs16(oracle.fmix32(x))
+        y = (y * inv2) % 2**32
+        y = unxs13(y)
+        y = (y * inv1) % 2**32
+        y = unxs16(y)
         assert y == x
+
+
+def test_fold_is_identity_below_2_32_and_mixes_the_high_word():
+    for x in (0, 1, 12345, 2**32 - 1):
+        assert oracle.fold(x) == x
+    assert oracle.fold(2**32) == 0x9E3779B9
+    assert oracle.fold(3 * 2**32 + 5) == 5 ^ ((3 * 0x9E3779B9) % 2**32)
+    # at V = 2^17 the edges at one vertex fold together at most a few times
+    # (only where that vertex is the smaller end of one edge and the larger
+    # end of the other); the fold feeds the checksum only, so such a pair
+    # merely shares checksums -- bucket membership uses the full index
+    V = 1 << 17
+    rng = np.random.default_rng(9)
+    for x in (int(t) for t in rng.integers(0, V, 8)):
+        ys = np.setdiff1d(np.arange(V, dtype=np.uint64), [x])
+        idx = np.minimum(ys, x) * np.uint64(V) + np.maximum(ys, x)
+        f = [oracle.fold(int(i)) for i in idx[:: max(1, len(idx) // 4096)]]
+        lo = idx & np.uint64(0xFFFFFFFF)
+        hi = idx >> np.uint64(32)
+        full = lo ^ ((hi * np.uint64(0x9E3779B9)) & np.uint64(0xFFFFFFFF))
+        assert f == [int(t) for t in full[:: max(1, len(idx) // 4096)]]
+        assert len(full) - len(np.unique(full)) <= 4
 
 
 def test_checksum_is_not_xor_linear():
@@ -391,3 +414,16 @@ def test_boruvka_kronecker_small():
     want = oracle.cc_edges(spec.V, eu, ev)
     assert np.array_equal(res["labels"], want)
     _check_forest(spec.V, res["forest"], eu, ev, want)
+
+
+@pytest.mark.parametrize("L,density,seed", [(9, 0.3, 1), (10, 0.45, 2), (11, 0.2, 3)])
+def test_kron_components_shortcut_matches_brute_force(L, density, seed):
+    from oracle.kron_cc import kron_components
+
+    V = 1 << L
+    spec = S.KronSpec(L=L, seed=seed, target_edges=density * V * (V - 1) / 2, n_iso=5, slice_log2=2 * L - 2)
+    eu, ev = spec.final_edges()
+    want = oracle.cc_edges(V, eu, ev)
+    got = kron_components(spec, n_hubs=64)
+    assert np.array_equal(got, want)
+    assert len(np.unique(want)) > 1  # isolated vertices exist, so the check is not trivial
