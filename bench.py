@@ -481,18 +481,24 @@ def run_serve(args, rank: int, world: int):
         if i % 2 == 0:
             spec = S.kron_for_updates(e, seed, n_upd, churn=0.1, chunk_updates=2 ** 22, n_iso=8)
             U, Vv, tot = generate_on_device(spec, torch, gz)
-            u = U[:tot].cpu().numpy().view(np.uint32).copy()
-            v = Vv[:tot].cpu().numpy().view(np.uint32).copy()
+            hu = torch.empty(tot, dtype=torch.int32, pin_memory=True)
+            hv = torch.empty(tot, dtype=torch.int32, pin_memory=True)
+            hu.copy_(U[:tot])
+            hv.copy_(Vv[:tot])
             del U, Vv
             kind = "kronecker"
         else:
-            u, v, _ = S.planted_sparse_stream(V, seed, n_upd)
+            u0, v0, _ = S.planted_sparse_stream(V, seed, n_upd)
+            hu = torch.from_numpy(u0.view(np.int32)).pin_memory()
+            hv = torch.from_numpy(v0.view(np.int32)).pin_memory()
             kind = "planted"
+        # pinned host payloads, lent to the server without a copy
+        u, v = hu.numpy().view(np.uint32), hv.numpy().view(np.uint32)
         cuts, pos = [], 0
         while pos < len(u):
             pos += int(2 ** rng.uniform(16, 20))
             cuts.append(min(pos, len(u)))
-        graphs.append({"V": V, "seed": seed, "u": u, "v": v, "cuts": cuts, "kind": kind})
+        graphs.append({"V": V, "seed": seed, "u": u, "v": v, "cuts": cuts, "kind": kind, "pin": (hu, hv)})
     total_updates = sum(len(g["u"]) for g in graphs)
     sizes = []
     import ctypes
@@ -531,7 +537,7 @@ def run_serve(args, rank: int, world: int):
             _, gi, kind, lo, hi = ev
             g = graphs[gi]
             if kind == "u":
-                srv.submit_update(gids[gi], g["u"][lo:hi], g["v"][lo:hi])
+                srv.submit_update(gids[gi], g["u"][lo:hi], g["v"][lo:hi], copy=False)
             elif kind == "q":
                 srv.submit_query(gids[gi])
             else:

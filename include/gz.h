@@ -63,9 +63,10 @@ typedef struct {
     uint32_t tile_records;  /* records per work tile of the batched kernel (default 1024) */
     uint32_t ctas_per_sm;   /* resident CTAs per SM of the persistent batched kernel (default: max) */
     uint32_t small_segment; /* node segments shorter than this skip shared-memory staging (default 4) */
-    uint32_t smem_mode;     /* delta update in shared memory: 0 load-xor-store, 1 shared atomics */
+    uint32_t smem_mode;     /* delta update in shared memory: 0 default (= 1), 1 shared atomics,
+                               2 load-xor-store */
     uint32_t no_graph;      /* 1: launch a chunk's kernels one by one instead of replaying the
-                               CUDA graph captured for the handle (default 0: graph) */
+                               CUDA graph captured for the handle after its 8th chunk (default 0) */
     uint32_t reserved[4];
 } gz_config;
 
@@ -167,6 +168,21 @@ gz_status gz_query_trace(gz_handle *h, int64_t *out);
 gz_status gz_export_sketch(gz_handle *h, uint32_t node_lo, uint32_t node_hi,
                            uint64_t *alpha, uint32_t *gamma, int on_device);
 
+/* Checkpoint / resume.  By linearity the node sketches are the whole state of
+ * a graph (Section 2.2: the stream is summarised by them), so a checkpoint is
+ * a 64-byte header -- magic "GZB3CKP1", version, V, K, R, seed, bytes per node
+ * sketch -- followed by the raw sketch array (exact-depth layout).  Both calls
+ * are synchronous; buf is host memory owned by the caller.
+ *   gz_checkpoint_bytes: size a checkpoint of h needs.
+ *   gz_checkpoint      : write it (GZ_EINVAL if size is too small, or if a
+ *                        rejected batch is still unreported).
+ *   gz_restore         : new handle holding exactly the checkpointed state
+ *                        (GZ_EINVAL on a bad magic, version or geometry). */
+gz_status gz_checkpoint_bytes(gz_handle *h, size_t *bytes);
+gz_status gz_checkpoint(gz_handle *h, void *buf, size_t size);
+gz_status gz_restore(const void *buf, size_t size, const gz_config *cfg, void *stream,
+                     gz_handle **out);
+
 /* Geometry and device pointer of the raw sketch array of a handle (exact-
  * depth form, layout per node: for each k, alpha[row][j] then gamma[row][j]).
  * Any output pointer may be NULL. */
@@ -247,10 +263,14 @@ gz_status gz_server_destroy(gz_server *s);
 gz_status gz_server_add_graph(gz_server *s, uint32_t V, uint64_t seed, const gz_config *cfg,
                               uint32_t *graph);
 
-/* Queue an update batch (host arrays, copied by the call; same meaning as
- * gz_edge_update).  *req_id identifies its completion. */
+/* Queue an update batch (host arrays; same meaning as gz_edge_update).  By
+ * default the call copies u and v; with flags & GZ_SUBMIT_NOCOPY it keeps the
+ * pointers instead, and the caller must keep both arrays unchanged until the
+ * request's completion has been polled (pinned memory gives the fastest
+ * host-to-device copies).  *req_id identifies its completion. */
+#define GZ_SUBMIT_NOCOPY 1u
 gz_status gz_server_submit_update(gz_server *s, uint32_t graph, const uint32_t *u,
-                                  const uint32_t *v, size_t n, uint64_t *req_id);
+                                  const uint32_t *v, size_t n, uint32_t flags, uint64_t *req_id);
 
 /* Queue a connected-components query; labels (host, V entries, or NULL) is
  * written before the completion is reported and must stay valid until then. */

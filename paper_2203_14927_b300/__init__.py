@@ -129,7 +129,8 @@ _SIGNATURES = {
     "gz_server_add_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p,
                                            ctypes.c_void_p]),
     "gz_server_submit_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
-                                               ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+                                               ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32,
+                                               ctypes.c_void_p]),
     "gz_server_submit_query": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
                                               ctypes.c_void_p]),
     "gz_server_close_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
@@ -138,6 +139,10 @@ _SIGNATURES = {
     "gz_server_drain": (ctypes.c_int, [ctypes.c_void_p]),
     "gz_server_stats_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gz_server_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "gz_checkpoint_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gz_checkpoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "gz_restore": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p]),
     "gz_sketch_update_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                                 ctypes.c_void_p, ctypes.c_void_p]),
@@ -309,6 +314,35 @@ class Graph:
                                            g.ctypes.data_as(ctypes.c_void_p), 0), "gz_export_sketch")
         return a, g
 
+    def checkpoint(self) -> np.ndarray:
+        """The handle's whole state as bytes (header + node sketches)."""
+        n = ctypes.c_size_t()
+        self._check(lib().gz_checkpoint_bytes(self._h, ctypes.byref(n)), "gz_checkpoint_bytes")
+        buf = np.empty(n.value, np.uint8)
+        self._check(lib().gz_checkpoint(self._h, buf.ctypes.data_as(ctypes.c_void_p), n.value), "gz_checkpoint")
+        return buf
+
+    @classmethod
+    def restore(cls, buf, stream=None, **cfg) -> "Graph":
+        """A new Graph holding exactly the checkpointed state."""
+        buf = np.ascontiguousarray(buf, np.uint8)
+        c = Config()
+        for k, val in cfg.items():
+            setattr(c, k, KERNELS[val] if k == "kernel" else val)
+        h = ctypes.c_void_p()
+        s = _current_stream() if stream is None else stream
+        st = lib().gz_restore(buf.ctypes.data_as(ctypes.c_void_p), buf.size, ctypes.byref(c), ctypes.c_void_p(s),
+                              ctypes.byref(h))
+        if st != GZ_OK:
+            raise GzError(st, "gz_restore failed")
+        g = cls.__new__(cls)
+        g._h = h
+        info = g.info()
+        g.V = info["V"]
+        g.K, g.R = info["K"], info["R"]
+        g.seed = int(np.frombuffer(buf[24:32].tobytes(), np.uint64)[0])
+        return g
+
     def profile_enable(self, on: bool = True):
         self._check(lib().gz_profile_enable(self._h, 1 if on else 0), "gz_profile_enable")
 
@@ -411,6 +445,7 @@ class Server:
         if st != GZ_OK:
             raise GzError(st, "gz_server_create failed")
         self._labels = {}
+        self._lent = {}
         self._V = {}
 
     def add_graph(self, V: int, seed: int = 0, **cfg) -> int:
@@ -424,14 +459,25 @@ class Server:
         self._V[gid.value] = V
         return gid.value
 
-    def submit_update(self, graph: int, u, v) -> int:
+    def submit_update(self, graph: int, u, v, copy: bool = True) -> int:
+        """Queue an update batch.  copy=False lends the arrays to the server
+        (kept alive here until the completion is polled)."""
+        u = np.asarray(u)
+        v = np.asarray(v)
+        if u.dtype == np.int32:
+            u = u.view(np.uint32)
+        if v.dtype == np.int32:
+            v = v.view(np.uint32)
         u = np.ascontiguousarray(u, np.uint32)
         v = np.ascontiguousarray(v, np.uint32)
         rid = ctypes.c_uint64()
         st = lib().gz_server_submit_update(self._s, graph, u.ctypes.data_as(ctypes.c_void_p),
-                                           v.ctypes.data_as(ctypes.c_void_p), len(u), ctypes.byref(rid))
+                                           v.ctypes.data_as(ctypes.c_void_p), len(u),
+                                           0 if copy else 1, ctypes.byref(rid))
         if st != GZ_OK:
             raise GzError(st, "gz_server_submit_update failed")
+        if not copy:
+            self._lent[rid.value] = (u, v)
         return rid.value
 
     def submit_query(self, graph: int) -> int:
@@ -457,6 +503,8 @@ class Server:
             d = {f: getattr(c, f) for f, _ in Completion._fields_}
             if c.kind == 1:
                 d["labels"] = self._labels.pop(c.req_id, None)
+            else:
+                self._lent.pop(c.req_id, None)
             out.append(d)
         return out
 

@@ -374,6 +374,69 @@ gz_status gz_profile_read(gz_handle* h, gz_profile* out) {
     return GZ_OK;
 }
 
+namespace {
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, V, K, R;
+    uint64_t seed, node_bytes;
+    uint8_t reserved[24];
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
+const char kMagic[8] = {'G', 'Z', 'B', '3', 'C', 'K', 'P', '1'};
+}  // namespace
+
+gz_status gz_checkpoint_bytes(gz_handle* h, size_t* bytes) {
+    if (!h || !bytes) return GZ_EINVAL;
+    *bytes = sizeof(CkptHeader) + (size_t)h->V * h->node_bytes;
+    return GZ_OK;
+}
+
+gz_status gz_checkpoint(gz_handle* h, void* buf, size_t size) {
+    if (!h || !buf) return GZ_EINVAL;
+    const size_t need = sizeof(CkptHeader) + (size_t)h->V * h->node_bytes;
+    if (size < need) return set_error(h, GZ_EINVAL, "checkpoint buffer too small");
+    gz_status s = check_rejected(h);
+    if (s != GZ_OK) return s;
+    CkptHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, kMagic, 8);
+    hd.version = 1;
+    hd.V = h->V;
+    hd.K = h->K;
+    hd.R = h->R;
+    hd.seed = h->seed;
+    hd.node_bytes = h->node_bytes;
+    std::memcpy(buf, &hd, sizeof(hd));
+    cudaError_t e = cudaMemcpyAsync(static_cast<uint8_t*>(buf) + sizeof(hd), h->d_sketch, need - sizeof(hd),
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_check(h, e, "checkpoint copy");
+}
+
+gz_status gz_restore(const void* buf, size_t size, const gz_config* cfg, void* stream, gz_handle** out) {
+    if (!buf || !out || size < sizeof(CkptHeader)) return GZ_EINVAL;
+    *out = nullptr;
+    CkptHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    uint32_t K, R;
+    if (std::memcmp(hd.magic, kMagic, 8) != 0 || hd.version != 1 || !gz::geometry(hd.V, &K, &R) ||
+        K != hd.K || R != hd.R || hd.node_bytes != (uint64_t)K * 84u * R ||
+        size < sizeof(hd) + (size_t)hd.V * hd.node_bytes)
+        return GZ_EINVAL;
+    gz_handle* h = nullptr;
+    gz_status s = gz_create(hd.V, hd.seed, cfg, stream, &h);
+    if (s != GZ_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(h->d_sketch, static_cast<const uint8_t*>(buf) + sizeof(hd),
+                                    (size_t)hd.V * hd.node_bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        gz_destroy(h);
+        return GZ_ECUDA;
+    }
+    *out = h;
+    return GZ_OK;
+}
+
 gz_status gz_info(gz_handle* h, uint32_t* V, uint32_t* K, uint32_t* R, size_t* node_bytes,
                   void** sketch_device) {
     if (!h) return GZ_EINVAL;

@@ -592,8 +592,9 @@ gz_status ingest_setup(gz_handle* h) {
     const bool wide = (uint64_t)h->V * h->V > (1ull << 32);
     if (h->tile % 4 != 0) return set_error(h, GZ_EINVAL, "tile_records must be a multiple of 4");
     h->batched_smem = (size_t)rs * h->block * 12 + (size_t)h->tile * (8 + (wide ? 16 : 4)) + (size_t)h->K * 4;
-    if (h->cfg.smem_mode > 1) return set_error(h, GZ_EINVAL, "smem_mode must be 0 or 1");
-    const void* fn = (const void*)batched_fn(h->cfg.smem_mode, wide);
+    if (h->cfg.smem_mode > 2) return set_error(h, GZ_EINVAL, "smem_mode must be 0, 1 or 2");
+    h->atomic_delta = h->cfg.smem_mode != 2;
+    const void* fn = (const void*)batched_fn(h->atomic_delta, wide);
     // The dynamic shared-memory cap is one process-wide setting per kernel, so
     // every caller sets the same value (the device's opt-in maximum); a
     // per-handle value would let handles of different sizes break each other.
@@ -653,7 +654,7 @@ static void enqueue_batched(gz_handle* h, const uint32_t* d_u, const uint32_t* d
     k_tile_nodes<<<(h->V + 255) / 256, 256, 0, st>>>(h->d_offsets, h->V, h->tile, h->d_flags, h->d_tile_node);
     if (ev1) record(ev1);
     const bool wide = (uint64_t)h->V * h->V > (1ull << 32);
-    batched_fn(h->cfg.smem_mode, wide)<<<h->batched_grid, h->block, h->batched_smem, st>>>(batched_args(h));
+    batched_fn(h->atomic_delta, wide)<<<h->batched_grid, h->block, h->batched_smem, st>>>(batched_args(h));
     if (ev2) record(ev2);
 }
 
@@ -758,7 +759,8 @@ gz_status ingest_batch(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, u
                                          h->d_flags);
         h->launches += 2;
         if ((ps = prof_event(h)) != GZ_OK) return ps;
-    } else if (!h->cfg.no_graph) {
+    } else if (!h->cfg.no_graph && h->batches_done >= 8) {
+        // the captured graph pays off once a handle keeps ingesting
         if ((ps = launch_graph(h, d_u, d_v, n)) != GZ_OK) return ps;
         h->launches += 7;
     } else {
@@ -771,6 +773,7 @@ gz_status ingest_batch(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, u
         enqueue_batched(h, d_u, d_v, n, grid, st, ev[0], ev[1], ev[2]);
         h->launches += 7;
     }
+    ++h->batches_done;
     if (h->prof) {
         h->prof_batches += 1;
         h->prof_updates += n;

@@ -32,7 +32,9 @@ using Clock = std::chrono::steady_clock;
 struct Request {
     uint64_t id;
     uint32_t kind;  // 0 update, 1 query
-    std::vector<uint32_t> u, v;
+    std::vector<uint32_t> u, v;            // owned copy, or empty when borrowed
+    const uint32_t *bu = nullptr, *bv = nullptr;  // the caller's arrays (GZ_SUBMIT_NOCOPY)
+    size_t n = 0;
     uint32_t* labels = nullptr;
     double submit_ms = 0;
 };
@@ -169,8 +171,8 @@ void worker_main(gz_server* s, int slot) {
             gz_status st = create_st;
             if (st == GZ_OK && !g->h) st = GZ_ENOMEM;
             if (st == GZ_OK && r.kind == 0) {
-                st = gz_edge_update(g->h, r.u.data(), r.v.data(), r.u.size(), 0);
-                c.n_updates = r.u.size();
+                st = gz_edge_update(g->h, r.bu, r.bv, r.n, 0);
+                c.n_updates = r.n;
                 c.status = st;
                 done.push_back(c);
                 ++unsynced;
@@ -323,15 +325,23 @@ static gz_status submit(gz_server* s, uint32_t graph, Request&& r, uint64_t* req
 }
 
 gz_status gz_server_submit_update(gz_server* s, uint32_t graph, const uint32_t* u, const uint32_t* v, size_t n,
-                                  uint64_t* req_id) {
+                                  uint32_t flags, uint64_t* req_id) {
     if (!s || (n && (!u || !v))) return GZ_EINVAL;
     Request r;
     r.kind = 0;
-    try {
-        r.u.assign(u, u + n);
-        r.v.assign(v, v + n);
-    } catch (...) {
-        return GZ_ENOMEM;
+    r.n = n;
+    if (flags & GZ_SUBMIT_NOCOPY) {
+        r.bu = u;
+        r.bv = v;
+    } else {
+        try {
+            r.u.assign(u, u + n);
+            r.v.assign(v, v + n);
+        } catch (...) {
+            return GZ_ENOMEM;
+        }
+        r.bu = r.u.data();
+        r.bv = r.v.data();
     }
     return submit(s, graph, std::move(r), req_id);
 }

@@ -66,7 +66,7 @@ def test_planted_small_config_bit_exact(kernel):
     assert np.array_equal(want["labels"], oracle.brute_cc(spec.V, u, v))
 
 
-@pytest.mark.parametrize("smem_mode", [0, 1])
+@pytest.mark.parametrize("smem_mode", [1, 2])
 @pytest.mark.parametrize("V", [2, 3, 77, 1000, 4097])
 def test_ragged_sizes_many_chunks_and_tiles(V, smem_mode):
     # chunk of 2^10 updates (many chunks + a ragged tail), tiles of 64 records
@@ -122,7 +122,23 @@ def test_host_and_device_inputs_agree():
     assert np.array_equal(a1, a2) and np.array_equal(b1, b2)
 
 
-@pytest.mark.parametrize("smem_mode", [0, 1])
+def test_graph_replay_and_direct_launches_agree():
+    # 40 chunks of 2^11 updates: the handle replays its captured CUDA graph
+    # from the 9th chunk on; with no_graph it launches every kernel itself
+    V = 5000
+    u, v = S.random_stream(V, 40 * 2048 - 77, seed=12)
+    A, G = oracle.ingest(V, 6, u, v)
+    g1 = _gpu_graph(V, 6, u, v, chunk_log2=11)
+    g2 = _gpu_graph(V, 6, u, v, chunk_log2=11, no_graph=1)
+    _assert_same_sketches(g1, A, G)
+    _assert_same_sketches(g2, A, G)
+    g1.profile_enable(True)  # the graph's event nodes are re-pointed when profiling
+    g1.edge_update(_dev(u[:9000]), _dev(v[:9000]))
+    p = g1.profile_read()
+    assert p["batches"] == 5 and p["update_ms"] > 0
+
+
+@pytest.mark.parametrize("smem_mode", [1, 2])
 def test_smem_modes_bit_exact_kronecker(smem_mode):
     spec = S.KronSpec(L=12, seed=8, target_edges=0.4 * 4096 * 4095 / 2, churn=0.1, n_iso=30,
                       slice_log2=20)
@@ -195,3 +211,25 @@ def test_full_size_kronecker_2p13_sampled_nodes():
     want = oracle.cc_edges(spec.V, eu, ev)
     assert st["fails_last"] == 0 and st["exhausted"] == 0
     assert np.array_equal(labels, want)
+
+
+def test_checkpoint_restore_resumes_exactly():
+    V = 2500
+    u, v = S.random_stream(V, 40000, seed=31)
+    A, G = oracle.ingest(V, 14, u, v)
+    g = gz.Graph(V, 14)
+    g.edge_update(_dev(u[:15000]), _dev(v[:15000]))
+    ck = g.checkpoint()
+    assert bytes(ck[:8]) == b"GZB3CKP1"
+    h = gz.Graph.restore(ck)
+    for x in (g, h):
+        x.edge_update(_dev(u[15000:]), _dev(v[15000:]))
+        x.sync()
+        _assert_same_sketches(x, A, G)
+    assert np.array_equal(g.connected_components()[0], h.connected_components()[0])
+    bad = ck.copy()
+    bad[0] ^= 1
+    with pytest.raises(gz.GzError):
+        gz.Graph.restore(bad)
+    with pytest.raises(gz.GzError):
+        gz.Graph.restore(ck[: len(ck) - 1])

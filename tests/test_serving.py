@@ -74,7 +74,8 @@ def test_results_in_the_mix_equal_results_alone_and_budget_holds():
         cursors[i] += 1
         remaining -= 1
         if r[0] == "u":
-            srv.submit_update(gids[i], r[1], r[2])
+            # half the batches are lent without a copy (kept alive until polled)
+            srv.submit_update(gids[i], r[1], r[2], copy=bool(i % 2))
         else:
             qids[srv.submit_query(gids[i])] = (i, sum(1 for x in graphs[i][2][:cursors[i]] if x[0] == "q") - 1)
         if cursors[i] == len(graphs[i][2]):
