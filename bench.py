@@ -304,7 +304,7 @@ def run_ours(args, rank: int, world: int):
     wide = spec.V * spec.V > (1 << 32)
     col_updates = upd_per_launch * 2 * 7 * K
     # HBM, by the method's bytes per chunk: the kernel's two records per update
-    # and one read + write of every node sketch (SURVEY 8(d) amortised RMW)
+    # and one read + write of every node sketch (the amortised read-modify-write of the batched design)
     hbm_bytes = 8.0 * upd_per_launch + 2.0 * s_total
     hbm = {"bound": "hbm", "achieved": hbm_bytes / sec / 1e9, "peak": peak, "unit": "GB/s",
            "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",

@@ -48,13 +48,12 @@ struct gz_handle {
     bool query_ready = false;
     uint32_t *q_label = nullptr, *q_parent = nullptr, *q_count = nullptr, *q_off = nullptr,
              *q_cursor = nullptr, *q_members = nullptr, *q_roots = nullptr, *q_target = nullptr,
-             *q_item_base = nullptr, *q_item_cnt = nullptr, *q_item_comp = nullptr,
-             *q_item_lo = nullptr, *q_item_hi = nullptr, *q_F = nullptr, *q_F2 = nullptr,
+             *q_slot = nullptr, *q_F = nullptr, *q_F2 = nullptr,
              *q_M = nullptr, *q_M2 = nullptr, *q_flag = nullptr, *q_pos = nullptr,
              *q_forest = nullptr, *q_ctr = nullptr, *h_ctr = nullptr;
     int64_t* q_res = nullptr;
-    uint8_t* q_partial = nullptr;
-    uint32_t q_items_cap = 0, q_M_members = 0;
+    uint64_t* q_acc = nullptr;     // per big component: XOR of its members' CubeSketch
+    uint32_t q_slots_cap = 0;
     int64_t* q_trace = nullptr;
     bool trace = false;
     bool trace_valid = false;
@@ -89,6 +88,11 @@ gz_status export_nested(gz_handle* h, uint32_t lo, uint32_t hi, uint64_t* d_alph
                         uint32_t* d_gamma);
 
 // query (gz_query.cu)
+// Components with more than kMergeChunk members are merged by chunks of
+// kMergeChunk members into an accumulator slot of their own; at most
+// V / (kMergeChunk + 1) components are that large.
+constexpr uint32_t kMergeChunk = 32;
+inline uint32_t query_slots(uint32_t V) { return V / (kMergeChunk + 1) + 1; }
 gz_status query_setup(gz_handle* h);
 gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* forest_uv,
                   size_t* n_edges, uint32_t* n_cc, gz_query_stats* st);

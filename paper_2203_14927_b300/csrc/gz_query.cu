@@ -4,9 +4,10 @@
 //
 // Round r:
 //   group    nodes by current component (counting sort by label);
-//   merge    component sketch = XOR of the members' CubeSketch r (big
-//            components are split into items of M members whose partial XORs
-//            are combined afterwards);
+//   merge    component sketch = XOR of the members' CubeSketch r (a
+//            component of more than M members is merged by chunks of M
+//            members, each XORed into the component's accumulator with
+//            atomics);
 //   sample   nested rows by suffix XOR, then the first bucket in the scan
 //            order of Fig. cube_code (columns, then rows ascending) that passes
 //            the checksum, decodes to an edge u < v < V and leaves the component;
@@ -30,15 +31,15 @@
 
 namespace gz {
 
-enum { C_ROOTS = 0, C_ITEMS = 1, C_EDGES = 2, C_FAILS = 3, C_FOREST = 4, C_NCC = 5, C_N = 8 };
+enum { C_ROOTS = 0, C_BIG = 1, C_EDGES = 2, C_FAILS = 3, C_FOREST = 4, C_NCC = 5, C_N = 8 };
 
 struct QArgs {
     SketchView s;
     const uint64_t* kc;  // checksum keys, 7K
     uint32_t V, K, R, round, M;
     uint32_t *label, *parent, *count, *off, *cursor, *members, *roots, *target;
-    uint32_t *item_base, *item_cnt, *item_comp, *item_lo, *item_hi;
-    uint64_t* partial;  // items x (21R/2) words
+    uint32_t* slot;     // accumulator slot of a component with more than M members
+    uint64_t* acc;      // slots x (21R/2) words, zero between rounds
     int64_t* res;
     int64_t* trace;     // K x V or null
     uint32_t* ctr;
@@ -72,10 +73,19 @@ __device__ void dsu_unite(uint32_t* parent, uint32_t a, uint32_t b) {
     }
 }
 
-__global__ void k_q_init(uint32_t* label, uint32_t* parent, uint32_t V) {
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
-        label[v] = v;
-        parent[v] = v;
+// Query start: every vertex is its own component (round 0 needs no grouping).
+__global__ void k_q_init(QArgs q) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < q.V; v += gridDim.x * blockDim.x) {
+        q.label[v] = v;
+        q.parent[v] = v;
+        q.count[v] = 1;
+        q.off[v] = v;
+        q.members[v] = v;
+        q.roots[v] = v;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        q.ctr[C_ROOTS] = q.V;
+        q.ctr[C_BIG] = 0;
     }
 }
 
@@ -85,121 +95,208 @@ __global__ void k_fill64(int64_t* p, uint64_t n, int64_t val) {
         p[i] = val;
 }
 
+// Grouping by label.  After round 0 most vertices share a few labels, so the
+// per-label counters are bumped once per warp and label (match_any), not once
+// per vertex.  The loops below step whole blocks, so every warp is convergent.
 __global__ void k_q_count(QArgs q) {
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < q.V; v += gridDim.x * blockDim.x)
-        atomicAdd(&q.count[q.label[v]], 1u);
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t b = blockIdx.x * blockDim.x; b < q.V; b += gridDim.x * blockDim.x) {
+        const uint32_t v = b + threadIdx.x;
+        const bool act = v < q.V;
+        const uint32_t l = act ? q.label[v] : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, l);
+        if (act && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&q.count[l], __popc(peers));
+    }
 }
 
 __global__ void k_q_group(QArgs q) {
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < q.V; v += gridDim.x * blockDim.x)
-        q.members[atomicAdd(&q.cursor[q.label[v]], 1u)] = v;
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t b = blockIdx.x * blockDim.x; b < q.V; b += gridDim.x * blockDim.x) {
+        const uint32_t v = b + threadIdx.x;
+        const bool act = v < q.V;
+        const uint32_t l = act ? q.label[v] : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, l);
+        const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
+        uint32_t pos = 0;
+        if (act && lane == leader) pos = atomicAdd(&q.cursor[l], __popc(peers));
+        pos = __shfl_sync(0xffffffffu, pos, leader);
+        if (act) q.members[pos + __popc(peers & ((1u << lane) - 1u))] = v;
+    }
 }
 
+// Root list (one append per warp) and an accumulator slot for every
+// component with more than M members.
 __global__ void k_q_roots(QArgs q) {
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < q.V; c += gridDim.x * blockDim.x) {
-        const uint32_t cnt = q.count[c];
-        if (cnt == 0) {
-            if (q.trace) q.trace[(uint64_t)q.round * q.V + c] = -3;
-            continue;
-        }
-        q.roots[atomicAdd(&q.ctr[C_ROOTS], 1u)] = c;
-        if (cnt > q.M) {
-            const uint32_t ni = (cnt + q.M - 1) / q.M;
-            const uint32_t base = atomicAdd(&q.ctr[C_ITEMS], ni);
-            q.item_base[c] = base;
-            q.item_cnt[c] = ni;
-            const uint32_t o = q.off[c];
-            for (uint32_t i = 0; i < ni; ++i) {
-                q.item_comp[base + i] = c;
-                q.item_lo[base + i] = o + i * q.M;
-                q.item_hi[base + i] = o + min(cnt, (i + 1) * q.M);
-            }
-        } else {
-            q.item_cnt[c] = 0;
-        }
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t b = blockIdx.x * blockDim.x; b < q.V; b += gridDim.x * blockDim.x) {
+        const uint32_t c = b + threadIdx.x;
+        const uint32_t cnt = c < q.V ? q.count[c] : 0u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, cnt > 0);
+        uint32_t base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&q.ctr[C_ROOTS], __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (cnt > 0) q.roots[base + __popc(bal & ((1u << lane) - 1u))] = c;
+        if (cnt > q.M) q.slot[c] = atomicAdd(&q.ctr[C_BIG], 1u);
+        if (c < q.V && cnt == 0 && q.trace) q.trace[(uint64_t)q.round * q.V + c] = -3;
     }
 }
 
-// Partial XOR of CubeSketch `round` over the members of one item.
-__global__ void k_q_merge_items(QArgs q) {
+// XOR of CubeSketch `round` over the members of every component with more
+// than M members, into that component's accumulator slot.  The members array
+// is grouped by component, so a chunk of M consecutive members meets at most
+// two such components: one that covers its start, one that covers its end.
+__global__ void __launch_bounds__(384) k_q_merge(QArgs q) {
+    __shared__ uint32_t s_node[kMergeChunk];
     const uint32_t nw = 21u * q.R / 2u;  // u64 words of one CubeSketch (84R bytes)
-    const uint32_t n_items = q.ctr[C_ITEMS];
-    for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const uint32_t lo = q.item_lo[it], hi = q.item_hi[it];
+    const uint32_t M = q.M, nchunks = (q.V + M - 1) / M;
+    for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const uint32_t lo = ch * M, hi = min(q.V, lo + M);
+        const uint32_t cA = q.label[q.members[lo]], cB = q.label[q.members[hi - 1]];
+        const uint32_t nA = q.count[cA], nB = q.count[cB];
+        const bool bigA = nA > M, bigB = cB != cA && nB > M;
+        if (!bigA && !bigB) continue;  // block-uniform
+        __syncthreads();               // s_node of the previous chunk is consumed
+        if (threadIdx.x < hi - lo) s_node[threadIdx.x] = q.members[lo + threadIdx.x];
+        __syncthreads();
+        const uint32_t eA = bigA ? min(hi, q.off[cA] + nA) - lo : 0u;
+        const uint32_t sB = bigB ? max(lo, q.off[cB]) - lo : hi - lo;
+        uint64_t* accA = bigA ? q.acc + (uint64_t)q.slot[cA] * nw : nullptr;
+        uint64_t* accB = bigB ? q.acc + (uint64_t)q.slot[cB] * nw : nullptr;
         for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) {
-            uint64_t acc = 0;
-            for (uint32_t m = lo; m < hi; ++m) {
-                const uint64_t* cube = reinterpret_cast<const uint64_t*>(q.s.cube(q.members[m], q.round));
-                acc ^= __ldg(cube + w);
+            if (bigA) {
+                uint64_t x = 0;
+#pragma unroll 8
+                for (uint32_t m = 0; m < eA; ++m)
+                    x ^= __ldg(reinterpret_cast<const uint64_t*>(q.s.cube(s_node[m], q.round)) + w);
+                atomicXor(reinterpret_cast<unsigned long long*>(accA + w), (unsigned long long)x);
             }
-            q.partial[(uint64_t)it * nw + w] = acc;
+            if (bigB) {
+                uint64_t x = 0;
+#pragma unroll 8
+                for (uint32_t m = sB; m < hi - lo; ++m)
+                    x ^= __ldg(reinterpret_cast<const uint64_t*>(q.s.cube(s_node[m], q.round)) + w);
+                atomicXor(reinterpret_cast<unsigned long long*>(accB + w), (unsigned long long)x);
+            }
         }
     }
 }
 
-// Merge (small components) + sample, one CTA per component.
+// Sample, one warp per component.  Lane l holds rows l and l+32 of all 7
+// columns of the component's CubeSketch `round`: the XOR of its members'
+// blocks (at most M of them), or its accumulator slot, which is cleared again
+// for the next round.  The nested rows (row i = XOR of exact rows >= i) come
+// from a warp-shuffle suffix XOR per column, and the first good bucket in
+// Fig. cube_code's order (columns, then rows ascending) is found with a ballot
+// per column.
+__device__ __forceinline__ uint64_t shfl_down64(uint64_t x, int off) {
+    const uint32_t lo = __shfl_down_sync(0xffffffffu, (uint32_t)x, off);
+    const uint32_t hi = __shfl_down_sync(0xffffffffu, (uint32_t)(x >> 32), off);
+    return ((uint64_t)hi << 32) | lo;
+}
+
 __global__ void __launch_bounds__(256) k_q_sample(QArgs q) {
-    extern __shared__ __align__(16) uint64_t S[];  // nw words: alpha[R][7] then gamma[R][7]
-    __shared__ uint32_t s_best;
-    const uint32_t nw = 21u * q.R / 2u, R = q.R, nb = GZ_COLS * R;
-    uint64_t* A = S;
-    uint32_t* G = reinterpret_cast<uint32_t*>(S + nb);
-    const uint32_t n_roots = q.ctr[C_ROOTS];
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t R = q.R, n_roots = q.ctr[C_ROOTS], nw = 21u * R / 2u;
     const uint64_t VV = (uint64_t)q.V * q.V;
-    for (uint32_t ri = blockIdx.x; ri < n_roots; ri += gridDim.x) {
+    const uint32_t r0 = lane, r1 = lane + 32;
+    for (uint32_t ri = warp; ri < n_roots; ri += nwarps) {
         const uint32_t c = q.roots[ri];
-        const uint32_t ni = q.item_cnt[c];
-        for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) {
-            uint64_t acc = 0;
-            if (ni == 0) {
-                const uint32_t lo = q.off[c], hi = lo + q.count[c];
-                for (uint32_t m = lo; m < hi; ++m) {
-                    const uint64_t* cube = reinterpret_cast<const uint64_t*>(q.s.cube(q.members[m], q.round));
-                    acc ^= __ldg(cube + w);
+        const uint32_t cnt = q.count[c];
+        const bool big = cnt > q.M;
+        uint64_t a0[GZ_COLS], a1[GZ_COLS];
+        uint32_t g0[GZ_COLS], g1[GZ_COLS];
+#pragma unroll
+        for (int j = 0; j < GZ_COLS; ++j) {
+            a0[j] = a1[j] = 0;
+            g0[j] = g1[j] = 0;
+        }
+        const uint32_t nsrc = big ? 1u : cnt;
+        const uint32_t my_node = (!big && lane < cnt) ? q.members[q.off[c] + lane] : 0u;
+        uint64_t* slot_base = big ? q.acc + (uint64_t)q.slot[c] * nw : nullptr;
+        for (uint32_t sidx = 0; sidx < nsrc; ++sidx) {
+            const uint64_t* A;
+            if (big) A = slot_base;
+            else A = reinterpret_cast<const uint64_t*>(q.s.cube(__shfl_sync(0xffffffffu, my_node, sidx), q.round));
+            const uint32_t* G = reinterpret_cast<const uint32_t*>(A + GZ_COLS * R);
+#pragma unroll
+            for (int j = 0; j < GZ_COLS; ++j) {
+                if (r0 < R) {
+                    a0[j] ^= A[r0 * GZ_COLS + j];
+                    g0[j] ^= G[r0 * GZ_COLS + j];
                 }
-            } else {
-                const uint32_t b = q.item_base[c];
-                for (uint32_t it = b; it < b + ni; ++it) acc ^= q.partial[(uint64_t)it * nw + w];
-            }
-            S[w] = acc;
-        }
-        if (threadIdx.x == 0) s_best = 0xffffffffu;
-        __syncthreads();
-        // nested rows: row i = XOR of exact rows i..R-1 (one thread per column)
-        if (threadIdx.x < GZ_COLS) {
-            const uint32_t j = threadIdx.x;
-            for (int row = (int)R - 2; row >= 0; --row) {
-                A[row * GZ_COLS + j] ^= A[(row + 1) * GZ_COLS + j];
-                G[row * GZ_COLS + j] ^= G[(row + 1) * GZ_COLS + j];
+                if (r1 < R) {
+                    a1[j] ^= A[r1 * GZ_COLS + j];
+                    g1[j] ^= G[r1 * GZ_COLS + j];
+                }
             }
         }
-        __syncthreads();
+        if (big) {  // clear the slot for the next round (each word is read by its own lane only)
+            uint32_t* G = reinterpret_cast<uint32_t*>(slot_base + GZ_COLS * R);
+#pragma unroll
+            for (int j = 0; j < GZ_COLS; ++j) {
+                if (r0 < R) {
+                    slot_base[r0 * GZ_COLS + j] = 0;
+                    G[r0 * GZ_COLS + j] = 0;
+                }
+                if (r1 < R) {
+                    slot_base[r1 * GZ_COLS + j] = 0;
+                    G[r1 * GZ_COLS + j] = 0;
+                }
+            }
+        }
         bool nz = false;
-        uint32_t best = 0xffffffffu;
-        for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
-            const uint32_t row = b / GZ_COLS, j = b - row * GZ_COLS;
-            const uint64_t a = A[b];
-            const uint32_t g = G[b];
-            if ((a | g) == 0) continue;
-            nz = true;
-            if (g != checksum(q.kc[q.round * GZ_COLS + j], a) || a >= VV) continue;
-            const uint32_t uu = (uint32_t)(a / q.V), vv = (uint32_t)(a % q.V);
-            if (uu >= vv) continue;
-            const bool in_u = q.label[uu] == c, in_v = q.label[vv] == c;
-            if (in_u == in_v) continue;
-            best = min(best, j * R + row);
+        int64_t result = -1;  // warp-uniform
+#pragma unroll
+        for (int j = 0; j < GZ_COLS; ++j) {
+            if (result >= 0) continue;
+            uint64_t x0 = a0[j], x1 = a1[j];
+            uint32_t y0 = g0[j], y1 = g1[j];
+            // suffix XOR over rows, within each half of the warp's rows
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint64_t t1 = shfl_down64(x1, off);
+                const uint32_t u1 = __shfl_down_sync(0xffffffffu, y1, off);
+                const uint64_t t0 = shfl_down64(x0, off);
+                const uint32_t u0 = __shfl_down_sync(0xffffffffu, y0, off);
+                if (lane + off < 32) {
+                    x1 ^= t1;
+                    y1 ^= u1;
+                    x0 ^= t0;
+                    y0 ^= u0;
+                }
+            }
+            // rows 0..31 also take every row from 32 on
+            const uint64_t carry_a = ((uint64_t)__shfl_sync(0xffffffffu, (uint32_t)(x1 >> 32), 0) << 32) |
+                                     __shfl_sync(0xffffffffu, (uint32_t)x1, 0);
+            const uint32_t carry_g = __shfl_sync(0xffffffffu, y1, 0);
+            x0 ^= carry_a;
+            y0 ^= carry_g;
+            const uint64_t kcj = q.kc[q.round * GZ_COLS + j];
+            auto good = [&](uint64_t a, uint32_t g, uint32_t row) -> bool {
+                if (row >= R || (a | g) == 0) return false;
+                if (g != checksum(kcj, a) || a >= VV) return false;
+                const uint32_t uu = (uint32_t)(a / q.V), vv = (uint32_t)(a % q.V);
+                if (uu >= vv) return false;
+                return (q.label[uu] == c) != (q.label[vv] == c);
+            };
+            nz |= __any_sync(0xffffffffu, (r0 < R && (x0 | y0)) || (r1 < R && (x1 | y1))) != 0;
+            const uint32_t b0 = __ballot_sync(0xffffffffu, good(x0, y0, r0));
+            const uint32_t b1 = __ballot_sync(0xffffffffu, good(x1, y1, r1));
+            if (b0 | b1) {
+                const uint32_t src = b0 ? (uint32_t)(__ffs(b0) - 1) : (uint32_t)(__ffs(b1) - 1);
+                const uint64_t pick = b0 ? x0 : x1;
+                result = (int64_t)(((uint64_t)__shfl_sync(0xffffffffu, (uint32_t)(pick >> 32), src) << 32) |
+                                   __shfl_sync(0xffffffffu, (uint32_t)pick, src));
+            }
         }
-        for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
-        if ((threadIdx.x & 31) == 0 && best != 0xffffffffu) atomicMin(&s_best, best);
-        const int any_nz = __syncthreads_or(nz);
-        if (threadIdx.x == 0) {
-            const uint32_t bb = s_best;
+        if (lane == 0) {
             int64_t r;
-            if (bb != 0xffffffffu) {
-                const uint32_t j = bb / R, row = bb - j * R;
-                r = (int64_t)A[row * GZ_COLS + j];
+            if (result >= 0) {
+                r = result;
                 atomicAdd(&q.ctr[C_EDGES], 1u);
-            } else if (any_nz) {
+            } else if (nz) {
                 r = -2;
                 atomicAdd(&q.ctr[C_FAILS], 1u);
             } else {
@@ -208,7 +305,6 @@ __global__ void __launch_bounds__(256) k_q_sample(QArgs q) {
             q.res[c] = r;
             if (q.trace) q.trace[(uint64_t)q.round * q.V + c] = r;
         }
-        __syncthreads();
     }
 }
 
@@ -277,9 +373,19 @@ __global__ void k_q_forest_advance(QArgs q, const uint32_t* pos) {
     q.ctr[C_FOREST] += pos[q.V];
 }
 
-__global__ void k_q_relabel(QArgs q) {
+// new component of every old root (its set's minimum vertex id) ...
+__global__ void k_q_newroot(QArgs q, uint32_t* newroot) {
+    const uint32_t n_roots = q.ctr[C_ROOTS];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_roots; i += gridDim.x * blockDim.x) {
+        const uint32_t c = q.roots[i];
+        newroot[c] = dsu_find(q.parent, c);
+    }
+}
+
+// ... then every vertex follows its old root
+__global__ void k_q_relabel(QArgs q, const uint32_t* newroot) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < q.V; v += gridDim.x * blockDim.x)
-        q.label[v] = dsu_find(q.parent, q.label[v]);
+        q.label[v] = newroot[q.label[v]];
 }
 
 __global__ void k_q_ncc(QArgs q) {
@@ -295,25 +401,21 @@ __global__ void k_q_ncc(QArgs q) {
 gz_status query_setup(gz_handle* h) {
     if (h->query_ready) return GZ_OK;
     const size_t V = h->V;
-    h->q_M_members = 64;
-    h->q_items_cap = (uint32_t)(2 * V / h->q_M_members + 2);
+    h->q_slots_cap = query_slots(h->V);
     auto alloc32 = [&](uint32_t** p, size_t n) { return cudaMallocAsync(p, n * sizeof(uint32_t), h->stream); };
     cudaError_t e = cudaSuccess;
     uint32_t** arrs[] = {&h->q_label, &h->q_parent, &h->q_members, &h->q_roots, &h->q_target,
-                         &h->q_item_base, &h->q_item_cnt, &h->q_F, &h->q_F2, &h->q_M, &h->q_M2,
+                         &h->q_slot, &h->q_F, &h->q_F2, &h->q_M, &h->q_M2,
                          &h->q_flag, &h->q_cursor};
     for (auto p : arrs)
         if (e == cudaSuccess) e = alloc32(p, V);
     if (e == cudaSuccess) e = alloc32(&h->q_count, V + 1);
     if (e == cudaSuccess) e = alloc32(&h->q_off, V + 1);
     if (e == cudaSuccess) e = alloc32(&h->q_pos, V + 1);
-    if (e == cudaSuccess) e = alloc32(&h->q_item_comp, h->q_items_cap);
-    if (e == cudaSuccess) e = alloc32(&h->q_item_lo, h->q_items_cap);
-    if (e == cudaSuccess) e = alloc32(&h->q_item_hi, h->q_items_cap);
     if (e == cudaSuccess) e = alloc32(&h->q_forest, 2 * V);
     if (e == cudaSuccess) e = alloc32(&h->q_ctr, C_N);
     if (e == cudaSuccess) e = cudaMallocAsync(&h->q_res, V * sizeof(int64_t), h->stream);
-    if (e == cudaSuccess) e = cudaMallocAsync(&h->q_partial, (size_t)h->q_items_cap * h->per_k_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&h->q_acc, (size_t)h->q_slots_cap * h->per_k_bytes, h->stream);
     if (e == cudaSuccess) {
         h->h_ctr = new (std::nothrow) uint32_t[C_N];
         if (!h->h_ctr) return set_error(h, GZ_ENOMEM, "query counters");
@@ -347,7 +449,7 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
     q.V = h->V;
     q.K = h->K;
     q.R = h->R;
-    q.M = h->q_M_members;
+    q.M = kMergeChunk;
     q.label = h->q_label;
     q.parent = h->q_parent;
     q.count = h->q_count;
@@ -356,39 +458,41 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
     q.members = h->q_members;
     q.roots = h->q_roots;
     q.target = h->q_target;
-    q.item_base = h->q_item_base;
-    q.item_cnt = h->q_item_cnt;
-    q.item_comp = h->q_item_comp;
-    q.item_lo = h->q_item_lo;
-    q.item_hi = h->q_item_hi;
-    q.partial = reinterpret_cast<uint64_t*>(h->q_partial);
+    q.slot = h->q_slot;
+    q.acc = h->q_acc;
     q.res = h->q_res;
     q.trace = h->trace ? h->q_trace : nullptr;
     q.ctr = h->q_ctr;
 
     const uint32_t V = h->V, tpb = 256;
     const uint32_t gV = grid_for(h, V, tpb);
-    k_q_init<<<gV, tpb, 0, stm>>>(h->q_label, h->q_parent, V);
+    k_q_init<<<gV, tpb, 0, stm>>>(q);
     h->launches += 2 + (q.trace ? 1 : 0);  // init, final count (+ trace fill)
     if (q.trace) k_fill64<<<grid_for(h, (uint64_t)h->K * V, tpb), tpb, 0, stm>>>(q.trace, (uint64_t)h->K * V, -4);
-    cudaError_t e = cudaMemsetAsync(h->q_ctr, 0, C_N * sizeof(uint32_t), stm);
+    cudaError_t e = cudaMemsetAsync(h->q_ctr + C_EDGES, 0, (C_N - C_EDGES) * sizeof(uint32_t), stm);
+    // the sampler clears every slot it reads; this only guards against a query
+    // that stopped on an error between a merge and its sampler
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->q_acc, 0, (size_t)h->q_slots_cap * h->per_k_bytes, stm);
     if (e != cudaSuccess) return cuda_check(h, e, "memset counters");
 
-    const size_t sample_smem = (size_t)h->per_k_bytes;
     uint32_t rounds = 0, fails_last = 0, fails_total = 0, exhausted = 0;
     for (uint32_t r = 0; r < h->K; ++r) {
         q.round = r;
         rounds = r + 1;
-        e = cudaMemsetAsync(h->q_count, 0, (size_t)(V + 1) * sizeof(uint32_t), stm);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->q_ctr, 0, 4 * sizeof(uint32_t), stm);  // roots..fails
-        if (e != cudaSuccess) return cuda_check(h, e, "memset round");
-        k_q_count<<<gV, tpb, 0, stm>>>(q);
-        launch_scan(h->q_count, h->q_off, h->q_cursor, V, stm, h->d_scan_tmp);
-        k_q_group<<<gV, tpb, 0, stm>>>(q);
-        k_q_roots<<<gV, tpb, 0, stm>>>(q);
-        k_q_merge_items<<<h->sm_count * 4, 384, 0, stm>>>(q);
-        k_q_sample<<<h->sm_count * 16, 256, sample_smem, stm>>>(q);
-        h->launches += 7;
+        if (r > 0) {
+            // group vertices by component (round 0 starts from singletons)
+            e = cudaMemsetAsync(h->q_count, 0, (size_t)(V + 1) * sizeof(uint32_t), stm);
+            if (e == cudaSuccess) e = cudaMemsetAsync(h->q_ctr, 0, 4 * sizeof(uint32_t), stm);  // roots..fails
+            if (e != cudaSuccess) return cuda_check(h, e, "memset round");
+            k_q_count<<<gV, tpb, 0, stm>>>(q);
+            launch_scan(h->q_count, h->q_off, h->q_cursor, V, stm, h->d_scan_tmp);
+            k_q_group<<<gV, tpb, 0, stm>>>(q);
+            k_q_roots<<<gV, tpb, 0, stm>>>(q);
+            k_q_merge<<<std::min<uint32_t>((V + kMergeChunk - 1) / kMergeChunk, h->sm_count * 5), 384, 0, stm>>>(q);
+            h->launches += 6;
+        }
+        k_q_sample<<<h->sm_count * 16, 256, 0, stm>>>(q);
+        h->launches += 1;
         e = cudaMemcpyAsync(h->h_ctr, h->q_ctr, C_N * sizeof(uint32_t), cudaMemcpyDeviceToHost, stm);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stm);
         if (e != cudaSuccess) return cuda_check(h, e, "query round");
@@ -418,7 +522,9 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
             k_q_forest_advance<<<1, 1, 0, stm>>>(q, h->q_pos);
             h->launches += J + 7;
         }
-        k_q_relabel<<<gV, tpb, 0, stm>>>(q);
+        k_q_newroot<<<grid_for(h, n_roots, tpb), tpb, 0, stm>>>(q, h->q_cursor);
+        k_q_relabel<<<gV, tpb, 0, stm>>>(q, h->q_cursor);
+        h->launches += 1;
     }
     k_q_ncc<<<gV, tpb, 0, stm>>>(q);
     e = cudaMemcpyAsync(h->h_ctr, h->q_ctr, C_N * sizeof(uint32_t), cudaMemcpyDeviceToHost, stm);

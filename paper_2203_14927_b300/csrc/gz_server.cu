@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "../../include/gz.h"
+#include "gz_handle.cuh"
 
 namespace {
 
@@ -82,12 +83,12 @@ namespace {
 uint64_t graph_bytes(uint32_t V, const gz_config* cfg) {
     size_t b = 0;
     gz_memory_bytes(V, cfg, &b);
-    // query scratch (labels, parents, members, ... and partial XORs) and the
-    // host-input staging buffers
+    // query scratch (labels, parents, members, ... and the merge accumulators)
+    // and the host-input staging buffers
     uint32_t K = 0, R = 0;
     gz_geometry(V, &K, &R);
     const uint32_t cl = cfg && cfg->chunk_log2 ? cfg->chunk_log2 : 24;
-    return b + (uint64_t)V * 96 + (2ull * V / 64 + 2) * 84ull * R + (4ull << cl) * 4;
+    return b + (uint64_t)V * 96 + (uint64_t)gz::query_slots(V) * 84ull * R + (4ull << cl) * 4;
 }
 
 // pick under the lock: a resident idle graph or an admissible waiting one,
