@@ -122,6 +122,18 @@ gz_status gz_set_stream(gz_handle *h, void *stream);
 gz_status gz_edge_update(gz_handle *h, const uint32_t *u, const uint32_t *v,
                          size_t n, int on_device);
 
+/* The same updates given as packed edge indices: idx[i] = min(u,v)*V +
+ * max(u,v), the coordinate of edge {u,v} in the node vectors of Section 3.1.
+ *   idx        : n u64 indices; host memory if on_device == 0, else device
+ *                memory (8-byte aligned).
+ *   Validation : an index that is not canonical (min >= max, so also a self
+ *                loop, or idx >= V^2) invalidates its batch, with the same
+ *                batches, discard rule and deferred GZ_EINVAL report as
+ *                gz_edge_update.
+ *   Ownership  : as gz_edge_update.  The first call allocates a decode
+ *                buffer of 8 * 2^chunk_log2 bytes on the device. */
+gz_status gz_edge_update_idx(gz_handle *h, const uint64_t *idx, size_t n, int on_device);
+
 /* Wait for all queued work of the handle; returns GZ_EINVAL once if a batch
  * was rejected since the last report. */
 gz_status gz_sync(gz_handle *h);
@@ -332,6 +344,14 @@ gz_status gz_sketch_update_noalloc(void *sketch, uint32_t V, uint64_t seed,
 const char *gz_last_error(gz_handle *h);
 
 /* Library version string. */
+/* Measured integer throughput of the current device, the ceiling of the
+ * batched update kernel (its work per (record, column) pair is integer only):
+ * kind 0 = 32-bit multiply-add, 1 = three-input logic op, 2 = the two
+ * interleaved.  *ops_per_s = thread-instructions per second over all SMs, the
+ * best of nine timed launches of some tens of milliseconds each (after one untimed).  Synchronous;
+ * uses its own stream and a 4-byte device allocation. */
+gz_status gz_int_peak(int kind, double *ops_per_s);
+
 const char *gz_version(void);
 
 #ifdef __cplusplus

@@ -105,6 +105,8 @@ _SIGNATURES = {
     "gz_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gz_edge_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                       ctypes.c_int]),
+    "gz_edge_update_idx": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]),
+    "gz_int_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p]),
     "gz_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "gz_reset": (ctypes.c_int, [ctypes.c_void_p]),
     "gz_connected_components": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -173,21 +175,35 @@ def geometry(V: int) -> tuple[int, int]:
     return K.value, R.value
 
 
-def _buffer(x):
-    """(pointer, n, on_device, keepalive) of a 1-D uint32/int32 array."""
+def int_peak(kind: str = "mixed") -> float:
+    """Measured integer thread-instructions/s of the current device
+    (gz_int_peak): "imad" (32-bit multiply-add), "lop3" (logic) or "mixed"."""
+    out = ctypes.c_double()
+    k = {"imad": 0, "lop3": 1, "mixed": 2}[kind]
+    st = lib().gz_int_peak(k, ctypes.byref(out))
+    if st != GZ_OK:
+        raise GzError(st, "gz_int_peak failed")
+    return out.value
+
+
+def _buffer(x, bits: int = 32):
+    """(pointer, n, on_device, keepalive) of a 1-D unsigned/signed integer
+    array of the given width (32 for vertex ids, 64 for packed indices)."""
     try:
         import torch
     except ImportError:  # pragma: no cover
         torch = None
     if torch is not None and isinstance(x, torch.Tensor):
-        if x.dtype not in (torch.int32, torch.uint32):
-            raise TypeError("update tensors must be int32 or uint32")
+        ok = (torch.int32, torch.uint32) if bits == 32 else (torch.int64, torch.uint64)
+        if x.dtype not in ok:
+            raise TypeError(f"update tensors must be int{bits} or uint{bits}")
         x = x.contiguous().reshape(-1)
         return x.data_ptr(), x.numel(), 1 if x.is_cuda else 0, x
     a = np.asarray(x)
-    if a.dtype == np.int32 and a.flags["C_CONTIGUOUS"]:
-        a = a.view(np.uint32)  # same bytes, no copy (keeps pinned memory pinned)
-    a = np.ascontiguousarray(a, dtype=np.uint32).reshape(-1)
+    signed, unsigned = (np.int32, np.uint32) if bits == 32 else (np.int64, np.uint64)
+    if a.dtype == signed and a.flags["C_CONTIGUOUS"]:
+        a = a.view(unsigned)  # same bytes, no copy (keeps pinned memory pinned)
+    a = np.ascontiguousarray(a, dtype=unsigned).reshape(-1)
     return a.ctypes.data, a.size, 0, a
 
 
@@ -264,6 +280,12 @@ class Graph:
         self._check(lib().gz_edge_update(self._h, ctypes.c_void_p(pu), ctypes.c_void_p(pv), nu, du),
                     "gz_edge_update")
         return ku, kv
+
+    def edge_update_idx(self, idx):
+        """Updates as packed indices min(u,v)*V + max(u,v) (int64/uint64)."""
+        p, n, d, k = _buffer(idx, 64)
+        self._check(lib().gz_edge_update_idx(self._h, ctypes.c_void_p(p), n, d), "gz_edge_update_idx")
+        return k
 
     def sync(self):
         self._check(lib().gz_sync(self._h), "gz_sync")

@@ -175,7 +175,7 @@ gz_status gz_destroy(gz_handle* h) {
                     h->q_cursor, h->q_members, h->q_roots, h->q_target, h->q_slot,
                     h->q_F, h->q_F2,
                     h->q_M, h->q_M2, h->q_flag, h->q_pos, h->q_forest, h->q_ctr, h->q_res,
-                    h->q_acc, h->q_trace, h->d_stats, h->d_scan_tmp, h->d_tile_node};
+                    h->q_acc, h->q_trace, h->d_stats, h->d_scan_tmp, h->d_tile_node, h->d_decode};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, h->stream);
     delete[] h->h_ctr;
@@ -248,6 +248,49 @@ gz_status gz_edge_update(gz_handle* h, const uint32_t* u, const uint32_t* v, siz
         if (e != cudaSuccess) return cuda_check(h, e, "update event");
     }
     // the caller may reuse its host buffers once every copy has landed
+    e = cudaStreamSynchronize(h->copy_stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "update sync");
+    return GZ_OK;
+}
+
+gz_status gz_edge_update_idx(gz_handle* h, const uint64_t* idx, size_t n, int on_device) {
+    if (!h) return GZ_EINVAL;
+    if (n == 0) return GZ_OK;
+    if (!idx) return set_error(h, GZ_EINVAL, "null index array");
+    cudaError_t e = cudaSuccess;
+    if (!h->d_decode) {
+        e = cudaMallocAsync(&h->d_decode, (size_t)2 * h->chunk * 4, h->stream);
+        if (e != cudaSuccess) return cuda_check(h, e, "decode buffer");
+    }
+    uint32_t* du = h->d_decode;
+    uint32_t* dv = du + h->chunk;
+    gz_status s;
+    if (on_device) {
+        for (size_t off = 0; off < n; off += h->chunk) {
+            const uint64_t m = std::min<uint64_t>(h->chunk, n - off);
+            if ((s = decode_idx(h, idx + off, m, du, dv)) != GZ_OK) return s;
+            if ((s = ingest_batch(h, du, dv, m)) != GZ_OK) return s;
+        }
+        return GZ_OK;
+    }
+    // Host input: the packed chunk (8 bytes per update) fills one staging
+    // buffer; it is free again once decoded.
+    if ((s = host_path_setup(h)) != GZ_OK) return s;
+    size_t i = 0;
+    for (size_t off = 0; off < n; off += h->chunk, ++i) {
+        const uint64_t m = std::min<uint64_t>(h->chunk, n - off);
+        const int b = (int)(i & 1);
+        uint64_t* sb = reinterpret_cast<uint64_t*>(h->d_stage + (size_t)b * 2 * h->chunk);
+        e = cudaStreamWaitEvent(h->copy_stream, h->ev_free[b], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sb, idx + off, m * 8, cudaMemcpyHostToDevice, h->copy_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_copied[b], h->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0);
+        if (e != cudaSuccess) return cuda_check(h, e, "update copy");
+        if ((s = decode_idx(h, sb, m, du, dv)) != GZ_OK) return s;
+        e = cudaEventRecord(h->ev_free[b], h->stream);
+        if (e != cudaSuccess) return cuda_check(h, e, "update event");
+        if ((s = ingest_batch(h, du, dv, m)) != GZ_OK) return s;
+    }
     e = cudaStreamSynchronize(h->copy_stream);
     if (e != cudaSuccess) return cuda_check(h, e, "update sync");
     return GZ_OK;

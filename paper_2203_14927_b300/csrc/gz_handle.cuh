@@ -34,6 +34,7 @@ struct gz_handle {
     uint32_t* d_records = nullptr; // 2*chunk
     uint32_t* d_tile_node = nullptr; // first node of every record tile (2*chunk/tile + 2)
     uint32_t* d_stage = nullptr;   // 2 buffers x (u, v) x chunk, host-input staging (lazy)
+    uint32_t* d_decode = nullptr;  // (u, v) x chunk decoded from packed indices (lazy)
     cudaStream_t copy_stream = nullptr;  // H2D copies of host input (lazy)
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
     uint32_t* d_flags = nullptr;   // [0] batch invalid, [1] work counter, [2] sticky invalid
@@ -84,6 +85,8 @@ gz_status cuda_check(gz_handle* h, cudaError_t e, const char* what);
 // ingestion (gz_ingest.cu)
 gz_status ingest_setup(gz_handle* h);
 gz_status ingest_batch(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, uint64_t n);
+// packed indices min*V+max -> (u, v); non-canonical indices become (0, 0)
+gz_status decode_idx(gz_handle* h, const uint64_t* d_idx, uint64_t n, uint32_t* d_u, uint32_t* d_v);
 gz_status export_nested(gz_handle* h, uint32_t lo, uint32_t hi, uint64_t* d_alpha,
                         uint32_t* d_gamma);
 

@@ -743,6 +743,35 @@ static gz_status launch_graph(gz_handle* h, const uint32_t* d_u, const uint32_t*
     return cuda_check(h, cudaGraphLaunch(h->graph_exec, h->stream), "cudaGraphLaunch");
 }
 
+// Packed edge index -> endpoints: idx = min*V + max, the coordinate of edge
+// {min, max} in the characteristic vector of Section 3.1.  A non-canonical
+// index (min >= max, or idx >= V^2) decodes to the self loop (0, 0), which
+// the validation of its batch then rejects.
+__global__ void k_decode_idx(const uint64_t* __restrict__ idx, uint64_t n, uint32_t V,
+                             uint32_t* __restrict__ u, uint32_t* __restrict__ v) {
+    const uint64_t VV = (uint64_t)V * V;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = idx[i];
+        uint32_t a = 0, b = 0;
+        if (x < VV) {
+            a = (uint32_t)(x / V);
+            b = (uint32_t)(x - (uint64_t)a * V);
+            if (a >= b) a = b = 0;
+        }
+        u[i] = a;
+        v[i] = b;
+    }
+}
+
+gz_status decode_idx(gz_handle* h, const uint64_t* d_idx, uint64_t n, uint32_t* d_u, uint32_t* d_v) {
+    if (n == 0) return GZ_OK;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>((n + 255) / 256, (uint64_t)h->sm_count * 8);
+    k_decode_idx<<<grid, 256, 0, h->stream>>>(d_idx, n, h->V, d_u, d_v);
+    h->launches += 1;
+    return cuda_check(h, cudaGetLastError(), "decode launch");
+}
+
 gz_status ingest_batch(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, uint64_t n) {
     if (n == 0) return GZ_OK;
     cudaStream_t st = h->stream;

@@ -233,3 +233,36 @@ def test_checkpoint_restore_resumes_exactly():
         gz.Graph.restore(bad)
     with pytest.raises(gz.GzError):
         gz.Graph.restore(ck[: len(ck) - 1])
+
+
+@pytest.mark.parametrize("on_device", [True, False])
+def test_packed_index_updates_match_oracle(on_device):
+    # gz_edge_update_idx: idx = min*V + max, several chunks and a ragged tail,
+    # both endpoint orders in the source stream (the packed form is canonical)
+    import torch
+    V = 3000
+    u, v = S.random_stream(V, 7000, seed=9, n_distinct=2500)
+    lo, hi = np.minimum(u, v).astype(np.uint64), np.maximum(u, v).astype(np.uint64)
+    idx = lo * np.uint64(V) + hi
+    A, G = oracle.ingest(V, 17, u, v)
+    g = gz.Graph(V, 17, chunk_log2=11)
+    if on_device:
+        g.edge_update_idx(torch.from_numpy(idx.view(np.int64)).cuda())
+    else:
+        g.edge_update_idx(idx)
+    g.sync()
+    _assert_same_sketches(g, A, G)
+
+
+def test_packed_index_rejects_non_canonical():
+    V = 50
+    u, v = S.random_stream(V, 400, seed=4)
+    g = _gpu_graph(V, 3, u, v)
+    before = g.export_sketch()
+    for bad in ([1 * V + 2, 7 * V + 3], [5 * V + 5], [V * V], [2 ** 63 + 1]):  # max<min, loop, >= V^2
+        g.edge_update_idx(np.array([3 * V + 4] + bad, np.uint64))
+        with pytest.raises(gz.GzError) as ei:
+            g.sync()
+        assert ei.value.status == gz.GZ_EINVAL
+    after = g.export_sketch()
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
