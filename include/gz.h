@@ -182,8 +182,9 @@ gz_status gz_export_sketch(gz_handle *h, uint32_t node_lo, uint32_t node_hi,
 
 /* Checkpoint / resume.  By linearity the node sketches are the whole state of
  * a graph (Section 2.2: the stream is summarised by them), so a checkpoint is
- * a 64-byte header -- magic "GZB3CKP1", version, V, K, R, seed, bytes per node
- * sketch -- followed by the raw sketch array (exact-depth layout).  Both calls
+ * a 64-byte header -- magic "GZB3CKP1", version (2), V, K, R, seed, bytes per
+ * node sketch -- followed by the raw sketch array (the device form of
+ * gz_info).  Both calls
  * are synchronous; buf is host memory owned by the caller.
  *   gz_checkpoint_bytes: size a checkpoint of h needs.
  *   gz_checkpoint      : write it (GZ_EINVAL if size is too small, or if a
@@ -195,9 +196,13 @@ gz_status gz_checkpoint(gz_handle *h, void *buf, size_t size);
 gz_status gz_restore(const void *buf, size_t size, const gz_config *cfg, void *stream,
                      gz_handle **out);
 
-/* Geometry and device pointer of the raw sketch array of a handle (exact-
- * depth form, layout per node: for each k, alpha[row][j] then gamma[row][j]).
- * Any output pointer may be NULL. */
+/* Geometry and device pointer of the raw sketch array of a handle.  Device
+ * form: exact-depth rows (an index is XORed into the one row of its depth; the
+ * paper's nested row i is the XOR of rows i..R-1), layout per node: for each
+ * k, alpha[row][j] (u64) then gamma'[row][j] (u32), where gamma' keeps the
+ * checksum sums before MurmurHash3's final step g ^= g >> 16 (a linear map, so
+ * a bucket's checksum sum is gamma' ^ (gamma' >> 16)).  Any output pointer may
+ * be NULL. */
 gz_status gz_info(gz_handle *h, uint32_t *V, uint32_t *K, uint32_t *R,
                   size_t *node_bytes, void **sketch_device);
 
@@ -315,9 +320,9 @@ const char *gz_server_last_error(gz_server *s);
  * gz_edge_update but allocates and frees nothing: its scratch is a fixed
  * array of about 10 MB in the library's static device memory, which every GPU
  * that loads the library holds until the process exits.
- *   sketch : device, V*K*84*R bytes of node sketches in the handle layout
- *            (exact-depth rows; per node, for each k, alpha[R][7] u64 then
- *            gamma[R][7] u32), zeroed for the empty graph; e.g. the array of
+ *   sketch : device, V*K*84*R bytes of node sketches in the device form of
+ *            gz_info (per node, for each k, alpha[R][7] u64 then
+ *            gamma'[R][7] u32), zeroed for the empty graph; e.g. the array of
  *            a handle from gz_info, or memory the caller owns.
  *   V, seed: vertex count (2 <= V <= GZ_NOALLOC_MAX_V) and the hash seed the
  *            sketches were built with.

@@ -443,7 +443,7 @@ gz_status gz_checkpoint(gz_handle* h, void* buf, size_t size) {
     CkptHeader hd;
     std::memset(&hd, 0, sizeof(hd));
     std::memcpy(hd.magic, kMagic, 8);
-    hd.version = 1;
+    hd.version = 2;  // 2: gamma words hold gamma' (checksum sums before the final xorshift)
     hd.V = h->V;
     hd.K = h->K;
     hd.R = h->R;
@@ -462,7 +462,7 @@ gz_status gz_restore(const void* buf, size_t size, const gz_config* cfg, void* s
     CkptHeader hd;
     std::memcpy(&hd, buf, sizeof(hd));
     uint32_t K, R;
-    if (std::memcmp(hd.magic, kMagic, 8) != 0 || hd.version != 1 || !gz::geometry(hd.V, &K, &R) ||
+    if (std::memcmp(hd.magic, kMagic, 8) != 0 || hd.version != 2 || !gz::geometry(hd.V, &K, &R) ||
         K != hd.K || R != hd.R || hd.node_bytes != (uint64_t)K * 84u * R ||
         size < sizeof(hd) + (size_t)hd.V * hd.node_bytes)
         return GZ_EINVAL;

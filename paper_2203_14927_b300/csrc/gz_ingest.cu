@@ -187,7 +187,7 @@ __global__ void k_tile_nodes(const uint32_t* __restrict__ offsets, uint32_t V, u
 struct ColKey {
     uint32_t a_lo, a_hi;
     uint64_t b;
-    uint32_t c_lo;  // checksum key
+    uint32_t c_pre;  // t ^ (t >> 16) part of the checksum key: lo32(c) ^ (lo32(c) >> 16)
 };
 
 __device__ __forceinline__ ColKey make_colkey(uint64_t a, uint64_t b, uint64_t c) {
@@ -195,7 +195,7 @@ __device__ __forceinline__ ColKey make_colkey(uint64_t a, uint64_t b, uint64_t c
     k.a_lo = (uint32_t)a;
     k.a_hi = (uint32_t)(a >> 32);
     k.b = b;
-    k.c_lo = (uint32_t)c;
+    k.c_pre = (uint32_t)c ^ ((uint32_t)c >> 16);
     return k;
 }
 
@@ -208,9 +208,21 @@ __device__ __forceinline__ uint32_t depth_hi(const ColKey& k, uint32_t x_lo, uin
     return hi;
 }
 
-// checksum of a staged record; fold = fold32(idx), computed once per record
-__device__ __forceinline__ uint32_t checksum_w(const ColKey& k, uint32_t fold) {
-    return fmix32(fold ^ k.c_lo);
+// Per-record half of the checksum's first step: with f = fold32(idx) and
+// t = f ^ lo32(c), t ^ (t >> 16) = (f ^ (f >> 16)) ^ c_pre, so the record's
+// part is staged once and each column adds its key with one XOR.
+__device__ __forceinline__ uint32_t fold_pre(uint64_t idx) {
+    const uint32_t f = fold32(idx);
+    return f ^ (f >> 16);
+}
+
+// stored checksum gamma' of a staged record (= checksum_pre(c, idx))
+__device__ __forceinline__ uint32_t checksum_w(const ColKey& k, uint32_t fpre) {
+    uint32_t h = fpre ^ k.c_pre;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    return h;
 }
 
 // cp.async (16-byte granules, L2 only): global -> shared without a register
@@ -229,13 +241,15 @@ __device__ __forceinline__ void cp_async_wait() {
 // One CTA = 32*ceil(7K/32) threads; thread c owns CubeSketch column c = 7k + j
 // (one "Graph Worker" per column; no two threads write one bucket).
 // Dynamic shared memory:
-//   delta planes: kAtomic: alpha lo, alpha hi, gamma (u32 each, RC = Rs*CP
-//                 slots); else alpha (u64) and gamma (u32).  Slot of (row d,
-//                 column c) = (c/32)*Rs*32 + d*32 + c%32: a warp's 32 lanes
-//                 hit 32 distinct banks whatever rows they update, and a row
-//                 step is a shift, not a multiply.
+//   delta rows: one 96-word block per (warp of columns, row d < Rs), warp w's
+//               block of row d at word (w*Rs + d)*96.  kAtomic: alpha lo,
+//               alpha hi, gamma' as three 32-word planes at +0, +32, +64;
+//               else alpha as 32 u64 (+0) and gamma' (+64).  A warp's 32 lanes
+//               hit 32 distinct banks whatever rows they update, and the three
+//               words of a column update share one address register.
 //   raw records  [2][tile] u32, filled by cp.async one tile ahead
-//   staged records [tile] (kWide: uint4 {idx_lo, idx_hi, fold32(idx), 0}; else u32 idx)
+//   staged records [tile] (kWide: uint4 {idx_lo, idx_hi, fold_pre, 0};
+//                  else uint2 {idx, fold_pre})
 //   per-k deepest touched row [K] u32
 // Tiles (equal record counts) are claimed from an atomic counter one tile
 // ahead, so the next tile's records and first node are fetched while the
@@ -246,30 +260,21 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
     if (p.flags[0]) return;
     const uint32_t CP = blockDim.x, c = threadIdx.x;
     const uint32_t Rs = p.Rs, R = p.R, RC = Rs * CP, T = p.tile;
-    uint64_t* dA = smem;                                 // kAtomic == false
-    uint32_t* dAlo = reinterpret_cast<uint32_t*>(smem);  // kAtomic == true
-    uint32_t* dAhi = dAlo + RC;
-    uint32_t* dG = reinterpret_cast<uint32_t*>(smem + RC);
-    uint32_t* raw = dG + RC;  // [2][T], 16-byte aligned (RC multiple of 32, T multiple of 4)
+    uint32_t* sw = reinterpret_cast<uint32_t*>(smem);  // delta blocks, 3*RC words
+    uint32_t* raw = sw + 3 * RC;  // [2][T], 16-byte aligned (RC multiple of 32, T multiple of 4)
     uint32_t* stage = raw + 2 * T;
     uint4* stage4 = reinterpret_cast<uint4*>(stage);
-    uint32_t* maxd = stage + (kWide ? 4u : 1u) * T;
+    uint2* stage2 = reinterpret_cast<uint2*>(stage);
+    uint32_t* maxd = stage + (kWide ? 4u : 2u) * T;
 
     const bool active = c < p.ncol;
     const uint32_t k = c / GZ_COLS, j = c - k * GZ_COLS;
-    // slot of (row 0, column c); row d adds d*32
-    const uint32_t cbase = (c >> 5) * Rs * 32 + (c & 31);
+    // word of (row 0, column c) in plane 0; row d adds d*96
+    uint32_t* cw = sw + (c >> 5) * Rs * 96 + (c & 31);
+    uint64_t* ca = reinterpret_cast<uint64_t*>(sw + (c >> 5) * Rs * 96) + (c & 31);  // !kAtomic alpha
     ColKey key{};
     if (active) key = make_colkey(p.keys.a[c], p.keys.b[c], p.keys.c[c]);
-    for (uint32_t i = c; i < RC; i += CP) {
-        if (kAtomic) {
-            dAlo[i] = 0;
-            dAhi[i] = 0;
-        } else {
-            dA[i] = 0;
-        }
-        dG[i] = 0;
-    }
+    for (uint32_t i = c; i < 3 * RC; i += CP) sw[i] = 0;
     for (uint32_t i = c; i < p.K; i += CP) maxd[i] = 0;
     const uint32_t total = p.offsets[p.V];
     const uint32_t ntiles = (total + T - 1) / T;
@@ -328,22 +333,32 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                 for (uint32_t i = c; i < nseg; i += CP) {
                     const uint64_t idx = edge_index(x, rb[pos - lo + i], p.V);
                     if (kWide) {
-                        stage4[i] = make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), fold32(idx), 0u);
+                        stage4[i] = make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), fold_pre(idx), 0u);
                     } else {
-                        stage[i] = (uint32_t)idx;
+                        stage2[i] = make_uint2((uint32_t)idx, fold_pre(idx));
                     }
                 }
                 __syncthreads();
                 if (nseg < p.small_seg) {
                     // short segment: straight to global memory
                     if (active) {
-                        const uint64_t ka = p.keys.a[c], kb = p.keys.b[c], kc = p.keys.c[c];
+                        const uint64_t ka = p.keys.a[c], kb = p.keys.b[c];
                         for (uint32_t i = 0; i < nseg; ++i) {
-                            const uint64_t idx = kWide ? ((uint64_t)stage4[i].y << 32 | stage4[i].x) : stage[i];
+                            uint64_t idx;
+                            uint32_t fp;
+                            if (kWide) {
+                                const uint4 q = stage4[i];
+                                idx = (uint64_t)q.y << 32 | q.x;
+                                fp = q.z;
+                            } else {
+                                const uint2 q = stage2[i];
+                                idx = q.x;
+                                fp = q.y;
+                            }
                             const uint32_t d = exact_depth(depth_word(ka, kb, idx), R);
                             atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, d, j)),
                                       (unsigned long long)idx);
-                            atomicXor(p.s.gamma(x, k, d, j), checksum(kc, idx));
+                            atomicXor(p.s.gamma(x, k, d, j), checksum_w(key, fp));
                         }
                     }
                 } else {
@@ -351,14 +366,14 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                     if (active) {
                         // one column update staged in shared memory (d < Rs)
                         auto put = [&](uint32_t d, uint32_t xlo, uint32_t xhi, uint32_t g) {
-                            const uint32_t slot = cbase + (d << 5);
                             if (kAtomic) {
-                                atomicXor(dAlo + slot, xlo);
-                                if (kWide) atomicXor(dAhi + slot, xhi);
-                                atomicXor(dG + slot, g);
+                                uint32_t* w = cw + d * 96;
+                                atomicXor(w, xlo);
+                                if (kWide) atomicXor(w + 32, xhi);
+                                atomicXor(w + 64, g);
                             } else {
-                                dA[slot] ^= ((uint64_t)xhi << 32) | xlo;
-                                dG[slot] ^= g;
+                                ca[d * 48] ^= ((uint64_t)xhi << 32) | xlo;
+                                cw[d * 96 + 64] ^= g;
                             }
                         };
                         // a column update whose exact depth is Rs or more goes to HBM
@@ -374,32 +389,34 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                         // four records at a time in straight-line code, so the
                         // four hash chains interleave; one rare branch for deep rows
                         for (; i + 4 <= nseg; i += 4) {
-                            uint32_t xlo[4], xhi[4], fold[4];
+                            uint32_t xlo[4], xhi[4], fp[4];
                             if (kWide) {
 #pragma unroll
                                 for (int r = 0; r < 4; ++r) {
                                     const uint4 q = stage4[i + r];
                                     xlo[r] = q.x;
                                     xhi[r] = q.y;
-                                    fold[r] = q.z;
+                                    fp[r] = q.z;
                                 }
                             } else {
-                                const uint4 q = reinterpret_cast<const uint4*>(stage)[i >> 2];
-                                xlo[0] = q.x;
-                                xlo[1] = q.y;
-                                xlo[2] = q.z;
-                                xlo[3] = q.w;
+                                const uint4 q0 = reinterpret_cast<const uint4*>(stage2)[i >> 1];
+                                const uint4 q1 = reinterpret_cast<const uint4*>(stage2)[(i >> 1) + 1];
+                                xlo[0] = q0.x;
+                                fp[0] = q0.y;
+                                xlo[1] = q0.z;
+                                fp[1] = q0.w;
+                                xlo[2] = q1.x;
+                                fp[2] = q1.y;
+                                xlo[3] = q1.z;
+                                fp[3] = q1.w;
 #pragma unroll
-                                for (int r = 0; r < 4; ++r) {
-                                    xhi[r] = 0;
-                                    fold[r] = xlo[r];
-                                }
+                                for (int r = 0; r < 4; ++r) xhi[r] = 0;
                             }
                             uint32_t d[4], g[4];
 #pragma unroll
                             for (int r = 0; r < 4; ++r) {
                                 d[r] = __clz(depth_hi<kWide>(key, xlo[r], xhi[r]));
-                                g[r] = checksum_w(key, fold[r]);
+                                g[r] = checksum_w(key, fp[r]);
                             }
                             const uint32_t dmax = max(max(d[0], d[1]), max(d[2], d[3]));
                             if (dmax < Rs) {
@@ -419,19 +436,20 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                             }
                         }
                         for (; i < nseg; ++i) {
-                            uint32_t xlo, xhi, fold;
+                            uint32_t xlo, xhi, fp;
                             if (kWide) {
                                 const uint4 q = stage4[i];
                                 xlo = q.x;
                                 xhi = q.y;
-                                fold = q.z;
+                                fp = q.z;
                             } else {
-                                xlo = stage[i];
+                                const uint2 q = stage2[i];
+                                xlo = q.x;
                                 xhi = 0;
-                                fold = xlo;
+                                fp = q.y;
                             }
                             const uint32_t d = __clz(depth_hi<kWide>(key, xlo, xhi));
-                            const uint32_t g = checksum_w(key, fold);
+                            const uint32_t g = checksum_w(key, fp);
                             if (d < Rs) {
                                 put(d, xlo, xhi, g);
                                 md = max(md, d);
@@ -448,25 +466,25 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                         const uint32_t row = rem / GZ_COLS, jj = rem - row * GZ_COLS;
                         if (row <= maxd[kk]) {
                             const uint32_t col = kk * GZ_COLS + jj;
-                            const uint32_t slot = (col >> 5) * Rs * 32 + (row << 5) + (col & 31);
+                            uint32_t* w = sw + ((col >> 5) * Rs + row) * 96 + (col & 31);
                             uint64_t a;
                             if (kAtomic) {
-                                a = ((uint64_t)dAhi[slot] << 32) | dAlo[slot];
+                                a = ((uint64_t)w[32] << 32) | w[0];
                             } else {
-                                a = dA[slot];
+                                a = reinterpret_cast<uint64_t*>(w - (col & 31))[col & 31];
                             }
-                            const uint32_t g = dG[slot];
+                            const uint32_t g = w[64];
                             if (a | g) {
                                 atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, kk, row, jj)),
                                           (unsigned long long)a);
                                 atomicXor(p.s.gamma(x, kk, row, jj), g);
                                 if (kAtomic) {
-                                    dAlo[slot] = 0;
-                                    dAhi[slot] = 0;
+                                    w[0] = 0;
+                                    w[32] = 0;
                                 } else {
-                                    dA[slot] = 0;
+                                    reinterpret_cast<uint64_t*>(w - (col & 31))[col & 31] = 0;
                                 }
-                                dG[slot] = 0;
+                                w[64] = 0;
                             }
                         }
                     }
@@ -531,7 +549,7 @@ __global__ void __launch_bounds__(1024) k_plain(const uint32_t* __restrict__ u,
         const uint32_t a = u[i], b = v[i];
         const uint64_t idx = edge_index(a, b, V);
         const uint32_t d = exact_depth(depth_word(ka, kb, idx), R);
-        const uint32_t g = checksum(kc, idx);
+        const uint32_t g = checksum_pre(kc, idx);
         atomicXor(reinterpret_cast<unsigned long long*>(s.alpha(a, k, d, j)), (unsigned long long)idx);
         atomicXor(s.gamma(a, k, d, j), g);
         atomicXor(reinterpret_cast<unsigned long long*>(s.alpha(b, k, d, j)), (unsigned long long)idx);
@@ -542,7 +560,8 @@ __global__ void __launch_bounds__(1024) k_plain(const uint32_t* __restrict__ u,
 // ------------------------------------------------------------------ export
 
 // Nested rows (Eq. 1-2) of nodes [lo, hi): thread per (node, k, j), suffix XOR
-// from row R-1 down to row 0.  Output layout [node][k][j][row].
+// from row R-1 down to row 0, gamma' -> gamma on the way out.  Output layout
+// [node][k][j][row].
 __global__ void k_export(SketchView s, uint32_t lo, uint32_t hi, uint32_t K, uint32_t R,
                          uint64_t* __restrict__ oa, uint32_t* __restrict__ og) {
     const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -557,7 +576,7 @@ __global__ void k_export(SketchView s, uint32_t lo, uint32_t hi, uint32_t K, uin
         acc ^= *s.alpha(node, k, row, j);
         accg ^= *s.gamma(node, k, row, j);
         oa[gid * R + row] = acc;
-        og[gid * R + row] = accg;
+        og[gid * R + row] = gamma_final(accg);
     }
 }
 
@@ -591,7 +610,7 @@ gz_status ingest_setup(gz_handle* h) {
     h->small_seg = h->cfg.small_segment ? h->cfg.small_segment : 4;
     const bool wide = (uint64_t)h->V * h->V > (1ull << 32);
     if (h->tile % 4 != 0) return set_error(h, GZ_EINVAL, "tile_records must be a multiple of 4");
-    h->batched_smem = (size_t)rs * h->block * 12 + (size_t)h->tile * (8 + (wide ? 16 : 4)) + (size_t)h->K * 4;
+    h->batched_smem = (size_t)rs * h->block * 12 + (size_t)h->tile * (8 + (wide ? 16 : 8)) + (size_t)h->K * 4;
     if (h->cfg.smem_mode > 2) return set_error(h, GZ_EINVAL, "smem_mode must be 0, 1 or 2");
     h->atomic_delta = h->cfg.smem_mode != 2;
     const void* fn = (const void*)batched_fn(h->atomic_delta, wide);
@@ -984,7 +1003,7 @@ extern "C" gz_status gz_sketch_update_noalloc(void* sketch, uint32_t V, uint64_t
         a.Rs = Rs;
         a.tile = tile;
         a.small_seg = 4;
-        const size_t smem = (size_t)Rs * block * 12 + (size_t)tile * (8 + (wide ? 16 : 4)) + (size_t)K * 4;
+        const size_t smem = (size_t)Rs * block * 12 + (size_t)tile * (8 + (wide ? 16 : 8)) + (size_t)K * 4;
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_fn(1, wide), (int)block, smem) !=
                 cudaSuccess ||

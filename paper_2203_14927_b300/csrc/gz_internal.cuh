@@ -7,7 +7,10 @@
 // depth = min(#leading zero bits of (a*idx+b), R-1); nested row i is recovered as
 // the XOR of stored rows i..R-1 (a fixed linear map, so merges commute with it).
 //
-// Layout: node-major; per node, K blocks of (alpha[R][7] u64, gamma[R][7] u32).
+// Gamma words hold gamma' (see fmix32_pre below): the paper's checksum sum of a
+// bucket is gamma' ^ (gamma' >> 16).
+//
+// Layout: node-major; per node, K blocks of (alpha[R][7] u64, gamma'[R][7] u32).
 // One CubeSketch (node, k) is therefore a contiguous 84*R-byte block, which is
 // what a Boruvka round reads per node.
 #pragma once
@@ -49,15 +52,21 @@ struct Keys {
     const uint64_t* c;
 };
 
-// MurmurHash3's 32-bit finalizer (Appleby 2011).
-__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+// MurmurHash3's 32-bit finalizer (Appleby 2011), without its last step
+// h ^= h >> 16.  That step is a linear, invertible map L over GF(2)^32, so it
+// commutes with XOR sums: the device keeps gamma' = XOR of fmix32_pre values
+// in every bucket, a bucket's paper checksum gamma is L(gamma'), and a
+// candidate alpha is good iff gamma' == fmix32_pre(fold(alpha) ^ lo32(c)).
+__device__ __forceinline__ uint32_t fmix32_pre(uint32_t h) {
     h ^= h >> 16;
     h *= 0x85EBCA6Bu;
     h ^= h >> 13;
     h *= 0xC2B2AE35u;
-    h ^= h >> 16;
     return h;
 }
+
+// L: stored gamma' -> the checksum sum gamma of Fig. cube_code.
+__device__ __forceinline__ uint32_t gamma_final(uint32_t g) { return g ^ (g >> 16); }
 
 // 32-bit fold of an edge index: lo32 ^ lo32(hi32 * 0x9E3779B9) (the identity
 // below 2^32).
@@ -65,9 +74,10 @@ __device__ __forceinline__ uint32_t fold32(uint64_t idx) {
     return static_cast<uint32_t>(idx) ^ (static_cast<uint32_t>(idx >> 32) * 0x9E3779B9u);
 }
 
-// Checksum h2 (Fig. cube_code): fmix32(fold(idx) ^ lo32(c)).
-__device__ __forceinline__ uint32_t checksum(uint64_t c, uint64_t idx) {
-    return fmix32(fold32(idx) ^ static_cast<uint32_t>(c));
+// Stored form of checksum h2 (Fig. cube_code) of one index:
+// h2(idx) = L(checksum_pre(c, idx)) = fmix32(fold(idx) ^ lo32(c)).
+__device__ __forceinline__ uint32_t checksum_pre(uint64_t c, uint64_t idx) {
+    return fmix32_pre(fold32(idx) ^ static_cast<uint32_t>(c));
 }
 
 // Depth hash: t = a*idx + b (mod 2^64), Dietzfelbinger's multiply-add-shift

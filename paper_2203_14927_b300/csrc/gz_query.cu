@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(256) k_q_sample(QArgs q) {
             const uint64_t kcj = q.kc[q.round * GZ_COLS + j];
             auto good = [&](uint64_t a, uint32_t g, uint32_t row) -> bool {
                 if (row >= R || (a | g) == 0) return false;
-                if (g != checksum(kcj, a) || a >= VV) return false;
+                if (g != checksum_pre(kcj, a) || a >= VV) return false;
                 const uint32_t uu = (uint32_t)(a / q.V), vv = (uint32_t)(a % q.V);
                 if (uu >= vv) return false;
                 return (q.label[uu] == c) != (q.label[vv] == c);
