@@ -59,12 +59,12 @@ enum {
 typedef struct {
     uint32_t chunk_log2;    /* updates processed per partition pass = 2^chunk_log2 (default 24) */
     uint32_t kernel;        /* GZ_KERNEL_BATCHED or GZ_KERNEL_PLAIN */
-    uint32_t smem_rows;     /* exact-depth rows staged in shared memory (default 16, max 32) */
-    uint32_t tile_records;  /* records per work tile of the batched kernel (default 1024) */
+    uint32_t smem_rows;     /* exact-depth rows staged in shared memory (default 12, max 32) */
+    uint32_t tile_records;  /* records per work tile of the batched kernel (default 512) */
     uint32_t ctas_per_sm;   /* resident CTAs per SM of the persistent batched kernel (default: max) */
     uint32_t small_segment; /* node segments shorter than this skip shared-memory staging (default 4) */
-    uint32_t smem_mode;     /* delta update in shared memory: 0 default (= 1), 1 shared atomics,
-                               2 load-xor-store */
+    uint32_t smem_mode;     /* delta update in shared memory: 0 default (= 1), 1 32-bit shared
+                               atomics, 2 load-xor-store */
     uint32_t no_graph;      /* 1: launch a chunk's kernels one by one instead of replaying the
                                CUDA graph captured for the handle after its 8th chunk (default 0) */
     uint32_t reserved[4];
@@ -214,7 +214,7 @@ typedef struct {
     uint64_t updates;          /* updates in those passes */
     double partition_ms;       /* validation + histogram, scan, scatter */
     double update_ms;          /* batched (or plain) sketch-update kernel */
-    uint64_t rows_flushed;     /* (node, k, row) rows the batched kernel XORed into HBM */
+    uint64_t rows_flushed;     /* (node, column, row) delta buckets the batched kernel's flush visited */
     uint64_t deep_updates;     /* column updates that bypassed shared memory */
     uint64_t kernel_launches;  /* kernels launched by this handle in the window */
 } gz_profile;

@@ -41,7 +41,7 @@ struct gz_handle {
     uint32_t* d_scan_tmp = nullptr; // ceil((V+1)/1024) tile sums of the scans
     uint32_t block = 0;            // columns padded to a warp multiple
     uint32_t smem_rows = 0, tile = 0, small_seg = 0, batched_grid = 0;
-    bool atomic_delta = true;      // shared-memory atomics for the delta XORs
+    uint32_t delta_mode = 1;       // batched kernel's delta update: 0 load-xor-store, 1 shared atomics
     uint64_t batches_done = 0;     // partition passes issued (graph capture after 8)
     size_t batched_smem = 0;
 

@@ -239,43 +239,46 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // One CTA = 32*ceil(7K/32) threads; thread c owns CubeSketch column c = 7k + j
-// (one "Graph Worker" per column; no two threads write one bucket).
+// (one "Graph Worker" per column; no two threads write one bucket, so each
+// thread also flushes its own delta rows and no barrier separates hashing from
+// flushing).
 // Dynamic shared memory:
 //   delta rows: one 96-word block per (warp of columns, row d < Rs), warp w's
-//               block of row d at word (w*Rs + d)*96.  kAtomic: alpha lo,
-//               alpha hi, gamma' as three 32-word planes at +0, +32, +64;
-//               else alpha as 32 u64 (+0) and gamma' (+64).  A warp's 32 lanes
-//               hit 32 distinct banks whatever rows they update, and the three
-//               words of a column update share one address register.
-//   raw records  [2][tile] u32, filled by cp.async one tile ahead
-//   staged records [tile] (kWide: uint4 {idx_lo, idx_hi, fold_pre, 0};
-//                  else uint2 {idx, fold_pre})
-//   per-k deepest touched row [K] u32
+//               block of row d at word (w*Rs + d)*96.  kMode 1 (32-bit
+//               shared atomics): alpha lo, alpha hi, gamma' as three 32-word
+//               planes at +0, +32, +64; kMode 0 (load-xor-store): alpha as 32
+//               u64 (+0), gamma' (+64).  A warp's 32 lanes hit 32 distinct
+//               banks whatever rows they update, and the words of a column
+//               update share one address register.
+//   raw records  [3][tile] u32, filled by cp.async one tile ahead
+//   staged records [2][tile] (kWide: uint4 {idx_lo, idx_hi, fold_pre, 0};
+//                  else uint2 {idx, fold_pre}), one buffer per node segment in turn
 // Tiles (equal record counts) are claimed from an atomic counter one tile
 // ahead, so the next tile's records and first node are fetched while the
-// current tile is being hashed.
-template <bool kAtomic, bool kWide>
+// current tile is being hashed.  Barriers: one per tile (its records have
+// landed) and one per node segment (its records are staged); three raw and two
+// stage buffers make those the only ones.  (Warps that claim and stage tiles
+// on their own, with no barrier at all, measured slower: the staging is then
+// repeated per warp and the larger per-warp buffers cost occupancy.)
+template <int kMode, bool kWide>
 __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
     extern __shared__ __align__(16) uint64_t smem[];
     if (p.flags[0]) return;
     const uint32_t CP = blockDim.x, c = threadIdx.x;
     const uint32_t Rs = p.Rs, R = p.R, RC = Rs * CP, T = p.tile;
+    constexpr uint32_t kStageWords = kWide ? 4u : 2u;
     uint32_t* sw = reinterpret_cast<uint32_t*>(smem);  // delta blocks, 3*RC words
-    uint32_t* raw = sw + 3 * RC;  // [2][T], 16-byte aligned (RC multiple of 32, T multiple of 4)
-    uint32_t* stage = raw + 2 * T;
-    uint4* stage4 = reinterpret_cast<uint4*>(stage);
-    uint2* stage2 = reinterpret_cast<uint2*>(stage);
-    uint32_t* maxd = stage + (kWide ? 4u : 2u) * T;
+    uint32_t* raw = sw + 3 * RC;  // [3][T], 16-byte aligned (RC multiple of 32, T multiple of 4)
+    uint32_t* stage_base = raw + 3 * T;  // [2][kStageWords*T]
 
     const bool active = c < p.ncol;
     const uint32_t k = c / GZ_COLS, j = c - k * GZ_COLS;
     // word of (row 0, column c) in plane 0; row d adds d*96
     uint32_t* cw = sw + (c >> 5) * Rs * 96 + (c & 31);
-    uint64_t* ca = reinterpret_cast<uint64_t*>(sw + (c >> 5) * Rs * 96) + (c & 31);  // !kAtomic alpha
+    uint64_t* ca = reinterpret_cast<uint64_t*>(sw + (c >> 5) * Rs * 96) + (c & 31);  // kMode 0 alpha
     ColKey key{};
     if (active) key = make_colkey(p.keys.a[c], p.keys.b[c], p.keys.c[c]);
     for (uint32_t i = c; i < 3 * RC; i += CP) sw[i] = 0;
-    for (uint32_t i = c; i < p.K; i += CP) maxd[i] = 0;
     const uint32_t total = p.offsets[p.V];
     const uint32_t ntiles = (total + T - 1) / T;
     unsigned long long n_rows = 0, n_deep = 0;
@@ -292,10 +295,10 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
         cp_async_commit();
     };
 
-    // Dynamic tiles with a lookahead of one: while tile t is processed, the
-    // records of the next tile (already claimed) stream in with cp.async and
-    // thread 0 claims the tile after that; its index is stored at the end of
-    // the tile, so the atomic's latency hides behind the tile's work.
+    // Tile ring s_t: iteration it processes s_t[it%3], prefetches s_t[(it+1)%3]
+    // and thread 0 writes the tile claimed for iteration it+2 into
+    // s_t[(it+2)%3] before the iteration's barrier; every thread read that slot
+    // (as iteration it-1's tile) before the previous barrier.
     __shared__ uint32_t s_t[3];
     if (c == 0) {
         s_t[0] = atomicAdd(p.work, 1u);
@@ -307,29 +310,36 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
         fetch(s_t[0], 0);
         x_next = p.tile_node[s_t[0]];
     }
+    uint32_t sbuf = 0;
     for (uint32_t it = 0;; ++it) {
         const uint32_t t = s_t[it % 3];
         if (t >= ntiles) break;
-        const uint32_t buf = it & 1;
         const uint32_t x_first = x_next;
         const uint32_t tn = s_t[(it + 1) % 3];
         uint32_t claimed = 0;
         if (c == 0) claimed = atomicAdd(p.work, 1u);
         if (tn < ntiles) {
-            fetch(tn, buf ^ 1);
+            fetch(tn, (it + 1) % 3);  // that buffer was last read in iteration it-2
             x_next = p.tile_node[tn];
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
         }
-        __syncthreads();  // raw[buf] complete and visible
-        const uint32_t* rb = raw + buf * T;
+        if (c == 0) s_t[(it + 2) % 3] = claimed;
+        __syncthreads();  // raw[it%3] complete and visible; s_t up to date
+        const uint32_t* rb = raw + (it % 3) * T;
         const uint32_t lo = t * T, hi = min(lo + T, total);
         uint32_t x = x_first, pos = lo;
         while (pos < hi) {
             const uint32_t seg_end = min(p.offsets[x + 1], hi);
             const uint32_t nseg = seg_end - pos;
             if (nseg > 0) {
+                // this stage buffer was last read two segments ago, before the
+                // previous segment's barrier
+                uint32_t* stage = stage_base + sbuf * kStageWords * T;
+                uint4* stage4 = reinterpret_cast<uint4*>(stage);
+                uint2* stage2 = reinterpret_cast<uint2*>(stage);
+                sbuf ^= 1u;
                 for (uint32_t i = c; i < nseg; i += CP) {
                     const uint64_t idx = edge_index(x, rb[pos - lo + i], p.V);
                     if (kWide) {
@@ -361,146 +371,125 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                             atomicXor(p.s.gamma(x, k, d, j), checksum_w(key, fp));
                         }
                     }
-                } else {
-                    uint32_t md = 0;
-                    if (active) {
-                        // one column update staged in shared memory (d < Rs)
-                        auto put = [&](uint32_t d, uint32_t xlo, uint32_t xhi, uint32_t g) {
-                            if (kAtomic) {
-                                uint32_t* w = cw + d * 96;
-                                atomicXor(w, xlo);
-                                if (kWide) atomicXor(w + 32, xhi);
-                                atomicXor(w + 64, g);
-                            } else {
-                                ca[d * 48] ^= ((uint64_t)xhi << 32) | xlo;
-                                cw[d * 96 + 64] ^= g;
-                            }
-                        };
-                        // a column update whose exact depth is Rs or more goes to HBM
-                        auto deep = [&](uint32_t xlo, uint32_t xhi, uint32_t g) {
-                            ++n_deep;
-                            const uint64_t idx = ((uint64_t)xhi << 32) | xlo;
-                            const uint32_t dd = exact_depth(depth_word(p.keys.a[c], p.keys.b[c], idx), R);
-                            atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, dd, j)),
-                                      (unsigned long long)idx);
-                            atomicXor(p.s.gamma(x, k, dd, j), g);
-                        };
-                        uint32_t i = 0;
-                        // four records at a time in straight-line code, so the
-                        // four hash chains interleave; one rare branch for deep rows
-                        for (; i + 4 <= nseg; i += 4) {
-                            uint32_t xlo[4], xhi[4], fp[4];
-                            if (kWide) {
-#pragma unroll
-                                for (int r = 0; r < 4; ++r) {
-                                    const uint4 q = stage4[i + r];
-                                    xlo[r] = q.x;
-                                    xhi[r] = q.y;
-                                    fp[r] = q.z;
-                                }
-                            } else {
-                                const uint4 q0 = reinterpret_cast<const uint4*>(stage2)[i >> 1];
-                                const uint4 q1 = reinterpret_cast<const uint4*>(stage2)[(i >> 1) + 1];
-                                xlo[0] = q0.x;
-                                fp[0] = q0.y;
-                                xlo[1] = q0.z;
-                                fp[1] = q0.w;
-                                xlo[2] = q1.x;
-                                fp[2] = q1.y;
-                                xlo[3] = q1.z;
-                                fp[3] = q1.w;
-#pragma unroll
-                                for (int r = 0; r < 4; ++r) xhi[r] = 0;
-                            }
-                            uint32_t d[4], g[4];
+                } else if (active) {
+                    uint32_t md = 0;  // deepest delta row this column touched
+                    // one column update staged in shared memory (d < Rs)
+                    auto put = [&](uint32_t d, uint32_t xlo, uint32_t xhi, uint32_t g) {
+                        if (kMode == 1) {
+                            uint32_t* w = cw + d * 96;
+                            atomicXor(w, xlo);
+                            if (kWide) atomicXor(w + 32, xhi);
+                            atomicXor(w + 64, g);
+                        } else {
+                            ca[d * 48] ^= ((uint64_t)xhi << 32) | xlo;
+                            cw[d * 96 + 64] ^= g;
+                        }
+                    };
+                    // a column update whose exact depth is Rs or more goes to HBM
+                    auto deep = [&](uint32_t xlo, uint32_t xhi, uint32_t g) {
+                        ++n_deep;
+                        const uint64_t idx = ((uint64_t)xhi << 32) | xlo;
+                        const uint32_t dd = exact_depth(depth_word(p.keys.a[c], p.keys.b[c], idx), R);
+                        atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, dd, j)),
+                                  (unsigned long long)idx);
+                        atomicXor(p.s.gamma(x, k, dd, j), g);
+                    };
+                    uint32_t i = 0;
+                    // four records at a time in straight-line code, so the
+                    // four hash chains interleave; one rare branch for deep rows
+                    for (; i + 4 <= nseg; i += 4) {
+                        uint32_t xlo[4], xhi[4], fp[4];
+                        if (kWide) {
 #pragma unroll
                             for (int r = 0; r < 4; ++r) {
-                                d[r] = __clz(depth_hi<kWide>(key, xlo[r], xhi[r]));
-                                g[r] = checksum_w(key, fp[r]);
+                                const uint4 q = stage4[i + r];
+                                xlo[r] = q.x;
+                                xhi[r] = q.y;
+                                fp[r] = q.z;
                             }
-                            const uint32_t dmax = max(max(d[0], d[1]), max(d[2], d[3]));
-                            if (dmax < Rs) {
+                        } else {
+                            const uint4 q0 = reinterpret_cast<const uint4*>(stage2)[i >> 1];
+                            const uint4 q1 = reinterpret_cast<const uint4*>(stage2)[(i >> 1) + 1];
+                            xlo[0] = q0.x;
+                            fp[0] = q0.y;
+                            xlo[1] = q0.z;
+                            fp[1] = q0.w;
+                            xlo[2] = q1.x;
+                            fp[2] = q1.y;
+                            xlo[3] = q1.z;
+                            fp[3] = q1.w;
 #pragma unroll
-                                for (int r = 0; r < 4; ++r) put(d[r], xlo[r], xhi[r], g[r]);
-                                md = max(md, dmax);
-                            } else {
+                            for (int r = 0; r < 4; ++r) xhi[r] = 0;
+                        }
+                        uint32_t d[4], g[4];
 #pragma unroll
-                                for (int r = 0; r < 4; ++r) {
-                                    if (d[r] < Rs) {
-                                        put(d[r], xlo[r], xhi[r], g[r]);
-                                        md = max(md, d[r]);
-                                    } else {
-                                        deep(xlo[r], xhi[r], g[r]);
-                                    }
-                                }
-                            }
+                        for (int r = 0; r < 4; ++r) {
+                            d[r] = __clz(depth_hi<kWide>(key, xlo[r], xhi[r]));
+                            g[r] = checksum_w(key, fp[r]);
                         }
-                        for (; i < nseg; ++i) {
-                            uint32_t xlo, xhi, fp;
-                            if (kWide) {
-                                const uint4 q = stage4[i];
-                                xlo = q.x;
-                                xhi = q.y;
-                                fp = q.z;
-                            } else {
-                                const uint2 q = stage2[i];
-                                xlo = q.x;
-                                xhi = 0;
-                                fp = q.y;
-                            }
-                            const uint32_t d = __clz(depth_hi<kWide>(key, xlo, xhi));
-                            const uint32_t g = checksum_w(key, fp);
-                            if (d < Rs) {
-                                put(d, xlo, xhi, g);
-                                md = max(md, d);
-                            } else {
-                                deep(xlo, xhi, g);
-                            }
-                        }
-                        atomicMax(&maxd[k], md);
-                    }
-                    __syncthreads();
-                    const uint32_t per_k = Rs * GZ_COLS;
-                    for (uint32_t q = c; q < p.K * per_k; q += CP) {
-                        const uint32_t kk = q / per_k, rem = q - kk * per_k;
-                        const uint32_t row = rem / GZ_COLS, jj = rem - row * GZ_COLS;
-                        if (row <= maxd[kk]) {
-                            const uint32_t col = kk * GZ_COLS + jj;
-                            uint32_t* w = sw + ((col >> 5) * Rs + row) * 96 + (col & 31);
-                            uint64_t a;
-                            if (kAtomic) {
-                                a = ((uint64_t)w[32] << 32) | w[0];
-                            } else {
-                                a = reinterpret_cast<uint64_t*>(w - (col & 31))[col & 31];
-                            }
-                            const uint32_t g = w[64];
-                            if (a | g) {
-                                atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, kk, row, jj)),
-                                          (unsigned long long)a);
-                                atomicXor(p.s.gamma(x, kk, row, jj), g);
-                                if (kAtomic) {
-                                    w[0] = 0;
-                                    w[32] = 0;
+                        const uint32_t dmax = max(max(d[0], d[1]), max(d[2], d[3]));
+                        if (dmax < Rs) {
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) put(d[r], xlo[r], xhi[r], g[r]);
+                            md = max(md, dmax);
+                        } else {
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) {
+                                if (d[r] < Rs) {
+                                    put(d[r], xlo[r], xhi[r], g[r]);
+                                    md = max(md, d[r]);
                                 } else {
-                                    reinterpret_cast<uint64_t*>(w - (col & 31))[col & 31] = 0;
+                                    deep(xlo[r], xhi[r], g[r]);
                                 }
-                                w[64] = 0;
                             }
                         }
                     }
-                    __syncthreads();
-                    for (uint32_t i = c; i < p.K; i += CP) {
-                        n_rows += maxd[i] + 1;
-                        maxd[i] = 0;
+                    for (; i < nseg; ++i) {
+                        uint32_t xlo, xhi, fp;
+                        if (kWide) {
+                            const uint4 q = stage4[i];
+                            xlo = q.x;
+                            xhi = q.y;
+                            fp = q.z;
+                        } else {
+                            const uint2 q = stage2[i];
+                            xlo = q.x;
+                            xhi = 0;
+                            fp = q.y;
+                        }
+                        const uint32_t d = __clz(depth_hi<kWide>(key, xlo, xhi));
+                        const uint32_t g = checksum_w(key, fp);
+                        if (d < Rs) {
+                            put(d, xlo, xhi, g);
+                            md = max(md, d);
+                        } else {
+                            deep(xlo, xhi, g);
+                        }
                     }
+                    // flush this column's touched rows into the node sketch
+                    for (uint32_t row = 0; row <= md; ++row) {
+                        uint32_t* w = cw + row * 96;
+                        const uint64_t a = kMode == 1 ? (((uint64_t)w[32] << 32) | w[0]) : ca[row * 48];
+                        const uint32_t g = w[64];
+                        if (a | g) {
+                            atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, row, j)),
+                                      (unsigned long long)a);
+                            atomicXor(p.s.gamma(x, k, row, j), g);
+                            if (kMode == 1) {
+                                w[0] = 0;
+                                w[32] = 0;
+                            } else {
+                                ca[row * 48] = 0;
+                            }
+                            w[64] = 0;
+                        }
+                    }
+                    n_rows += md + 1;
                 }
-                __syncthreads();
             }
             pos = seg_end;
             ++x;
         }
-        if (c == 0) s_t[(it + 2) % 3] = claimed;
-        __syncthreads();
     }
     cp_async_wait<0>();
     if (n_rows) atomicAdd(&p.stats[0], n_rows);
@@ -509,9 +498,10 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
 
 using BatchedFn = void (*)(BatchedArgs);
 
+// mode: 0 load-xor-store, 1 32-bit shared atomics
 static BatchedFn batched_fn(uint32_t mode, bool wide) {
-    if (mode) return wide ? k_batched<true, true> : k_batched<true, false>;
-    return wide ? k_batched<false, true> : k_batched<false, false>;
+    if (mode == 1) return wide ? k_batched<1, true> : k_batched<1, false>;
+    return wide ? k_batched<0, true> : k_batched<0, false>;
 }
 
 // Raise the dynamic shared-memory cap of every batched-kernel variant to the
@@ -602,7 +592,7 @@ static Keys keys_of(const gz_handle* h) {
 gz_status ingest_setup(gz_handle* h) {
     h->block = (h->ncol + 31) / 32 * 32;
     if (h->block > 1024) return set_error(h, GZ_EINVAL, "too many CubeSketch columns for one CTA");
-    uint32_t rs = h->cfg.smem_rows ? h->cfg.smem_rows : 16;
+    uint32_t rs = h->cfg.smem_rows ? h->cfg.smem_rows : 12;
     rs = std::min<uint32_t>(rs, 32);
     rs = std::min<uint32_t>(rs, h->R);
     h->smem_rows = rs;
@@ -610,10 +600,10 @@ gz_status ingest_setup(gz_handle* h) {
     h->small_seg = h->cfg.small_segment ? h->cfg.small_segment : 4;
     const bool wide = (uint64_t)h->V * h->V > (1ull << 32);
     if (h->tile % 4 != 0) return set_error(h, GZ_EINVAL, "tile_records must be a multiple of 4");
-    h->batched_smem = (size_t)rs * h->block * 12 + (size_t)h->tile * (8 + (wide ? 16 : 8)) + (size_t)h->K * 4;
+    h->batched_smem = (size_t)rs * h->block * 12 + (size_t)h->tile * (12 + (wide ? 32 : 16));
     if (h->cfg.smem_mode > 2) return set_error(h, GZ_EINVAL, "smem_mode must be 0, 1 or 2");
-    h->atomic_delta = h->cfg.smem_mode != 2;
-    const void* fn = (const void*)batched_fn(h->atomic_delta, wide);
+    h->delta_mode = h->cfg.smem_mode == 2 ? 0u : 1u;  // kernel mode: 1 shared atomics, 0 load-xor-store
+    const void* fn = (const void*)batched_fn(h->delta_mode, wide);
     // The dynamic shared-memory cap is one process-wide setting per kernel, so
     // every caller sets the same value (the device's opt-in maximum); a
     // per-handle value would let handles of different sizes break each other.
@@ -665,7 +655,7 @@ static void enqueue_batched(gz_handle* h, const uint32_t* d_u, const uint32_t* d
         else cudaEventRecord(ev, st);
     };
     if (ev0) record(ev0);
-    cudaMemsetAsync(h->d_flags, 0, 2 * sizeof(uint32_t), st);  // batch flag + work
+    cudaMemsetAsync(h->d_flags, 0, 2 * sizeof(uint32_t), st);  // batch flag + tile counter
     cudaMemsetAsync(h->d_counts, 0, (size_t)(h->V + 1) * sizeof(uint32_t), st);
     k_validate_count<<<grid, 256, 0, st>>>(d_u, d_v, n, h->V, h->d_counts, h->d_flags);
     launch_scan(h->d_counts, h->d_offsets, h->d_cursor, h->V, st, h->d_scan_tmp);
@@ -673,7 +663,7 @@ static void enqueue_batched(gz_handle* h, const uint32_t* d_u, const uint32_t* d
     k_tile_nodes<<<(h->V + 255) / 256, 256, 0, st>>>(h->d_offsets, h->V, h->tile, h->d_flags, h->d_tile_node);
     if (ev1) record(ev1);
     const bool wide = (uint64_t)h->V * h->V > (1ull << 32);
-    batched_fn(h->atomic_delta, wide)<<<h->batched_grid, h->block, h->batched_smem, st>>>(batched_args(h));
+    batched_fn(h->delta_mode, wide)<<<h->batched_grid, h->block, h->batched_smem, st>>>(batched_args(h));
     if (ev2) record(ev2);
 }
 
@@ -965,7 +955,7 @@ extern "C" gz_status gz_sketch_update_noalloc(void* sketch, uint32_t V, uint64_t
     }
     const uint32_t R = 2 * L, ncol = 7 * K;
     const uint32_t block = (ncol + 31) / 32 * 32;
-    const uint32_t Rs = std::min<uint32_t>(16, R), tile = kTile;
+    const uint32_t Rs = std::min<uint32_t>(12, R), tile = kTile;
     const bool wide = (uint64_t)V * V > (1ull << 32);
 
     uint64_t* keys = reinterpret_cast<uint64_t*>(base + kKeys);
@@ -1003,7 +993,7 @@ extern "C" gz_status gz_sketch_update_noalloc(void* sketch, uint32_t V, uint64_t
         a.Rs = Rs;
         a.tile = tile;
         a.small_seg = 4;
-        const size_t smem = (size_t)Rs * block * 12 + (size_t)tile * (8 + (wide ? 16 : 8)) + (size_t)K * 4;
+        const size_t smem = (size_t)Rs * block * 12 + (size_t)tile * (12 + (wide ? 32 : 16));
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_fn(1, wide), (int)block, smem) !=
                 cudaSuccess ||
