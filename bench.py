@@ -152,6 +152,40 @@ def oracle_rate(spec: S.KronSpec, seed: int, budget_s: float, max_nodes: int = 6
     return endpoint_updates / 2.0 / spent, spent, used, endpoint_updates
 
 
+def mem_available_bytes() -> int:
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def paper_design_rate(V: int, seed: int, u, v):
+    """The paper's CPU design (per-node buffers, parallel workers; Section 5.1)
+    on every host core, over the given stream prefix.  All V node sketches
+    when host memory allows (3x their size available), else the first node
+    range that fits (updates/s then counts the endpoint updates applied / 2)."""
+    import oracle
+
+    K, R = oracle.geometry(V)
+    per_node = K * 7 * R * 12
+    avail = mem_available_bytes()
+    span = V if avail >= 3 * V * per_node else max(1024, min(V, avail // (4 * per_node)))
+    inside = ((u < span).astype(np.int64) + (v < span).astype(np.int64)).sum()
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    oracle.ingest_batched(V, seed, u, v, 0, span, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": float(inside) / 2.0 / dt, "unit": "updates/s", "cores": threads,
+            "kind": "the paper's design: per-node buffers applied by parallel workers (OpenMP), "
+                    "nested CubeSketch rows",
+            "sample": f"first {len(u)} updates of the same stream, nodes [0, {span}) of {V} "
+                      f"({int(inside)} endpoint updates, {dt:.1f} s)"}
+
+
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
@@ -429,6 +463,11 @@ def run_ours(args, rank: int, world: int):
                "sample": f"oracle sketch_node over {len(nodes)} random nodes of the same graph "
                          f"({eu} endpoint updates, {spent:.1f} s), single thread",
                "cpu": cpu_model(), "host_cores": host_cores()}
+        n_pd = min(total, 1 << args.paper_design_log2)
+        cpu["paper_design"] = paper_design_rate(spec.V, seed, u_all[:n_pd].cpu().numpy().view(np.uint32),
+                                                v_all[:n_pd].cpu().numpy().view(np.uint32))
+        log(f"[bench] paper-design CPU baseline: {cpu['paper_design']['value'] / 1e6:.2f} M updates/s "
+            f"on {cpu['paper_design']['cores']} threads")
 
     if rank == 0:
         out = {
@@ -681,6 +720,8 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--kernel", choices=["batched", "plain"], default="batched")
     ap.add_argument("--queries", type=int, default=20)
+    ap.add_argument("--paper-design-log2", type=int, default=22,
+                    help="stream prefix (log2 updates) for the OpenMP paper-design CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=40.0)
     ap.add_argument("--e2e-log2", type=int, default=28)

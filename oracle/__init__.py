@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gz_oracle.c")
+_SRC_BATCHED = os.path.join(_HERE, "gz_cpu_batched.c")
 _LIB = os.path.join(_HERE, "libgz_oracle.so")
 
 COLS = 7
@@ -30,11 +31,13 @@ NOT_RUN = -4
 
 
 def build(force: bool = False) -> str:
-    """Compile gz_oracle.c into libgz_oracle.so (plain gcc, -O2)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile gz_oracle.c (and the paper-design CPU baseline gz_cpu_batched.c,
+    OpenMP) into libgz_oracle.so (plain gcc, -O2)."""
+    srcs = [_SRC, _SRC_BATCHED]
+    if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(s) for s in srcs):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-Wextra", "-shared",
-                               "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-Wextra", "-fopenmp", "-shared",
+                               "-fPIC", "-o", tmp, *srcs])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -75,6 +78,10 @@ def lib():
         L.gzo_brute_cc.argtypes = [u32, sz, p, p, p]
         L.gzo_cc_edges.restype = ctypes.c_int
         L.gzo_cc_edges.argtypes = [u32, sz, p, p, p]
+        L.gzb_ingest_batched.restype = ctypes.c_int
+        L.gzb_ingest_batched.argtypes = [u32, u64, sz, p, p, u32, u32, p, p, ctypes.c_int, sz]
+        L.gzb_max_threads.restype = ctypes.c_int
+        L.gzb_max_threads.argtypes = []
         _lib = L
     return _lib
 
@@ -131,6 +138,26 @@ def empty_sketches(V: int, nodes: int | None = None):
     K, R = geometry(V)
     n = V if nodes is None else nodes
     return (np.zeros((n, K, COLS, R), np.uint64), np.zeros((n, K, COLS, R), np.uint32))
+
+
+def ingest_batched(V: int, seed: int, u, v, node_lo: int = 0, node_hi: int | None = None,
+                   threads: int = 0, chunk: int = 1 << 22):
+    """The paper's CPU design (per-node buffers applied by parallel workers,
+    Section 5.1) over the stream (u, v), sketching nodes [node_lo, node_hi)
+    only; nested form like ingest().  A timed baseline, not the oracle."""
+    node_hi = V if node_hi is None else node_hi
+    u = np.ascontiguousarray(u, np.uint32)
+    v = np.ascontiguousarray(v, np.uint32)
+    alpha, gamma = empty_sketches(V, node_hi - node_lo)
+    rc = lib().gzb_ingest_batched(V, seed, len(u), _ptr(u), _ptr(v), node_lo, node_hi,
+                                  _ptr(alpha), _ptr(gamma), threads, chunk)
+    if rc != 0:
+        raise ValueError(f"gzb_ingest_batched failed ({rc})")
+    return alpha, gamma
+
+
+def max_threads() -> int:
+    return int(lib().gzb_max_threads())
 
 
 def ingest(V: int, seed: int, u, v, alpha=None, gamma=None):

@@ -427,3 +427,17 @@ def test_kron_components_shortcut_matches_brute_force(L, density, seed):
     got = kron_components(spec, n_hubs=64)
     assert np.array_equal(got, want)
     assert len(np.unique(want)) > 1  # isolated vertices exist, so the check is not trivial
+
+
+def test_paper_design_cpu_baseline_equals_oracle():
+    # the OpenMP per-node-buffer baseline (Section 5.1's design) must produce
+    # the oracle's sketches bit for bit, for every node range and chunking
+    V = 300
+    u, v = S.random_stream(V, 6000, seed=12, n_distinct=2000)
+    A, G = oracle.ingest(V, 9, u, v)
+    a, g = oracle.ingest_batched(V, 9, u, v, threads=4, chunk=777)
+    assert np.array_equal(a, A) and np.array_equal(g, G)
+    a, g = oracle.ingest_batched(V, 9, u, v, node_lo=37, node_hi=190, threads=3, chunk=1 << 20)
+    assert np.array_equal(a, A[37:190]) and np.array_equal(g, G[37:190])
+    with pytest.raises(ValueError):
+        oracle.ingest_batched(V, 9, np.array([3], np.uint32), np.array([3], np.uint32))
