@@ -36,8 +36,43 @@ WORKLOADS = {
     "kron17": (17, 4.0e9, 0.1, 17, "V=2^17 Graph500-initiator Kronecker stream, ~4e9 updates, 10% churn"),
     "kron15": (15, 3.0e8, 0.1, 15, "V=2^15 Graph500-initiator Kronecker stream, ~3e8 updates, 10% churn"),
     "kron13": (13, 2.0e7, 0.1, 13, "V=2^13 Graph500-initiator Kronecker stream, ~2e7 updates, 10% churn"),
+    # beyond the paper's largest graph (kron18): 123 GB of node sketches on one GPU
+    "kron20": (20, 8.0e9, 0.1, 20, "V=2^20 Graph500-initiator Kronecker stream, ~8e9 updates, 10% churn"),
 }
 CHUNK_LOG2 = 24
+
+# DRAM bytes per launch of k_batched from one ncu capture (one-pass
+# dram__bytes_read.sum + dram__bytes_write.sum) of this bench's own step; valid
+# only for the kernel sources (sha256 of gz_ingest.cu + gz_internal.cuh, first
+# 16 hex digits) and configuration it was taken with.
+TRAFFIC = {
+    "kron17": {"sha": "2e65820e7f65d1b0",
+               "cfg": {"smem_mode": 1, "tile_records": 512, "smem_rows": 12, "ctas_per_sm": 0, "chunk_log2": 26},
+               "bytes_per_launch": 10.272e9, "updates_per_launch": 66592033,
+               "source": "profiles/k_batched_kron17_dram.md"},
+}
+
+
+def kernel_sha() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("gz_ingest.cu", "gz_internal.cuh"):
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2203_14927_b300", "csrc", f),
+                  "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str, cfg: dict, kernel: str):
+    t = TRAFFIC.get(workload)
+    if kernel != "batched" or not t:
+        return None, "no ncu capture for this workload"
+    if kernel_sha() != t["sha"]:
+        return None, "kernel sources changed since the ncu capture"
+    if any(cfg.get(k) != v for k, v in t["cfg"].items()):
+        return None, f"ncu capture taken at config {t['cfg']}"
+    return t["bytes_per_launch"], t["source"]
 
 
 def log(*a):
@@ -340,12 +375,18 @@ def run_ours(args, rank: int, world: int):
     s_total = spec.V * K * 84 * R
     wide = spec.V * spec.V > (1 << 32)
     col_updates = upd_per_launch * 2 * 7 * K
-    # HBM, by the method's bytes per chunk: the kernel's two records per update
-    # and one read + write of every node sketch (the amortised read-modify-write of the batched design)
-    hbm_bytes = 8.0 * upd_per_launch + 2.0 * s_total
+    # HBM, by the bytes the batched update must move per launch: its two
+    # records per update (8 B) and a read-modify-write of every exact-depth
+    # bucket a node segment changed (12 B each way; the kernel counts these
+    # buckets as rows_flushed).  The full-sketch bound, one read and write of
+    # every node sketch per chunk, overstates it whenever nodes touch few rows.
+    rows_per_launch = prof["rows_flushed"] / launches
+    traffic, traffic_note = measured_traffic(args.workload, cfg, args.kernel)
+    hbm_bytes = 8.0 * upd_per_launch + 24.0 * rows_per_launch
     hbm = {"bound": "hbm", "achieved": hbm_bytes / sec / 1e9, "peak": peak, "unit": "GB/s",
            "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-           "bytes_per_launch": hbm_bytes}
+           "bytes_per_launch": hbm_bytes, "touched_buckets_per_launch": rows_per_launch,
+           "full_sketch_bytes_per_launch": 8.0 * upd_per_launch + 2.0 * s_total}
     hbm["frac"] = hbm["achieved"] / peak
     # integer issue: 16 (V > 2^16) or 14 32-bit operations per column update,
     # against the measured integer ceilings of this GPU (gz_int_peak: chains of
@@ -372,7 +413,8 @@ def run_ours(args, rank: int, world: int):
     roofline = dict(binding)
     roofline.update({
         "kernel": "k_batched" if args.kernel == "batched" else "k_plain",
-        "traffic": None,
+        "traffic": traffic,
+        "traffic_source": traffic_note,
         "avg_launch_ms": avg_ms, "launches": launches, "updates_per_launch": upd_per_launch,
         "column_updates_per_s": col_updates / sec,
         "share_of_step": prof["update_ms"] / ms if ms > 0 else None,
@@ -410,18 +452,19 @@ def run_ours(args, rank: int, world: int):
         torch.cuda.synchronize()
         h2d_gbs = 4 * n_e2e / (e0.elapsed_time(e1) / 1000.0) / 1e9
         del dtmp
-        ge = gz.Graph(spec.V, seed=seed, kernel=args.kernel, **cfg)
-        ge.edge_update(hu_np, hv_np)  # warm-up
-        ge.connected_components()
+        # the same handle, now fed from host memory (a second 2^20-node
+        # graph would not fit beside the first one and the device stream)
+        g.reset()
+        g.edge_update(hu_np, hv_np)  # warm-up of the host path
+        g.connected_components()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         reps = 2
         for _ in range(reps):
-            ge.reset()
-            ge.edge_update(hu_np, hv_np)
-            labels, ncc_e, _ = ge.connected_components()
+            g.reset()
+            g.edge_update(hu_np, hv_np)
+            labels, ncc_e, _ = g.connected_components()
         te = (time.perf_counter() - t1) / reps
-        ge.close()
         del hu, hv
         e2e = {"value": world * n_e2e / te, "unit": "updates/s", "h2d_bytes_per_step": 8 * n_e2e,
                "pinned_h2d_gbs": h2d_gbs,
@@ -434,23 +477,26 @@ def run_ours(args, rank: int, world: int):
     plain = None
     if not args.no_plain and args.kernel == "batched":
         n_pl = min(total, 1 << args.plain_log2)
-        gp = gz.Graph(spec.V, seed=seed, kernel="plain", chunk_log2=CHUNK_LOG2)
-        gp.edge_update(u_all[:1 << 20], v_all[:1 << 20])
-        torch.cuda.synchronize()
-        gp.reset()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        gp.edge_update(u_all[:n_pl], v_all[:n_pl])
-        e1.record(stream)
-        torch.cuda.synchronize()
-        tp = e0.elapsed_time(e1) / 1000.0
-        # same prefix through the batched path for a like-for-like ratio
+        # the batched path on the prefix first, for a like-for-like ratio
         g.reset()
         e0.record(stream)
         g.edge_update(u_all[:n_pl], v_all[:n_pl])
         e1.record(stream)
         torch.cuda.synchronize()
         tb = e0.elapsed_time(e1) / 1000.0
+        free_b, _ = torch.cuda.mem_get_info()
+        if free_b < 1.1 * gz.memory_bytes(spec.V, kernel="plain", chunk_log2=CHUNK_LOG2):
+            g.close()  # make room for the plain kernel's sketches
+        gp = gz.Graph(spec.V, seed=seed, kernel="plain", chunk_log2=CHUNK_LOG2)
+        gp.edge_update(u_all[:1 << 20], v_all[:1 << 20])
+        torch.cuda.synchronize()
+        gp.reset()
+        e0.record(stream)
+        gp.edge_update(u_all[:n_pl], v_all[:n_pl])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tp = e0.elapsed_time(e1) / 1000.0
         gp.close()
         plain = {"value": n_pl / tp, "unit": "updates/s", "sample": f"first {n_pl} updates (2^{args.plain_log2})",
                  "batched_same_prefix": n_pl / tb, "speedup_batched_over_plain": tp / tb}
@@ -706,13 +752,77 @@ def run_failures(args, rank: int, world: int):
     print(json.dumps(out), flush=True)
 
 
+def run_stream_queries(args, rank: int, world: int):
+    """Queries during the stream (the experiment of Fig. query): ingest the
+    kron17 stream and issue a CC query after every tenth of it.  Each query
+    first waits for the updates already queued (the flush of Section 5.2) and
+    then runs Boruvka; both are reported, with the rate of the whole job."""
+    import torch
+
+    import paper_2203_14927_b300 as gz
+    from paper_2203_14927_b300 import autotune
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(0)
+    L, n_upd, churn, seed, desc = WORKLOADS["kron17"]
+    spec = S.kron_for_updates(L, seed, n_upd, churn=churn, chunk_updates=2 ** CHUNK_LOG2)
+    U, Vv, total = generate_on_device(spec, torch, gz)
+    u_all, v_all = U[:total], Vv[:total]
+    cfg = dict(autotune.DEFAULT)
+    if args.cfg:
+        cfg.update(json.loads(args.cfg))
+    g = gz.Graph(spec.V, seed=seed, **cfg)
+    cuts = [round(total * i / 10) for i in range(11)]
+
+    def run(with_queries: bool):
+        g.reset()
+        torch.cuda.synchronize()
+        rows = []
+        t0 = time.perf_counter()
+        for i in range(1, 11):
+            g.edge_update(u_all[cuts[i - 1]:cuts[i]], v_all[cuts[i - 1]:cuts[i]])
+            if with_queries:
+                tq = time.perf_counter()
+                labels, ncc, st = g.connected_components()
+                wall = (time.perf_counter() - tq) * 1000.0
+                rows.append({"fraction": i / 10, "updates": cuts[i], "components": ncc, "rounds": st["rounds"],
+                             "query_ms": st["ms"], "wait_for_queued_ingest_ms": max(0.0, wall - st["ms"]),
+                             "status": st["status"]})
+        g.sync()
+        return time.perf_counter() - t0, rows
+
+    for _ in range(max(1, args.warmup)):
+        run(True)
+    t_plain, _ = run(False)
+    t_q, rows = run(True)
+    q = sorted(r["query_ms"] for r in rows)
+    out = {
+        "metric": "edge_updates_per_sec", "value": total / t_q, "unit": "updates/s", "n_gpus": 1,
+        "steps": 1, "warmup": max(1, args.warmup), "ms_per_step": t_q * 1000.0, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic: seeded Kronecker insert/delete stream generated on device",
+        "config": {"workload": f"kron17 with a CC query after every 10% of the stream: {desc}",
+                   "V": spec.V, "updates": total, "cfg": cfg,
+                   "timing": "host wall clock around the whole job (ingest calls + queries)"},
+        "ingest_only_updates_per_s": total / t_plain,
+        "query_overhead": t_q / t_plain - 1.0,
+        "query_ms": {"p50_ms": float(np.percentile(q, 50)), "max_ms": q[-1], "n": len(q)},
+        "per_query": rows,
+        "paper": "Fig. query1: kron17, queries every 10% of the stream, 3.95e6 updates/s with 400-byte buffers",
+    }
+    g.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve", "failures"], default="kron17")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve", "failures", "stream_queries"],
+                    default="kron17")
     ap.add_argument("--seeds", type=int, default=20)
     ap.add_argument("--fail-workload", choices=sorted(WORKLOADS), default="kron17")
     ap.add_argument("--serve-graphs", type=int, default=64)
@@ -735,13 +845,15 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
-        if args.workload in ("serve", "failures"):
+        if args.workload in ("serve", "failures", "stream_queries"):
             args.workload = "kron17"
         run_reference(args, rank, world)
     elif args.workload == "serve":
         run_serve(args, rank, world)
     elif args.workload == "failures":
         run_failures(args, rank, world)
+    elif args.workload == "stream_queries":
+        run_stream_queries(args, rank, world)
     else:
         run_ours(args, rank, world)
 

@@ -214,7 +214,7 @@ typedef struct {
     uint64_t updates;          /* updates in those passes */
     double partition_ms;       /* validation + histogram, scan, scatter */
     double update_ms;          /* batched (or plain) sketch-update kernel */
-    uint64_t rows_flushed;     /* (node, column, row) delta buckets the batched kernel's flush visited */
+    uint64_t rows_flushed;     /* (node, column, row) buckets the batched kernel's flush XORed into HBM */
     uint64_t deep_updates;     /* column updates that bypassed shared memory */
     uint64_t kernel_launches;  /* kernels launched by this handle in the window */
 } gz_profile;

@@ -175,6 +175,29 @@ def geometry(V: int) -> tuple[int, int]:
     return K.value, R.value
 
 
+def _config(kernel: str = "batched", chunk_log2: int = 0, smem_rows: int = 0, tile_records: int = 0,
+            ctas_per_sm: int = 0, small_segment: int = 0, smem_mode: int = 0, no_graph: int = 0) -> Config:
+    cfg = Config()
+    cfg.chunk_log2 = chunk_log2
+    cfg.kernel = KERNELS[kernel]
+    cfg.smem_rows = smem_rows
+    cfg.tile_records = tile_records
+    cfg.ctas_per_sm = ctas_per_sm
+    cfg.small_segment = small_segment
+    cfg.smem_mode = smem_mode
+    cfg.no_graph = no_graph
+    return cfg
+
+
+def memory_bytes(V: int, **cfg) -> int:
+    """Device bytes a handle of V nodes allocates at creation (gz_memory_bytes)."""
+    out = ctypes.c_size_t()
+    st = lib().gz_memory_bytes(V, ctypes.byref(_config(**cfg)), ctypes.byref(out))
+    if st != GZ_OK:
+        raise GzError(st, "gz_memory_bytes failed")
+    return out.value
+
+
 def int_peak(kind: str = "mixed") -> float:
     """Measured integer thread-instructions/s of the current device
     (gz_int_peak): "imad" (32-bit multiply-add), "lop3" (logic) or "mixed"."""
@@ -223,15 +246,9 @@ class Graph:
     def __init__(self, V: int, seed: int = 0, *, kernel: str = "batched", chunk_log2: int = 0,
                  smem_rows: int = 0, tile_records: int = 0, ctas_per_sm: int = 0,
                  small_segment: int = 0, smem_mode: int = 0, no_graph: int = 0, stream=None):
-        cfg = Config()
-        cfg.chunk_log2 = chunk_log2
-        cfg.kernel = KERNELS[kernel]
-        cfg.smem_rows = smem_rows
-        cfg.tile_records = tile_records
-        cfg.ctas_per_sm = ctas_per_sm
-        cfg.small_segment = small_segment
-        cfg.smem_mode = smem_mode
-        cfg.no_graph = no_graph
+        cfg = _config(kernel=kernel, chunk_log2=chunk_log2, smem_rows=smem_rows, tile_records=tile_records,
+                      ctas_per_sm=ctas_per_sm, small_segment=small_segment, smem_mode=smem_mode,
+                      no_graph=no_graph)
         self._h = ctypes.c_void_p()
         s = _current_stream() if stream is None else stream
         st = lib().gz_create(V, seed & ((1 << 64) - 1), ctypes.byref(cfg), ctypes.c_void_p(s),

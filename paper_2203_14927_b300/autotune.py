@@ -22,9 +22,9 @@ SPACE = {
     "tile_records": [256, 512, 1024, 2048],
     "smem_rows": [10, 12, 16],
     "ctas_per_sm": [0, 2, 3],
-    "chunk_log2": [23, 24, 25, 26],
+    "chunk_log2": [24, 25, 26, 27],
 }
-DEFAULT = {"smem_mode": 1, "tile_records": 512, "smem_rows": 12, "ctas_per_sm": 0, "chunk_log2": 25}
+DEFAULT = {"smem_mode": 1, "tile_records": 512, "smem_rows": 12, "ctas_per_sm": 0, "chunk_log2": 26}
 
 CACHE = os.environ.get("GZ_TUNE_CACHE",
                        os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_configs.json"))

@@ -482,9 +482,9 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                                 ca[row * 48] = 0;
                             }
                             w[64] = 0;
+                            ++n_rows;
                         }
                     }
-                    n_rows += md + 1;
                 }
             }
             pos = seg_end;

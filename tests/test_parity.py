@@ -266,3 +266,21 @@ def test_packed_index_rejects_non_canonical():
         assert ei.value.status == gz.GZ_EINVAL
     after = g.export_sketch()
     assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+
+
+def test_queries_during_the_stream_see_each_prefix():
+    # a CC query after every quarter of the stream (the experiment of Fig.
+    # query): each sees exactly the sketches of the prefix ingested so far;
+    # queries leave the sketches untouched, so ingestion simply continues
+    spec = S.PlantedSpec(V=1024, seed=21, n_comp=8, p=0.1, extra=0.2, cycles=20)
+    u, v, comp = S.planted_stream(spec)
+    g = gz.Graph(spec.V, 5, chunk_log2=14)
+    cuts = [len(u) * i // 4 for i in range(5)]
+    for i in range(1, 5):
+        g.edge_update(_dev(u[cuts[i - 1]:cuts[i]]), _dev(v[cuts[i - 1]:cuts[i]]))
+        labels, ncc, st = g.connected_components()
+        A, G = oracle.ingest(spec.V, 5, u[:cuts[i]], v[:cuts[i]])
+        want = oracle.boruvka(spec.V, 5, A, G)
+        assert np.array_equal(labels, want["labels"]), i
+        assert np.array_equal(labels, oracle.brute_cc(spec.V, u[:cuts[i]], v[:cuts[i]])), i
+    _assert_same_sketches(g, A, G)
