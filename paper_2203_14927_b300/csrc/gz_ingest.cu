@@ -800,7 +800,7 @@ gz_status ingest_batch(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, u
     } else if (!h->cfg.no_graph && h->batches_done >= 8) {
         // the captured graph pays off once a handle keeps ingesting
         if ((ps = launch_graph(h, d_u, d_v, n)) != GZ_OK) return ps;
-        h->launches += 7;
+        h->launches += 6;  // validate, 2 scan, scatter, tile table, batched
     } else {
         cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
         for (int i = 0; i < 3 && h->prof; ++i) {
@@ -809,7 +809,7 @@ gz_status ingest_batch(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, u
         }
         const uint32_t grid = (uint32_t)std::min<uint64_t>((n + 255) / 256, (uint64_t)h->sm_count * 8);
         enqueue_batched(h, d_u, d_v, n, grid, st, ev[0], ev[1], ev[2]);
-        h->launches += 7;
+        h->launches += 6;
     }
     ++h->batches_done;
     if (h->prof) {

@@ -502,7 +502,7 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
         if (n_ed == 0) break;
         if (r == h->K - 1) exhausted = 1;
         k_q_link<<<grid_for(h, n_roots, tpb), tpb, 0, stm>>>(q);
-        h->launches += 2;  // link, relabel
+        h->launches += 1;  // link
         if (want_forest) {
             uint32_t *F = h->q_F, *F2 = h->q_F2, *Mx = h->q_M, *Mx2 = h->q_M2;
             const uint32_t gR = grid_for(h, n_roots, tpb);
@@ -524,7 +524,7 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
         }
         k_q_newroot<<<grid_for(h, n_roots, tpb), tpb, 0, stm>>>(q, h->q_cursor);
         k_q_relabel<<<gV, tpb, 0, stm>>>(q, h->q_cursor);
-        h->launches += 1;
+        h->launches += 2;
     }
     k_q_ncc<<<gV, tpb, 0, stm>>>(q);
     e = cudaMemcpyAsync(h->h_ctr, h->q_ctr, C_N * sizeof(uint32_t), cudaMemcpyDeviceToHost, stm);
