@@ -43,10 +43,9 @@ CHUNK_LOG2 = 24
 
 # DRAM bytes per launch of k_batched from one ncu capture (one-pass
 # dram__bytes_read.sum + dram__bytes_write.sum) of this bench's own step; valid
-# only for the kernel sources (sha256 of gz_ingest.cu + gz_internal.cuh, first
-# 16 hex digits) and configuration it was taken with.
+# only for the kernel source it was taken with (kernel_sha) and its configuration.
 TRAFFIC = {
-    "kron17": {"sha": "2e65820e7f65d1b0",
+    "kron17": {"sha": "12b49f74df1987c5",
                "cfg": {"smem_mode": 1, "tile_records": 512, "smem_rows": 12, "ctas_per_sm": 0, "chunk_log2": 26},
                "bytes_per_launch": 10.272e9, "updates_per_launch": 66592033,
                "source": "profiles/k_batched_kron17_dram.md"},
@@ -54,13 +53,19 @@ TRAFFIC = {
 
 
 def kernel_sha() -> str:
+    """Fingerprint of the batched kernel's device code: its section of
+    gz_ingest.cu (from the "batched update" banner to the dispatch table) and
+    gz_internal.cuh."""
     import hashlib
 
-    h = hashlib.sha256()
-    for f in ("gz_ingest.cu", "gz_internal.cuh"):
-        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2203_14927_b300", "csrc", f),
-                  "rb") as fh:
-            h.update(fh.read())
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2203_14927_b300", "csrc")
+    with open(os.path.join(d, "gz_ingest.cu")) as fh:
+        src = fh.read()
+    lo = src.index("// ------------------------------------------------------------------ batched update")
+    hi = src.index("using BatchedFn = void (*)(BatchedArgs);")
+    h = hashlib.sha256(src[lo:hi].encode())
+    with open(os.path.join(d, "gz_internal.cuh"), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:16]
 
 
