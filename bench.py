@@ -820,13 +820,84 @@ def run_stream_queries(args, rank: int, world: int):
     print(json.dumps(out), flush=True)
 
 
+# Fig. l0speedup, single-threaded CPU rates of the paper (updates/s):
+# vector length -> (standard l0, CubeSketch)
+PAPER_L0 = {10 ** 3: (223000, 7322000), 10 ** 4: (124000, 5180000), 10 ** 5: (54800, 4384000),
+            10 ** 6: (29300, 3730000), 10 ** 7: (20900, 3177000), 10 ** 8: (16300, 2825000),
+            10 ** 9: (13100, 2587000), 10 ** 10: (1350, 2272000), 10 ** 11: (918, 2108000),
+            10 ** 12: (833, 1963000)}
+
+
+def run_l0(args, rank: int, world: int):
+    """Micro-benchmark of Fig. l0speedup on the GPU: ingestion rate of the
+    standard l0 sampler (Fig. agm_code) and of CubeSketch into vector sketches
+    of length n = 1e3 .. 1e12, many independent sketches at once (one thread
+    per sketch column), with the CPU oracle's single-thread rates beside them."""
+    import torch
+
+    import oracle
+    import paper_2203_14927_b300 as gz
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda")
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    sketches, m, seed = sm * 256, 256, 42
+    rows = []
+    for e in range(3, 13):
+        n = 10 ** e
+        gen = torch.Generator(device=dev).manual_seed(e)
+        x = torch.randint(1, n + 1, (sketches, m), device=dev, generator=gen, dtype=torch.int64)
+        dl = (torch.randint(0, 2, (sketches, m), device=dev, generator=gen, dtype=torch.int32) * 2 - 1)
+        R, bc, bs = gz.l0_geometry(n)
+        rec = {"n": n, "rows": R}
+        for kind, name, nb in ((gz.L0_CUBE, "cubesketch", bc), (gz.L0_STANDARD, "standard", bs)):
+            buf = torch.zeros(sketches * nb, dtype=torch.uint8, device=dev)
+            gz.l0_update(kind, n, seed, x, buf, dl)  # warm-up
+            best = float("inf")
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                gz.l0_update(kind, n, seed, x, buf, dl)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1000.0)
+            rec[f"gpu_{name}_updates_per_s"] = sketches * m / best
+            # CPU oracle, single thread, bounded sample
+            xs = x[0].cpu().numpy().view(np.uint64)
+            ds = dl[0].cpu().numpy()
+            t0, k = time.perf_counter(), 0
+            while time.perf_counter() - t0 < args.l0_cpu_seconds:
+                oracle.l0_update(kind, n, seed, xs, ds)
+                k += len(xs)
+            rec[f"cpu_oracle_{name}_updates_per_s"] = k / (time.perf_counter() - t0)
+        rec["gpu_speedup_cube_over_standard"] = (rec["gpu_cubesketch_updates_per_s"]
+                                                 / rec["gpu_standard_updates_per_s"])
+        rec["paper_cpu_standard"], rec["paper_cpu_cubesketch"] = PAPER_L0[n]
+        rows.append(rec)
+        log(f"[l0] n=1e{e}: GPU cube {rec['gpu_cubesketch_updates_per_s'] / 1e9:.2f} G/s, "
+            f"standard {rec['gpu_standard_updates_per_s'] / 1e9:.3f} G/s "
+            f"({rec['gpu_speedup_cube_over_standard']:.1f}x)")
+    out = {
+        "metric": "l0_updates_per_sec", "value": rows[-1]["gpu_cubesketch_updates_per_s"], "unit": "updates/s",
+        "n_gpus": 1, "steps": 3, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic: uniform positions, +-1 deltas",
+        "config": {"workload": "Fig. l0speedup on the GPU: vector sketches of length 1e3..1e12, "
+                               f"{sketches} sketches x {m} updates, 7 columns, thread per column",
+                   "value": "CubeSketch rate at n = 1e12"},
+        "per_length": rows,
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve", "failures", "stream_queries"],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve", "failures", "stream_queries", "l0"],
                     default="kron17")
     ap.add_argument("--seeds", type=int, default=20)
     ap.add_argument("--fail-workload", choices=sorted(WORKLOADS), default="kron17")
@@ -838,6 +909,7 @@ def main():
     ap.add_argument("--paper-design-log2", type=int, default=22,
                     help="stream prefix (log2 updates) for the OpenMP paper-design CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--l0-cpu-seconds", type=float, default=0.5)
     ap.add_argument("--ref-seconds", type=float, default=40.0)
     ap.add_argument("--e2e-log2", type=int, default=28)
     ap.add_argument("--plain-log2", type=int, default=26)
@@ -850,7 +922,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
-        if args.workload in ("serve", "failures", "stream_queries"):
+        if args.workload in ("serve", "failures", "stream_queries", "l0"):
             args.workload = "kron17"
         run_reference(args, rank, world)
     elif args.workload == "serve":
@@ -859,6 +931,8 @@ def main():
         run_failures(args, rank, world)
     elif args.workload == "stream_queries":
         run_stream_queries(args, rank, world)
+    elif args.workload == "l0":
+        run_l0(args, rank, world)
     else:
         run_ours(args, rank, world)
 

@@ -349,6 +349,39 @@ gz_status gz_sketch_update_noalloc(void *sketch, uint32_t V, uint64_t seed,
 const char *gz_last_error(gz_handle *h);
 
 /* Library version string. */
+/* Single-vector l0 sketches, for the micro-benchmark of Fig. l0speedup: the
+ * standard l0 sampler of Fig. agm_code (Section 3.1) beside CubeSketch
+ * (Fig. cube_code) on a plain vector of length n.  Both use 7 columns and
+ * R = ceil(log2 n) rows, column keys a_j = SM(seed,3j)|1, b_j = SM(seed,3j+1),
+ * c_j = SM(seed,3j+2) (SplitMix64), and put position x into rows 0..d,
+ * d = min(clz64(a_j*x + b_j), R-1) (nested rows, as in both figures).
+ *   GZ_L0_CUBE     bucket (alpha u64, gamma u32): alpha ^= x,
+ *                  gamma ^= fmix32(fold(x) ^ lo32(c_j)).
+ *                  Layout per sketch: alpha[7][R] then gamma[7][R], padded
+ *                  to a multiple of 8 bytes (84R rounded up).
+ *   GZ_L0_STANDARD bucket (a, b, c), u64 each: a += x*delta, b += delta
+ *                  (two's complement), c = (c + delta * r_j^x) mod p with
+ *                  p = 2^61 - 1 and r_j = 1 + c_j mod (p - 1).
+ *                  Layout per sketch: a[7][R], b[7][R], c[7][R]. */
+#define GZ_L0_CUBE 0
+#define GZ_L0_STANDARD 1
+
+/* rows R and the bytes of one sketch of each kind for vector length n >= 2 */
+gz_status gz_l0_geometry(uint64_t n, uint32_t *rows, uint32_t *bytes_cube, uint32_t *bytes_standard);
+
+/* Apply m updates to each of `sketches` independent sketches of one kind.
+ *   x       : device, sketches*m positions in 1..n, sketch-major (sketch s
+ *             takes x[s*m .. s*m+m), in that order).
+ *   delta   : device, sketches*m values +1 or -1, or NULL for all +1
+ *             (CubeSketch ignores it: a delete is the same toggle).
+ *   buckets : device, sketches * bytes-per-sketch, updated in place.
+ *   stream  : cudaStream_t of the work (NULL = default stream); asynchronous.
+ * Positions outside 1..n and deltas other than +-1 are not checked on the
+ * device; they give meaningless buckets, not faults.  Returns GZ_EINVAL for an
+ * unknown kind, n < 2 or n >= 2^61, or null buffers. */
+gz_status gz_l0_update(int kind, uint64_t n, uint64_t seed, uint32_t sketches, uint32_t m,
+                       const uint64_t *x, const int32_t *delta, void *buckets, void *stream);
+
 /* Measured integer throughput of the current device, the ceiling of the
  * batched update kernel (its work per (record, column) pair is integer only):
  * kind 0 = 32-bit multiply-add, 1 = three-input logic op, 2 = the two

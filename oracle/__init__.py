@@ -21,6 +21,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gz_oracle.c")
 _SRC_BATCHED = os.path.join(_HERE, "gz_cpu_batched.c")
+_SRC_L0 = os.path.join(_HERE, "gz_oracle_l0.c")
 _LIB = os.path.join(_HERE, "libgz_oracle.so")
 
 COLS = 7
@@ -33,7 +34,7 @@ NOT_RUN = -4
 def build(force: bool = False) -> str:
     """Compile gz_oracle.c (and the paper-design CPU baseline gz_cpu_batched.c,
     OpenMP) into libgz_oracle.so (plain gcc, -O2)."""
-    srcs = [_SRC, _SRC_BATCHED]
+    srcs = [_SRC, _SRC_L0, _SRC_BATCHED]
     if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(s) for s in srcs):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-Wextra", "-fopenmp", "-shared",
@@ -78,6 +79,16 @@ def lib():
         L.gzo_brute_cc.argtypes = [u32, sz, p, p, p]
         L.gzo_cc_edges.restype = ctypes.c_int
         L.gzo_cc_edges.argtypes = [u32, sz, p, p, p]
+        L.gzo_l0_rows.restype = u32
+        L.gzo_l0_rows.argtypes = [u64]
+        L.gzo_mulmod61.restype = u64
+        L.gzo_mulmod61.argtypes = [u64, u64]
+        L.gzo_powmod61.restype = u64
+        L.gzo_powmod61.argtypes = [u64, u64]
+        L.gzo_l0_update.restype = ctypes.c_int
+        L.gzo_l0_update.argtypes = [ctypes.c_int, u64, u64, sz, p, p, p]
+        L.gzo_l0_query.restype = ctypes.c_int64
+        L.gzo_l0_query.argtypes = [ctypes.c_int, u64, u64, p, p]
         L.gzb_ingest_batched.restype = ctypes.c_int
         L.gzb_ingest_batched.argtypes = [u32, u64, sz, p, p, u32, u32, p, p, ctypes.c_int, sz]
         L.gzb_max_threads.restype = ctypes.c_int
@@ -154,6 +165,55 @@ def ingest_batched(V: int, seed: int, u, v, node_lo: int = 0, node_hi: int | Non
     if rc != 0:
         raise ValueError(f"gzb_ingest_batched failed ({rc})")
     return alpha, gamma
+
+
+# ---- single-vector l0 sketches (Fig. agm_code standard sampler, Fig. cube_code)
+
+L0_CUBE, L0_STANDARD = 0, 1
+P61 = (1 << 61) - 1
+
+
+def l0_rows(n: int) -> int:
+    return int(lib().gzo_l0_rows(n))
+
+
+def l0_bytes(kind: int, n: int) -> int:
+    """Bytes of one vector sketch: CubeSketch 7R x 12 padded to a multiple of 8
+    (trailing zero bytes), standard 7R x 24."""
+    R = l0_rows(n)
+    return (84 * R + 7) // 8 * 8 if kind == L0_CUBE else 168 * R
+
+
+def mulmod61(x: int, y: int) -> int:
+    return int(lib().gzo_mulmod61(x, y))
+
+
+def powmod61(r: int, e: int) -> int:
+    return int(lib().gzo_powmod61(r, e))
+
+
+def l0_update(kind: int, n: int, seed: int, x, delta=None, buckets=None) -> np.ndarray:
+    """Apply updates (x[i], delta[i] = +-1) to one vector sketch; returns its
+    bytes (a fresh zero sketch when buckets is None)."""
+    x = np.ascontiguousarray(x, np.uint64)
+    if buckets is None:
+        buckets = np.zeros(l0_bytes(kind, n), np.uint8)
+    dptr = None
+    if delta is not None:
+        delta = np.ascontiguousarray(delta, np.int32)
+        dptr = _ptr(delta)
+    rc = lib().gzo_l0_update(kind, n, seed, len(x), _ptr(x), dptr, _ptr(buckets))
+    if rc != 0:
+        raise ValueError("invalid l0 update")
+    return buckets
+
+
+def l0_query(kind: int, n: int, seed: int, buckets: np.ndarray):
+    """(position, value) sampled from one vector sketch; position -1 = EMPTY,
+    -2 = FAIL."""
+    val = np.zeros(1, np.int64)
+    pos = int(lib().gzo_l0_query(kind, n, seed, _ptr(buckets), _ptr(val)))
+    return pos, int(val[0])
 
 
 def max_threads() -> int:

@@ -107,6 +107,10 @@ _SIGNATURES = {
                                       ctypes.c_int]),
     "gz_edge_update_idx": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]),
     "gz_int_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p]),
+    "gz_l0_geometry": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gz_l0_update": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                    ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p]),
     "gz_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "gz_reset": (ctypes.c_int, [ctypes.c_void_p]),
     "gz_connected_components": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -207,6 +211,31 @@ def int_peak(kind: str = "mixed") -> float:
     if st != GZ_OK:
         raise GzError(st, "gz_int_peak failed")
     return out.value
+
+
+L0_CUBE, L0_STANDARD = 0, 1
+
+
+def l0_geometry(n: int) -> tuple[int, int, int]:
+    """(rows, bytes of a CubeSketch, bytes of a standard sketch) for length n."""
+    r, bc, bs = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    st = lib().gz_l0_geometry(n, ctypes.byref(r), ctypes.byref(bc), ctypes.byref(bs))
+    if st != GZ_OK:
+        raise GzError(st, f"gz_l0_geometry(n={n}) failed")
+    return r.value, bc.value, bs.value
+
+
+def l0_update(kind: int, n: int, seed: int, x, buckets, delta=None, stream=None):
+    """Apply x (torch int64 CUDA tensor, [sketches, m]) with optional +-1 deltas
+    (int32, same shape) to `sketches` vector sketches in `buckets` (a CUDA
+    tensor of sketches * bytes-per-sketch bytes); asynchronous."""
+    sketches, m = x.shape
+    s = _current_stream() if stream is None else stream
+    st = lib().gz_l0_update(kind, n, seed & ((1 << 64) - 1), sketches, m, ctypes.c_void_p(x.data_ptr()),
+                            ctypes.c_void_p(delta.data_ptr() if delta is not None else None),
+                            ctypes.c_void_p(buckets.data_ptr()), ctypes.c_void_p(s))
+    if st != GZ_OK:
+        raise GzError(st, "gz_l0_update failed")
 
 
 def _buffer(x, bits: int = 32):
