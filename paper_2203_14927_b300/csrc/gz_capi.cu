@@ -178,7 +178,9 @@ gz_status gz_destroy(gz_handle* h) {
                     h->q_acc, h->q_trace, h->d_stats, h->d_scan_tmp, h->d_tile_node, h->d_decode};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, h->stream);
-    delete[] h->h_ctr;
+    if (h->h_ctr) cudaFreeHost(h->h_ctr);
+    if (h->q_graph_exec) cudaGraphExecDestroy(h->q_graph_exec);
+    if (h->q_graph) cudaGraphDestroy(h->q_graph);
     for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
     for (int b = 0; b < 2; ++b) {
         if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);

@@ -31,12 +31,18 @@
 
 namespace gz {
 
-enum { C_ROOTS = 0, C_BIG = 1, C_EDGES = 2, C_FAILS = 3, C_FOREST = 4, C_NCC = 5, C_N = 8 };
+// device counters of a query: per round (roots, large components, sampled
+// edges, FAIL results), per query (forest edges, components), the round index
+// and the loop decision, and the statistics of the rounds run so far
+enum {
+    C_ROOTS = 0, C_BIG = 1, C_EDGES = 2, C_FAILS = 3, C_FOREST = 4, C_NCC = 5, C_ROUND = 6, C_GO = 7,
+    C_ROUNDS = 8, C_FLAST = 9, C_FTOT = 10, C_EXH = 11, C_N = 12
+};
 
 struct QArgs {
     SketchView s;
     const uint64_t* kc;  // checksum keys, 7K
-    uint32_t V, K, R, round, M;
+    uint32_t V, K, R, M;  // the round index lives in ctr[C_ROUND]
     uint32_t *label, *parent, *count, *off, *cursor, *members, *roots, *target;
     uint32_t* slot;     // accumulator slot of a component with more than M members
     uint64_t* acc;      // slots x (21R/2) words, zero between rounds
@@ -84,9 +90,25 @@ __global__ void k_q_init(QArgs q) {
         q.roots[v] = v;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int i = 0; i < C_N; ++i) q.ctr[i] = 0;
         q.ctr[C_ROOTS] = q.V;
-        q.ctr[C_BIG] = 0;
     }
+}
+
+// End of round r = ctr[C_ROUND]: record the round's statistics, decide
+// whether another round runs (a sampled edge and a fresh CubeSketch left), and
+// advance the round index.  With use_cond the decision also sets the
+// condition of the graph's WHILE node.
+__global__ void k_q_next(QArgs q, cudaGraphConditionalHandle cond, int use_cond) {
+    const uint32_t r = q.ctr[C_ROUND], e = q.ctr[C_EDGES], f = q.ctr[C_FAILS];
+    q.ctr[C_ROUNDS] = r + 1;
+    q.ctr[C_FLAST] = f;
+    q.ctr[C_FTOT] += f;
+    if (e > 0 && r + 1 == q.K) q.ctr[C_EXH] = 1;
+    const uint32_t go = e > 0 && r + 1 < q.K;
+    q.ctr[C_GO] = go;
+    q.ctr[C_ROUND] = r + 1;
+    if (use_cond) cudaGraphSetConditional(cond, go);
 }
 
 __global__ void k_fill64(int64_t* p, uint64_t n, int64_t val) {
@@ -127,7 +149,7 @@ __global__ void k_q_group(QArgs q) {
 // Root list (one append per warp) and an accumulator slot for every
 // component with more than M members.
 __global__ void k_q_roots(QArgs q) {
-    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t lane = threadIdx.x & 31, round = q.ctr[C_ROUND];
     for (uint32_t b = blockIdx.x * blockDim.x; b < q.V; b += gridDim.x * blockDim.x) {
         const uint32_t c = b + threadIdx.x;
         const uint32_t cnt = c < q.V ? q.count[c] : 0u;
@@ -137,7 +159,7 @@ __global__ void k_q_roots(QArgs q) {
         base = __shfl_sync(0xffffffffu, base, 0);
         if (cnt > 0) q.roots[base + __popc(bal & ((1u << lane) - 1u))] = c;
         if (cnt > q.M) q.slot[c] = atomicAdd(&q.ctr[C_BIG], 1u);
-        if (c < q.V && cnt == 0 && q.trace) q.trace[(uint64_t)q.round * q.V + c] = -3;
+        if (c < q.V && cnt == 0 && q.trace) q.trace[(uint64_t)round * q.V + c] = -3;
     }
 }
 
@@ -145,10 +167,10 @@ __global__ void k_q_roots(QArgs q) {
 // than M members, into that component's accumulator slot.  The members array
 // is grouped by component, so a chunk of M consecutive members meets at most
 // two such components: one that covers its start, one that covers its end.
-__global__ void __launch_bounds__(384) k_q_merge(QArgs q) {
+__global__ void __launch_bounds__(1024) k_q_merge(QArgs q) {
     __shared__ uint32_t s_node[kMergeChunk];
     const uint32_t nw = 21u * q.R / 2u;  // u64 words of one CubeSketch (84R bytes)
-    const uint32_t M = q.M, nchunks = (q.V + M - 1) / M;
+    const uint32_t M = q.M, nchunks = (q.V + M - 1) / M, round = q.ctr[C_ROUND];
     for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
         const uint32_t lo = ch * M, hi = min(q.V, lo + M);
         const uint32_t cA = q.label[q.members[lo]], cB = q.label[q.members[hi - 1]];
@@ -167,14 +189,14 @@ __global__ void __launch_bounds__(384) k_q_merge(QArgs q) {
                 uint64_t x = 0;
 #pragma unroll 8
                 for (uint32_t m = 0; m < eA; ++m)
-                    x ^= __ldg(reinterpret_cast<const uint64_t*>(q.s.cube(s_node[m], q.round)) + w);
+                    x ^= __ldg(reinterpret_cast<const uint64_t*>(q.s.cube(s_node[m], round)) + w);
                 atomicXor(reinterpret_cast<unsigned long long*>(accA + w), (unsigned long long)x);
             }
             if (bigB) {
                 uint64_t x = 0;
 #pragma unroll 8
                 for (uint32_t m = sB; m < hi - lo; ++m)
-                    x ^= __ldg(reinterpret_cast<const uint64_t*>(q.s.cube(s_node[m], q.round)) + w);
+                    x ^= __ldg(reinterpret_cast<const uint64_t*>(q.s.cube(s_node[m], round)) + w);
                 atomicXor(reinterpret_cast<unsigned long long*>(accB + w), (unsigned long long)x);
             }
         }
@@ -198,7 +220,7 @@ __global__ void __launch_bounds__(256) k_q_sample(QArgs q) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    const uint32_t R = q.R, n_roots = q.ctr[C_ROOTS], nw = 21u * R / 2u;
+    const uint32_t R = q.R, n_roots = q.ctr[C_ROOTS], nw = 21u * R / 2u, round = q.ctr[C_ROUND];
     const uint64_t VV = (uint64_t)q.V * q.V;
     const uint32_t r0 = lane, r1 = lane + 32;
     for (uint32_t ri = warp; ri < n_roots; ri += nwarps) {
@@ -218,7 +240,7 @@ __global__ void __launch_bounds__(256) k_q_sample(QArgs q) {
         for (uint32_t sidx = 0; sidx < nsrc; ++sidx) {
             const uint64_t* A;
             if (big) A = slot_base;
-            else A = reinterpret_cast<const uint64_t*>(q.s.cube(__shfl_sync(0xffffffffu, my_node, sidx), q.round));
+            else A = reinterpret_cast<const uint64_t*>(q.s.cube(__shfl_sync(0xffffffffu, my_node, sidx), round));
             const uint32_t* G = reinterpret_cast<const uint32_t*>(A + GZ_COLS * R);
 #pragma unroll
             for (int j = 0; j < GZ_COLS; ++j) {
@@ -273,7 +295,7 @@ __global__ void __launch_bounds__(256) k_q_sample(QArgs q) {
             const uint32_t carry_g = __shfl_sync(0xffffffffu, y1, 0);
             x0 ^= carry_a;
             y0 ^= carry_g;
-            const uint64_t kcj = q.kc[q.round * GZ_COLS + j];
+            const uint64_t kcj = q.kc[round * GZ_COLS + j];
             auto good = [&](uint64_t a, uint32_t g, uint32_t row) -> bool {
                 if (row >= R || (a | g) == 0) return false;
                 if (g != checksum_pre(kcj, a) || a >= VV) return false;
@@ -303,7 +325,7 @@ __global__ void __launch_bounds__(256) k_q_sample(QArgs q) {
                 r = -1;
             }
             q.res[c] = r;
-            if (q.trace) q.trace[(uint64_t)q.round * q.V + c] = r;
+            if (q.trace) q.trace[(uint64_t)round * q.V + c] = r;
         }
     }
 }
@@ -416,10 +438,7 @@ gz_status query_setup(gz_handle* h) {
     if (e == cudaSuccess) e = alloc32(&h->q_ctr, C_N);
     if (e == cudaSuccess) e = cudaMallocAsync(&h->q_res, V * sizeof(int64_t), h->stream);
     if (e == cudaSuccess) e = cudaMallocAsync(&h->q_acc, (size_t)h->q_slots_cap * h->per_k_bytes, h->stream);
-    if (e == cudaSuccess) {
-        h->h_ctr = new (std::nothrow) uint32_t[C_N];
-        if (!h->h_ctr) return set_error(h, GZ_ENOMEM, "query counters");
-    }
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_ctr, C_N * sizeof(uint32_t));  // pinned: read in a graph
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_check(h, e, "query scratch allocation");
     h->query_ready = true;
@@ -430,16 +449,7 @@ static inline uint32_t grid_for(const gz_handle* h, uint64_t n, uint32_t tpb) {
     return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((n + tpb - 1) / tpb, (uint64_t)h->sm_count * 8));
 }
 
-gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* forest_uv,
-                  size_t* n_edges, uint32_t* n_cc, gz_query_stats* st) {
-    auto t0 = std::chrono::steady_clock::now();
-    gz_status s = query_setup(h);
-    if (s != GZ_OK) return s;
-    if (h->trace && !h->q_trace) {
-        cudaError_t e = cudaMallocAsync(&h->q_trace, (size_t)h->K * h->V * sizeof(int64_t), h->stream);
-        if (e != cudaSuccess) return cuda_check(h, e, "trace allocation");
-    }
-    cudaStream_t stm = h->stream;
+static QArgs query_args(gz_handle* h) {
     QArgs q;
     q.s.base = h->d_sketch;
     q.s.node_bytes = h->node_bytes;
@@ -463,77 +473,200 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
     q.res = h->q_res;
     q.trace = h->trace ? h->q_trace : nullptr;
     q.ctr = h->q_ctr;
+    return q;
+}
 
-    const uint32_t V = h->V, tpb = 256;
-    const uint32_t gV = grid_for(h, V, tpb);
-    k_q_init<<<gV, tpb, 0, stm>>>(q);
-    h->launches += 2 + (q.trace ? 1 : 0);  // init, final count (+ trace fill)
-    if (q.trace) k_fill64<<<grid_for(h, (uint64_t)h->K * V, tpb), tpb, 0, stm>>>(q.trace, (uint64_t)h->K * V, -4);
-    cudaError_t e = cudaMemsetAsync(h->q_ctr + C_EDGES, 0, (C_N - C_EDGES) * sizeof(uint32_t), stm);
-    // the sampler clears every slot it reads; this only guards against a query
-    // that stopped on an error between a merge and its sampler
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->q_acc, 0, (size_t)h->q_slots_cap * h->per_k_bytes, stm);
-    if (e != cudaSuccess) return cuda_check(h, e, "memset counters");
+constexpr uint32_t kTpb = 256;
 
-    uint32_t rounds = 0, fails_last = 0, fails_total = 0, exhausted = 0;
-    for (uint32_t r = 0; r < h->K; ++r) {
-        q.round = r;
-        rounds = r + 1;
-        if (r > 0) {
-            // group vertices by component (round 0 starts from singletons)
-            e = cudaMemsetAsync(h->q_count, 0, (size_t)(V + 1) * sizeof(uint32_t), stm);
-            if (e == cudaSuccess) e = cudaMemsetAsync(h->q_ctr, 0, 4 * sizeof(uint32_t), stm);  // roots..fails
-            if (e != cudaSuccess) return cuda_check(h, e, "memset round");
-            k_q_count<<<gV, tpb, 0, stm>>>(q);
-            launch_scan(h->q_count, h->q_off, h->q_cursor, V, stm, h->d_scan_tmp);
-            k_q_group<<<gV, tpb, 0, stm>>>(q);
-            k_q_roots<<<gV, tpb, 0, stm>>>(q);
-            k_q_merge<<<std::min<uint32_t>((V + kMergeChunk - 1) / kMergeChunk, h->sm_count * 5), 384, 0, stm>>>(q);
-            h->launches += 6;
-        }
-        k_q_sample<<<h->sm_count * 16, 256, 0, stm>>>(q);
-        h->launches += 1;
-        e = cudaMemcpyAsync(h->h_ctr, h->q_ctr, C_N * sizeof(uint32_t), cudaMemcpyDeviceToHost, stm);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stm);
-        if (e != cudaSuccess) return cuda_check(h, e, "query round");
-        const uint32_t n_roots = h->h_ctr[C_ROOTS], n_ed = h->h_ctr[C_EDGES], n_fail = h->h_ctr[C_FAILS];
-        fails_last = n_fail;
-        fails_total += n_fail;
-        if (n_ed == 0) break;
-        if (r == h->K - 1) exhausted = 1;
-        k_q_link<<<grid_for(h, n_roots, tpb), tpb, 0, stm>>>(q);
-        h->launches += 1;  // link
-        if (want_forest) {
-            uint32_t *F = h->q_F, *F2 = h->q_F2, *Mx = h->q_M, *Mx2 = h->q_M2;
-            const uint32_t gR = grid_for(h, n_roots, tpb);
-            k_q_fj_init<<<gR, tpb, 0, stm>>>(q, F, Mx, h->q_flag);
-            uint32_t J = 1;
-            while ((1ull << (J - 1)) < (uint64_t)n_roots) ++J;
-            for (uint32_t it = 0; it < J; ++it) {
-                k_q_fj_step<<<gR, tpb, 0, stm>>>(q, F, Mx, F2, Mx2);
-                std::swap(F, F2);
-                std::swap(Mx, Mx2);
+// query start: singletons, counters, clear accumulator slots (the sampler
+// clears every slot it reads; this only guards against a query that stopped
+// on an error between a merge and its sampler)
+static void enqueue_start(gz_handle* h, const QArgs& q, cudaStream_t stm) {
+    k_q_init<<<grid_for(h, h->V, kTpb), kTpb, 0, stm>>>(q);
+    cudaMemsetAsync(h->q_acc, 0, (size_t)h->q_slots_cap * h->per_k_bytes, stm);
+}
+
+// group vertices by component and merge the large components (rounds > 0;
+// round 0 starts from singletons)
+static void enqueue_grouping(gz_handle* h, const QArgs& q, cudaStream_t stm) {
+    const uint32_t V = h->V, gV = grid_for(h, V, kTpb);
+    cudaMemsetAsync(h->q_count, 0, (size_t)(V + 1) * sizeof(uint32_t), stm);
+    cudaMemsetAsync(h->q_ctr, 0, 4 * sizeof(uint32_t), stm);  // roots, big, edges, fails
+    k_q_count<<<gV, kTpb, 0, stm>>>(q);
+    launch_scan(h->q_count, h->q_off, h->q_cursor, V, stm, h->d_scan_tmp);
+    k_q_group<<<gV, kTpb, 0, stm>>>(q);
+    k_q_roots<<<gV, kTpb, 0, stm>>>(q);
+    // one thread per word of a CubeSketch (one pass over its 21R/2 words)
+    const uint32_t mt = std::min<uint32_t>(1024, (21u * h->R / 2u + 31) / 32 * 32);
+    k_q_merge<<<std::min<uint32_t>((V + kMergeChunk - 1) / kMergeChunk, h->sm_count * (2048 / mt)), mt, 0, stm>>>(q);
+}
+
+static void enqueue_sample(gz_handle* h, const QArgs& q, cudaStream_t stm) {
+    k_q_sample<<<h->sm_count * 16, 256, 0, stm>>>(q);
+}
+
+static void enqueue_link(gz_handle* h, const QArgs& q, cudaStream_t stm) {
+    k_q_link<<<grid_for(h, h->V, kTpb), kTpb, 0, stm>>>(q);
+}
+
+// new component of every old root, then every vertex follows its old root
+// (no-ops after a round without a sampled edge: no union happened)
+static void enqueue_relabel(gz_handle* h, const QArgs& q, cudaStream_t stm) {
+    const uint32_t gV = grid_for(h, h->V, kTpb);
+    k_q_newroot<<<gV, kTpb, 0, stm>>>(q, h->q_cursor);
+    k_q_relabel<<<gV, kTpb, 0, stm>>>(q, h->q_cursor);
+}
+
+// kernels of a query run as one CUDA graph: start, round 0, WHILE(another
+// round) { round }, component count and counters to the host
+constexpr uint64_t kLaunchesStartEnd = 2, kLaunchesRound0 = 5, kLaunchesRound = 11;
+
+// The CC query as one CUDA graph, captured once per handle: round 0, then a
+// conditional WHILE node whose body is one more round; k_q_next at the end of
+// every round sets the node's condition on the device, so the host waits once
+// per query instead of once per round.
+static gz_status build_query_graph(gz_handle* h) {
+    const QArgs q = query_args(h);
+    cudaStream_t cs = nullptr, bs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    cudaGraph_t cg = nullptr;
+    cudaGraphConditionalHandle cond = 0;
+    if (e == cudaSuccess) {
+        enqueue_start(h, q, cs);
+        enqueue_sample(h, q, cs);
+        enqueue_link(h, q, cs);
+        enqueue_relabel(h, q, cs);
+        cudaStreamCaptureStatus cst;
+        e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, nullptr, nullptr, nullptr);
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, cg, 0, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess) k_q_next<<<1, 1, 0, cs>>>(q, cond, 1);
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &nd);
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode = nullptr;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, cg, deps, nullptr, nd, &cp);
+        if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1,
+                                                                      cudaStreamSetCaptureDependencies);
+        if (e == cudaSuccess) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                enqueue_grouping(h, q, bs);
+                enqueue_sample(h, q, bs);
+                enqueue_link(h, q, bs);
+                enqueue_relabel(h, q, bs);
+                k_q_next<<<1, 1, 0, bs>>>(q, cond, 1);
+                e = cudaStreamEndCapture(bs, &body);
             }
-            k_q_fj_mark<<<gR, tpb, 0, stm>>>(q, F, Mx, h->q_flag);
-            // q_cursor is free again: reuse it for the accept flags
-            k_q_accept<<<gV, tpb, 0, stm>>>(q, h->q_flag, h->q_cursor);
-            launch_scan(h->q_cursor, h->q_pos, nullptr, V, stm, h->d_scan_tmp);
-            k_q_forest_write<<<gV, tpb, 0, stm>>>(q, h->q_cursor, h->q_pos, h->q_forest);
-            k_q_forest_advance<<<1, 1, 0, stm>>>(q, h->q_pos);
-            h->launches += J + 7;
         }
-        k_q_newroot<<<grid_for(h, n_roots, tpb), tpb, 0, stm>>>(q, h->q_cursor);
-        k_q_relabel<<<gV, tpb, 0, stm>>>(q, h->q_cursor);
-        h->launches += 2;
+        if (e == cudaSuccess) {
+            k_q_ncc<<<grid_for(h, h->V, kTpb), kTpb, 0, cs>>>(q);
+            e = cudaMemcpyAsync(h->h_ctr, h->q_ctr, C_N * sizeof(uint32_t), cudaMemcpyDeviceToHost, cs);
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->q_graph_exec, g, 0);
+        if (g) h->q_graph = g;
     }
-    k_q_ncc<<<gV, tpb, 0, stm>>>(q);
-    e = cudaMemcpyAsync(h->h_ctr, h->q_ctr, C_N * sizeof(uint32_t), cudaMemcpyDeviceToHost, stm);
+    if (bs) cudaStreamDestroy(bs);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (h->q_graph_exec) cudaGraphExecDestroy(h->q_graph_exec);
+        if (h->q_graph) cudaGraphDestroy(h->q_graph);
+        h->q_graph_exec = nullptr;
+        h->q_graph = nullptr;
+        return cuda_check(h, e, "query graph capture");
+    }
+    return GZ_OK;
+}
+
+gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* forest_uv,
+                  size_t* n_edges, uint32_t* n_cc, gz_query_stats* st) {
+    auto t0 = std::chrono::steady_clock::now();
+    gz_status s = query_setup(h);
+    if (s != GZ_OK) return s;
+    if (h->trace && !h->q_trace) {
+        cudaError_t e = cudaMallocAsync(&h->q_trace, (size_t)h->K * h->V * sizeof(int64_t), h->stream);
+        if (e != cudaSuccess) return cuda_check(h, e, "trace allocation");
+    }
+    cudaStream_t stm = h->stream;
+    const QArgs q = query_args(h);
+    const uint32_t V = h->V;
+    cudaError_t e = cudaSuccess;
+
+    if (!want_forest && !h->trace) {
+        if (!h->q_graph_exec && (s = build_query_graph(h)) != GZ_OK) return s;
+        e = cudaGraphLaunch(h->q_graph_exec, stm);
+    } else {
+        // forest or trace: the same rounds driven from the host, which reads
+        // the round's counters after the sampler (the forest kernels are sized
+        // by the number of components)
+        enqueue_start(h, q, stm);
+        if (q.trace) k_fill64<<<grid_for(h, (uint64_t)h->K * V, kTpb), kTpb, 0, stm>>>(q.trace, (uint64_t)h->K * V, -4);
+        h->launches += 1 + (q.trace ? 1 : 0);
+        for (uint32_t r = 0; r < h->K && e == cudaSuccess; ++r) {
+            if (r > 0) {
+                enqueue_grouping(h, q, stm);
+                h->launches += 6;
+            }
+            enqueue_sample(h, q, stm);
+            e = cudaMemcpyAsync(h->h_ctr, h->q_ctr, C_N * sizeof(uint32_t), cudaMemcpyDeviceToHost, stm);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(stm);
+            if (e != cudaSuccess) break;
+            const uint32_t n_roots = h->h_ctr[C_ROOTS], n_ed = h->h_ctr[C_EDGES];
+            if (n_ed > 0) {
+                enqueue_link(h, q, stm);
+                if (want_forest) {
+                    uint32_t *F = h->q_F, *F2 = h->q_F2, *Mx = h->q_M, *Mx2 = h->q_M2;
+                    const uint32_t gR = grid_for(h, n_roots, kTpb), gV = grid_for(h, V, kTpb);
+                    k_q_fj_init<<<gR, kTpb, 0, stm>>>(q, F, Mx, h->q_flag);
+                    uint32_t J = 1;
+                    while ((1ull << (J - 1)) < (uint64_t)n_roots) ++J;
+                    for (uint32_t it = 0; it < J; ++it) {
+                        k_q_fj_step<<<gR, kTpb, 0, stm>>>(q, F, Mx, F2, Mx2);
+                        std::swap(F, F2);
+                        std::swap(Mx, Mx2);
+                    }
+                    k_q_fj_mark<<<gR, kTpb, 0, stm>>>(q, F, Mx, h->q_flag);
+                    // q_cursor is free again: reuse it for the accept flags
+                    k_q_accept<<<gV, kTpb, 0, stm>>>(q, h->q_flag, h->q_cursor);
+                    launch_scan(h->q_cursor, h->q_pos, nullptr, V, stm, h->d_scan_tmp);
+                    k_q_forest_write<<<gV, kTpb, 0, stm>>>(q, h->q_cursor, h->q_pos, h->q_forest);
+                    k_q_forest_advance<<<1, 1, 0, stm>>>(q, h->q_pos);
+                    h->launches += J + 7;
+                }
+                enqueue_relabel(h, q, stm);
+                h->launches += 3;
+            }
+            k_q_next<<<1, 1, 0, stm>>>(q, 0, 0);
+            h->launches += 2;  // sample, next
+            if (n_ed == 0) break;
+        }
+        if (e == cudaSuccess) {
+            k_q_ncc<<<grid_for(h, V, kTpb), kTpb, 0, stm>>>(q);
+            h->launches += 1;
+            e = cudaMemcpyAsync(h->h_ctr, h->q_ctr, C_N * sizeof(uint32_t), cudaMemcpyDeviceToHost, stm);
+        }
+    }
     if (e == cudaSuccess && labels)
         e = cudaMemcpyAsync(labels, h->q_label, (size_t)V * sizeof(uint32_t), cudaMemcpyDeviceToHost, stm);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stm);
-    if (e != cudaSuccess) return cuda_check(h, e, "query results");
+    if (e != cudaSuccess) return cuda_check(h, e, "query");
     const uint32_t ncc = h->h_ctr[C_NCC];
     const uint32_t nf = h->h_ctr[C_FOREST];
+    const uint32_t rounds = h->h_ctr[C_ROUNDS], fails_last = h->h_ctr[C_FLAST];
+    const uint32_t fails_total = h->h_ctr[C_FTOT], exhausted = h->h_ctr[C_EXH];
+    if (!want_forest && !h->trace)
+        h->launches += kLaunchesStartEnd + kLaunchesRound0 + (uint64_t)(rounds ? rounds - 1 : 0) * kLaunchesRound;
     if (want_forest) {
         if (forest_uv && nf) {
             e = cudaMemcpy(forest_uv, h->q_forest, (size_t)nf * 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost);

@@ -49,6 +49,13 @@ def _assert_same_query(g, A, G, seed):
     assert np.array_equal(forest, want["forest"])
     labels2, ncc, st2 = g.connected_components()
     assert np.array_equal(labels2, want["labels"]) and ncc == want["n_components"]
+    # untraced CC queries run as one CUDA graph (device-side round loop)
+    g.enable_trace(False)
+    for _ in range(2):
+        labels3, ncc3, st3 = g.connected_components()
+        assert np.array_equal(labels3, want["labels"]) and ncc3 == want["n_components"]
+        assert st3["rounds"] == want["rounds"] and st3["fails_last"] == want["fails_last"]
+        assert st3["fails_total"] == st2["fails_total"] and st3["exhausted"] == st2["exhausted"]
     return want
 
 
