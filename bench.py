@@ -332,6 +332,8 @@ def run_ours(args, rank: int, world: int):
         cfg.update(json.loads(args.cfg))
     if args.kernel == "plain":
         cfg = {"chunk_log2": CHUNK_LOG2}
+    if args.device_sketch_mb:
+        cfg["device_sketch_mb"] = args.device_sketch_mb
     g = gz.Graph(spec.V, seed=seed, kernel=args.kernel, **cfg)
     qtimes = []
 
@@ -545,6 +547,10 @@ def run_ours(args, rank: int, world: int):
                 "l2": "no flush needed: stream (%.1f GB) and sketches (%.1f GB) exceed the 126 MB L2"
                       % (8 * total / 1e9, spec.V * K * 84 * R / 1e9),
                 "step": "reset sketches + ingest whole stream + one CC query",
+                "sketches_beyond_hbm": None if not args.device_sketch_mb else
+                f"{args.device_sketch_mb} MiB of sketches in HBM, the rest "
+                f"({spec.V * K * 84 * R / 1e9 - args.device_sketch_mb * 2 ** 20 / 1e9:.1f} GB or more) in pinned host "
+                "memory, streamed through two device shard slots per chunk",
             },
             "roofline": roofline,
             "query_ms": query,
@@ -918,6 +924,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--cfg", default="", help="JSON gz_config overrides, e.g. '{\"smem_mode\": 1}'")
+    ap.add_argument("--device-sketch-mb", type=int, default=0,
+                    help="HBM budget for node sketches (MiB); the rest live in pinned host memory")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

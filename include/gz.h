@@ -67,8 +67,24 @@ typedef struct {
                                atomics, 2 load-xor-store */
     uint32_t no_graph;      /* 1: launch a chunk's kernels one by one instead of replaying the
                                CUDA graph captured for the handle after its 8th chunk (default 0) */
-    uint32_t reserved[4];
+    uint32_t device_sketch_mb; /* HBM for node sketches, MiB (0: all of them in HBM).  When the
+                               sketches need more, nodes beyond the budget live in pinned host
+                               memory (sketches beyond HBM, below) */
+    uint32_t reserved[3];
 } gz_config;
+
+/* Sketches beyond HBM (the paper's hybrid streaming model of Section 4, with
+ * host memory as the slow tier): with cfg.device_sketch_mb set below the
+ * sketches' size, the nodes are cut into shards of a quarter of the budget
+ * (at most 512 MiB, at least one node);
+ * the first shards that fit the budget stay in HBM and the others live in
+ * pinned host memory.  Each chunk of updates is partitioned once; the batched
+ * update then runs on the resident shards in place and on each host shard
+ * after copying it into one of two device slots, the copy-in of the next shard
+ * and the copy-out of the previous one overlapping the update of the current
+ * one (so large chunks amortise the transfers, as large buffers amortise disk
+ * I/O in the paper).  Queries copy CubeSketch r of every node into one device
+ * array per Boruvka round.  Results are identical to an all-HBM handle. */
 
 /* Statistics of the last query. */
 typedef struct {
@@ -201,8 +217,9 @@ gz_status gz_restore(const void *buf, size_t size, const gz_config *cfg, void *s
  * paper's nested row i is the XOR of rows i..R-1), layout per node: for each
  * k, alpha[row][j] (u64) then gamma'[row][j] (u32), where gamma' keeps the
  * checksum sums before MurmurHash3's final step g ^= g >> 16 (a linear map, so
- * a bucket's checksum sum is gamma' ^ (gamma' >> 16)).  Any output pointer may
- * be NULL. */
+ * a bucket's checksum sum is gamma' ^ (gamma' >> 16)).  For a handle with
+ * sketches beyond HBM the array holds the resident nodes only (a prefix of the
+ * node range; NULL when none is resident).  Any output pointer may be NULL. */
 gz_status gz_info(gz_handle *h, uint32_t *V, uint32_t *K, uint32_t *R,
                   size_t *node_bytes, void **sketch_device);
 

@@ -44,7 +44,8 @@ class Config(ctypes.Structure):
         ("small_segment", ctypes.c_uint32),
         ("smem_mode", ctypes.c_uint32),
         ("no_graph", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 4),
+        ("device_sketch_mb", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 3),
     ]
 
 
@@ -180,7 +181,8 @@ def geometry(V: int) -> tuple[int, int]:
 
 
 def _config(kernel: str = "batched", chunk_log2: int = 0, smem_rows: int = 0, tile_records: int = 0,
-            ctas_per_sm: int = 0, small_segment: int = 0, smem_mode: int = 0, no_graph: int = 0) -> Config:
+            ctas_per_sm: int = 0, small_segment: int = 0, smem_mode: int = 0, no_graph: int = 0,
+            device_sketch_mb: int = 0) -> Config:
     cfg = Config()
     cfg.chunk_log2 = chunk_log2
     cfg.kernel = KERNELS[kernel]
@@ -190,6 +192,7 @@ def _config(kernel: str = "batched", chunk_log2: int = 0, smem_rows: int = 0, ti
     cfg.small_segment = small_segment
     cfg.smem_mode = smem_mode
     cfg.no_graph = no_graph
+    cfg.device_sketch_mb = device_sketch_mb
     return cfg
 
 
@@ -274,10 +277,11 @@ class Graph:
 
     def __init__(self, V: int, seed: int = 0, *, kernel: str = "batched", chunk_log2: int = 0,
                  smem_rows: int = 0, tile_records: int = 0, ctas_per_sm: int = 0,
-                 small_segment: int = 0, smem_mode: int = 0, no_graph: int = 0, stream=None):
+                 small_segment: int = 0, smem_mode: int = 0, no_graph: int = 0, device_sketch_mb: int = 0,
+                 stream=None):
         cfg = _config(kernel=kernel, chunk_log2=chunk_log2, smem_rows=smem_rows, tile_records=tile_records,
                       ctas_per_sm=ctas_per_sm, small_segment=small_segment, smem_mode=smem_mode,
-                      no_graph=no_graph)
+                      no_graph=no_graph, device_sketch_mb=device_sketch_mb)
         self._h = ctypes.c_void_p()
         s = _current_stream() if stream is None else stream
         st = lib().gz_create(V, seed & ((1 << 64) - 1), ctypes.byref(cfg), ctypes.c_void_p(s),

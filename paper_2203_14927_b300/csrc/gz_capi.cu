@@ -53,6 +53,20 @@ static bool geometry(uint32_t V, uint32_t* K, uint32_t* R) {
     return true;
 }
 
+void tier_geometry(uint32_t V, uint64_t node_bytes, uint32_t budget_mb, uint32_t* shard_nodes,
+                   uint32_t* res_nodes) {
+    const uint64_t budget = (uint64_t)budget_mb << 20;
+    // shards of a quarter of the budget, at most 512 MiB and at least one node
+    const uint64_t target = std::min<uint64_t>(512ull << 20, budget / 4);
+    const uint64_t sn = std::max<uint64_t>(1, std::min<uint64_t>(V, target / node_bytes));
+    *shard_nodes = (uint32_t)sn;
+    if (budget_mb == 0 || (uint64_t)V * node_bytes <= budget) {
+        *res_nodes = V;
+        return;
+    }
+    *res_nodes = (uint32_t)std::min<uint64_t>(V, budget / node_bytes / sn * sn);
+}
+
 static size_t scratch_bytes(uint32_t V, uint64_t chunk) {
     return (size_t)3 * (V + 1) * 4 + (size_t)2 * chunk * 4 + 64;
 }
@@ -86,7 +100,13 @@ gz_status gz_memory_bytes(uint32_t V, const gz_config* cfg, size_t* bytes) {
     if (!gz::geometry(V, &K, &R) || !bytes) return GZ_EINVAL;
     const uint32_t cl = cfg && cfg->chunk_log2 ? cfg->chunk_log2 : 24;
     const uint64_t chunk = 1ull << cl;
-    *bytes = (size_t)V * K * 84ull * R + (size_t)K * 7 * 24 + scratch_bytes(V, chunk);
+    const uint64_t node_bytes = (uint64_t)K * 84ull * R;
+    uint32_t shard_nodes = 0, res_nodes = 0;
+    tier_geometry(V, node_bytes, cfg ? cfg->device_sketch_mb : 0, &shard_nodes, &res_nodes);
+    size_t tier = 0;
+    if (res_nodes < V)  // two shard slots and the per-round query gather array
+        tier = 2 * (size_t)shard_nodes * node_bytes + (size_t)V * 84ull * R;
+    *bytes = (size_t)res_nodes * node_bytes + tier + (size_t)K * 7 * 24 + scratch_bytes(V, chunk);
     return GZ_OK;
 }
 
@@ -134,10 +154,34 @@ gz_status gz_create(uint32_t V, uint64_t seed, const gz_config* cfg, void* strea
     // Stream-ordered allocations: creating or destroying a handle never
     // synchronises the whole device (cudaFree would), so a server can admit
     // and release graphs while other graphs' work runs.
-    const size_t sk = (size_t)V * h->node_bytes;
+    tier_geometry(V, h->node_bytes, h->cfg.device_sketch_mb, &h->shard_nodes, &h->res_nodes);
+    h->tiered = h->res_nodes < V;
+    if (h->tiered && h->cfg.kernel != GZ_KERNEL_BATCHED) {
+        set_error(h, GZ_EINVAL, "sketches beyond HBM need the batched kernel");
+        g_create_err = h->err;
+        delete[] hk;
+        delete h;
+        return GZ_EINVAL;
+    }
+    const size_t sk = (size_t)h->res_nodes * h->node_bytes;
     cudaStream_t as = h->stream;
-    e = cudaMallocAsync(&h->d_sketch, sk, as);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_sketch, 0, sk, h->stream);
+    e = sk ? cudaMallocAsync(&h->d_sketch, sk, as) : cudaSuccess;
+    if (e == cudaSuccess && sk) e = cudaMemsetAsync(h->d_sketch, 0, sk, h->stream);
+    if (h->tiered) {
+        const size_t hb = (size_t)(V - h->res_nodes) * h->node_bytes;
+        const size_t slot = (size_t)h->shard_nodes * h->node_bytes;
+        if (e == cudaSuccess) e = cudaMallocHost(&h->h_sketch, hb);
+        if (e == cudaSuccess) std::memset(h->h_sketch, 0, hb);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaMallocAsync(&h->d_slot[b], slot, as);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_tin[b], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_tdone[b], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_tout[b], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaMallocAsync(&h->d_gather, (size_t)V * h->per_k_bytes, as);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->tier_in, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->tier_out, cudaStreamNonBlocking);
+    }
     if (e == cudaSuccess) e = cudaMallocAsync(&h->d_keys, 3 * ncol * sizeof(uint64_t), as);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->d_keys, hk, 3 * ncol * sizeof(uint64_t), cudaMemcpyHostToDevice, as);
@@ -169,13 +213,16 @@ gz_status gz_create(uint32_t V, uint64_t seed, const gz_config* cfg, void* strea
 
 gz_status gz_destroy(gz_handle* h) {
     if (!h) return GZ_EINVAL;
+    if (h->tier_in) cudaStreamSynchronize(h->tier_in);
+    if (h->tier_out) cudaStreamSynchronize(h->tier_out);
     cudaStreamSynchronize(h->stream);
     void* ptrs[] = {h->d_sketch, h->d_keys, h->d_counts, h->d_offsets, h->d_cursor, h->d_records,
                     h->d_stage, h->d_flags, h->q_label, h->q_parent, h->q_count, h->q_off,
                     h->q_cursor, h->q_members, h->q_roots, h->q_target, h->q_slot,
                     h->q_F, h->q_F2,
                     h->q_M, h->q_M2, h->q_flag, h->q_pos, h->q_forest, h->q_ctr, h->q_res,
-                    h->q_acc, h->q_trace, h->d_stats, h->d_scan_tmp, h->d_tile_node, h->d_decode};
+                    h->q_acc, h->q_trace, h->d_stats, h->d_scan_tmp, h->d_tile_node, h->d_decode,
+                    h->d_slot[0], h->d_slot[1], h->d_gather};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, h->stream);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);
@@ -187,6 +234,15 @@ gz_status gz_destroy(gz_handle* h) {
         if (h->ev_free[b]) cudaEventDestroy(h->ev_free[b]);
     }
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    for (int b = 0; b < 2; ++b) {
+        if (h->ev_tin[b]) cudaEventDestroy(h->ev_tin[b]);
+        if (h->ev_tdone[b]) cudaEventDestroy(h->ev_tdone[b]);
+        if (h->ev_tout[b]) cudaEventDestroy(h->ev_tout[b]);
+    }
+    if (h->tier_in) cudaStreamDestroy(h->tier_in);
+    if (h->tier_out) cudaStreamDestroy(h->tier_out);
+    cudaStreamSynchronize(h->stream);
+    if (h->h_sketch) cudaFreeHost(h->h_sketch);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->graph) cudaGraphDestroy(h->graph);
     for (int i = 0; i < 3; ++i)
@@ -317,7 +373,13 @@ gz_status gz_sync(gz_handle* h) {
 
 gz_status gz_reset(gz_handle* h) {
     if (!h) return GZ_EINVAL;
-    cudaError_t e = cudaMemsetAsync(h->d_sketch, 0, (size_t)h->V * h->node_bytes, h->stream);
+    cudaError_t e = cudaSuccess;
+    if (h->res_nodes) e = cudaMemsetAsync(h->d_sketch, 0, (size_t)h->res_nodes * h->node_bytes, h->stream);
+    if (h->tiered) {  // host shards: wait for every queued update and copy-out, then clear
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->tier_out);
+        if (e == cudaSuccess) std::memset(h->h_sketch, 0, (size_t)(h->V - h->res_nodes) * h->node_bytes);
+    }
     return cuda_check(h, e, "reset");
 }
 
@@ -452,9 +514,14 @@ gz_status gz_checkpoint(gz_handle* h, void* buf, size_t size) {
     hd.seed = h->seed;
     hd.node_bytes = h->node_bytes;
     std::memcpy(buf, &hd, sizeof(hd));
-    cudaError_t e = cudaMemcpyAsync(static_cast<uint8_t*>(buf) + sizeof(hd), h->d_sketch, need - sizeof(hd),
-                                    cudaMemcpyDeviceToHost, h->stream);
+    uint8_t* dst = static_cast<uint8_t*>(buf) + sizeof(hd);
+    const size_t res = (size_t)h->res_nodes * h->node_bytes;
+    cudaError_t e = res ? cudaMemcpyAsync(dst, h->d_sketch, res, cudaMemcpyDeviceToHost, h->stream) : cudaSuccess;
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (h->tiered && e == cudaSuccess) {
+        e = cudaStreamSynchronize(h->tier_out);
+        if (e == cudaSuccess) std::memcpy(dst + res, h->h_sketch, need - sizeof(hd) - res);
+    }
     return cuda_check(h, e, "checkpoint copy");
 }
 
@@ -471,9 +538,11 @@ gz_status gz_restore(const void* buf, size_t size, const gz_config* cfg, void* s
     gz_handle* h = nullptr;
     gz_status s = gz_create(hd.V, hd.seed, cfg, stream, &h);
     if (s != GZ_OK) return s;
-    cudaError_t e = cudaMemcpyAsync(h->d_sketch, static_cast<const uint8_t*>(buf) + sizeof(hd),
-                                    (size_t)hd.V * hd.node_bytes, cudaMemcpyHostToDevice, h->stream);
+    const uint8_t* src = static_cast<const uint8_t*>(buf) + sizeof(hd);
+    const size_t res = (size_t)h->res_nodes * hd.node_bytes;
+    cudaError_t e = res ? cudaMemcpyAsync(h->d_sketch, src, res, cudaMemcpyHostToDevice, h->stream) : cudaSuccess;
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (h->tiered && e == cudaSuccess) std::memcpy(h->h_sketch, src + res, (size_t)hd.V * hd.node_bytes - res);
     if (e != cudaSuccess) {
         gz_destroy(h);
         return GZ_ECUDA;

@@ -45,6 +45,17 @@ struct gz_handle {
     uint64_t batches_done = 0;     // partition passes issued (graph capture after 8)
     size_t batched_smem = 0;
 
+    // sketches beyond HBM: nodes [0, res_nodes) in d_sketch, the others in
+    // pinned host memory h_sketch, streamed shard by shard through two slots
+    bool tiered = false;
+    uint32_t shard_nodes = 0, res_nodes = 0;
+    uint8_t* h_sketch = nullptr;
+    uint8_t* d_slot[2] = {nullptr, nullptr};
+    cudaStream_t tier_in = nullptr, tier_out = nullptr;
+    cudaEvent_t ev_tin[2] = {nullptr, nullptr}, ev_tdone[2] = {nullptr, nullptr},
+                ev_tout[2] = {nullptr, nullptr};
+    uint8_t* d_gather = nullptr;   // query: CubeSketch r of every node, V * per_k_bytes
+
     // query scratch (allocated on first query)
     bool query_ready = false;
     uint32_t *q_label = nullptr, *q_parent = nullptr, *q_count = nullptr, *q_off = nullptr,
@@ -91,6 +102,15 @@ gz_status ingest_batch(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, u
 gz_status decode_idx(gz_handle* h, const uint64_t* d_idx, uint64_t n, uint32_t* d_u, uint32_t* d_v);
 gz_status export_nested(gz_handle* h, uint32_t lo, uint32_t hi, uint64_t* d_alpha,
                         uint32_t* d_gamma);
+
+// sketches beyond HBM: shard size and resident nodes for a device budget of
+// budget_mb MiB (0 = everything resident: *res_nodes = V)
+void tier_geometry(uint32_t V, uint64_t node_bytes, uint32_t budget_mb, uint32_t* shard_nodes,
+                   uint32_t* res_nodes);
+// make the handle stream wait for the last copy-outs of host shards
+gz_status tier_settle(gz_handle* h);
+// copy the full sketches of nodes [lo, hi) into dst (device, (hi-lo)*node_bytes) on the handle stream
+gz_status tier_gather_nodes(gz_handle* h, uint32_t lo, uint32_t hi, uint8_t* dst);
 
 // query (gz_query.cu)
 // Components with more than kMergeChunk members are merged by chunks of

@@ -168,6 +168,9 @@ struct BatchedArgs {
     uint32_t* work;  // tile counter
     unsigned long long* stats;  // [0] rows flushed, [1] deep column updates
     uint32_t V, K, R, ncol, Rs, tile, small_seg;
+    // node window: only records of nodes [node_lo, node_hi) are applied, and
+    // node x's sketch is at s.base + (x - node_lo) * s.node_bytes
+    uint32_t node_lo, node_hi;
 };
 
 // tile_node[t] = the node x with offsets[x] <= t*tile < offsets[x+1]: node x
@@ -280,7 +283,10 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
     if (active) key = make_colkey(p.keys.a[c], p.keys.b[c], p.keys.c[c]);
     for (uint32_t i = c; i < 3 * RC; i += CP) sw[i] = 0;
     const uint32_t total = p.offsets[p.V];
-    const uint32_t ntiles = (total + T - 1) / T;
+    // the window's records [rec_lo, rec_hi) lie in tiles t_lo .. t_lo+ntiles-1
+    const uint32_t rec_lo = p.offsets[p.node_lo], rec_hi = p.offsets[p.node_hi];
+    const uint32_t t_lo = rec_lo / T;
+    const uint32_t ntiles = rec_hi > rec_lo ? (rec_hi + T - 1) / T - t_lo : 0u;
     unsigned long long n_rows = 0, n_deep = 0;
 
     // records of tile t -> raw[buf]: 16-byte granules, the tail zero-filled
@@ -307,8 +313,8 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
     __syncthreads();
     uint32_t x_next = 0;
     if (s_t[0] < ntiles) {
-        fetch(s_t[0], 0);
-        x_next = p.tile_node[s_t[0]];
+        fetch(t_lo + s_t[0], 0);
+        x_next = max(p.tile_node[t_lo + s_t[0]], p.node_lo);
     }
     uint32_t sbuf = 0;
     for (uint32_t it = 0;; ++it) {
@@ -319,8 +325,8 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
         uint32_t claimed = 0;
         if (c == 0) claimed = atomicAdd(p.work, 1u);
         if (tn < ntiles) {
-            fetch(tn, (it + 1) % 3);  // that buffer was last read in iteration it-2
-            x_next = p.tile_node[tn];
+            fetch(t_lo + tn, (it + 1) % 3);  // that buffer was last read in iteration it-2
+            x_next = max(p.tile_node[t_lo + tn], p.node_lo);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
@@ -328,11 +334,13 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
         if (c == 0) s_t[(it + 2) % 3] = claimed;
         __syncthreads();  // raw[it%3] complete and visible; s_t up to date
         const uint32_t* rb = raw + (it % 3) * T;
-        const uint32_t lo = t * T, hi = min(lo + T, total);
-        uint32_t x = x_first, pos = lo;
+        const uint32_t tile_lo = (t_lo + t) * T;  // raw[] holds records from tile_lo on
+        const uint32_t hi = min(tile_lo + T, rec_hi);
+        uint32_t x = x_first, pos = max(tile_lo, rec_lo);
         while (pos < hi) {
             const uint32_t seg_end = min(p.offsets[x + 1], hi);
             const uint32_t nseg = seg_end - pos;
+            const uint32_t xs = x - p.node_lo;  // node's place in the sketch window
             if (nseg > 0) {
                 // this stage buffer was last read two segments ago, before the
                 // previous segment's barrier
@@ -341,7 +349,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                 uint2* stage2 = reinterpret_cast<uint2*>(stage);
                 sbuf ^= 1u;
                 for (uint32_t i = c; i < nseg; i += CP) {
-                    const uint64_t idx = edge_index(x, rb[pos - lo + i], p.V);
+                    const uint64_t idx = edge_index(x, rb[pos - tile_lo + i], p.V);
                     if (kWide) {
                         stage4[i] = make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), fold_pre(idx), 0u);
                     } else {
@@ -366,9 +374,9 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                                 fp = q.y;
                             }
                             const uint32_t d = exact_depth(depth_word(ka, kb, idx), R);
-                            atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, d, j)),
+                            atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(xs, k, d, j)),
                                       (unsigned long long)idx);
-                            atomicXor(p.s.gamma(x, k, d, j), checksum_w(key, fp));
+                            atomicXor(p.s.gamma(xs, k, d, j), checksum_w(key, fp));
                         }
                     }
                 } else if (active) {
@@ -390,9 +398,9 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                         ++n_deep;
                         const uint64_t idx = ((uint64_t)xhi << 32) | xlo;
                         const uint32_t dd = exact_depth(depth_word(p.keys.a[c], p.keys.b[c], idx), R);
-                        atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, dd, j)),
+                        atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(xs, k, dd, j)),
                                   (unsigned long long)idx);
-                        atomicXor(p.s.gamma(x, k, dd, j), g);
+                        atomicXor(p.s.gamma(xs, k, dd, j), g);
                     };
                     uint32_t i = 0;
                     // four records at a time in straight-line code, so the
@@ -472,9 +480,9 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                         const uint64_t a = kMode == 1 ? (((uint64_t)w[32] << 32) | w[0]) : ca[row * 48];
                         const uint32_t g = w[64];
                         if (a | g) {
-                            atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, row, j)),
+                            atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(xs, k, row, j)),
                                       (unsigned long long)a);
-                            atomicXor(p.s.gamma(x, k, row, j), g);
+                            atomicXor(p.s.gamma(xs, k, row, j), g);
                             if (kMode == 1) {
                                 w[0] = 0;
                                 w[32] = 0;
@@ -640,7 +648,69 @@ static BatchedArgs batched_args(gz_handle* h) {
     a.tile = h->tile;
     a.small_seg = h->small_seg;
     a.stats = reinterpret_cast<unsigned long long*>(h->d_stats);
+    a.node_lo = 0;
+    a.node_hi = h->V;
     return a;
+}
+
+// Sketches beyond HBM: the batched update of one partitioned chunk, window by
+// window.  Resident nodes are updated in place; each host shard is copied into
+// device slot (i & 1) on tier_in, updated on st, and copied back on tier_out.
+// A slot's copy-in waits for its previous copy-out, and tier_out runs its
+// copies in issue order, so a shard's copy-in also follows its copy-out of the
+// previous chunk.  The tile counter is cleared before every launch.
+static void enqueue_tiered_updates(gz_handle* h, cudaStream_t st) {
+    const bool wide = (uint64_t)h->V * h->V > (1ull << 32);
+    const BatchedFn fn = batched_fn(h->delta_mode, wide);
+    BatchedArgs a = batched_args(h);
+    if (h->res_nodes) {
+        a.node_lo = 0;
+        a.node_hi = h->res_nodes;
+        fn<<<h->batched_grid, h->block, h->batched_smem, st>>>(a);
+    }
+    uint32_t i = 0;
+    for (uint32_t lo = h->res_nodes; lo < h->V; lo += h->shard_nodes, ++i) {
+        const uint32_t hi = std::min<uint32_t>(h->V, lo + h->shard_nodes), b = i & 1u;
+        const size_t bytes = (size_t)(hi - lo) * h->node_bytes;
+        uint8_t* host = h->h_sketch + (size_t)(lo - h->res_nodes) * h->node_bytes;
+        cudaStreamWaitEvent(h->tier_in, h->ev_tout[b], 0);  // an event never recorded is complete
+        cudaMemcpyAsync(h->d_slot[b], host, bytes, cudaMemcpyHostToDevice, h->tier_in);
+        cudaEventRecord(h->ev_tin[b], h->tier_in);
+        cudaStreamWaitEvent(st, h->ev_tin[b], 0);
+        cudaMemsetAsync(h->d_flags + 1, 0, sizeof(uint32_t), st);  // tile counter
+        a.s.base = h->d_slot[b];
+        a.node_lo = lo;
+        a.node_hi = hi;
+        fn<<<h->batched_grid, h->block, h->batched_smem, st>>>(a);
+        cudaEventRecord(h->ev_tdone[b], st);
+        cudaStreamWaitEvent(h->tier_out, h->ev_tdone[b], 0);
+        cudaMemcpyAsync(host, h->d_slot[b], bytes, cudaMemcpyDeviceToHost, h->tier_out);
+        cudaEventRecord(h->ev_tout[b], h->tier_out);
+    }
+    h->launches += i + (h->res_nodes ? 1 : 0) - 1;  // beyond the one batched launch counted per chunk
+}
+
+gz_status tier_settle(gz_handle* h) {
+    if (!h->tiered) return GZ_OK;
+    cudaError_t e = cudaStreamWaitEvent(h->stream, h->ev_tout[0], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_tout[1], 0);
+    return cuda_check(h, e, "tier settle");
+}
+
+gz_status tier_gather_nodes(gz_handle* h, uint32_t lo, uint32_t hi, uint8_t* dst) {
+    gz_status s = tier_settle(h);
+    if (s != GZ_OK) return s;
+    cudaError_t e = cudaSuccess;
+    const uint32_t r_hi = std::min(hi, h->res_nodes);
+    if (lo < r_hi)
+        e = cudaMemcpyAsync(dst, h->d_sketch + (size_t)lo * h->node_bytes, (size_t)(r_hi - lo) * h->node_bytes,
+                            cudaMemcpyDeviceToDevice, h->stream);
+    const uint32_t h_lo = std::max(lo, h->res_nodes);
+    if (e == cudaSuccess && h_lo < hi)
+        e = cudaMemcpyAsync(dst + (size_t)(h_lo - lo) * h->node_bytes,
+                            h->h_sketch + (size_t)(h_lo - h->res_nodes) * h->node_bytes,
+                            (size_t)(hi - h_lo) * h->node_bytes, cudaMemcpyHostToDevice, h->stream);
+    return cuda_check(h, e, "tier gather");
 }
 
 // The batched pipeline of one chunk on stream st: validation + histogram,
@@ -663,7 +733,11 @@ static void enqueue_batched(gz_handle* h, const uint32_t* d_u, const uint32_t* d
     k_tile_nodes<<<(h->V + 255) / 256, 256, 0, st>>>(h->d_offsets, h->V, h->tile, h->d_flags, h->d_tile_node);
     if (ev1) record(ev1);
     const bool wide = (uint64_t)h->V * h->V > (1ull << 32);
-    batched_fn(h->delta_mode, wide)<<<h->batched_grid, h->block, h->batched_smem, st>>>(batched_args(h));
+    if (!h->tiered) {
+        batched_fn(h->delta_mode, wide)<<<h->batched_grid, h->block, h->batched_smem, st>>>(batched_args(h));
+    } else {
+        enqueue_tiered_updates(h, st);
+    }
     if (ev2) record(ev2);
 }
 
@@ -797,7 +871,7 @@ gz_status ingest_batch(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, u
                                          h->d_flags);
         h->launches += 2;
         if ((ps = prof_event(h)) != GZ_OK) return ps;
-    } else if (!h->cfg.no_graph && h->batches_done >= 8) {
+    } else if (!h->cfg.no_graph && !h->tiered && h->batches_done >= 8) {
         // the captured graph pays off once a handle keeps ingesting
         if ((ps = launch_graph(h, d_u, d_v, n)) != GZ_OK) return ps;
         h->launches += 6;  // validate, 2 scan, scatter, tile table, batched
@@ -834,8 +908,23 @@ gz_status export_nested(gz_handle* h, uint32_t lo, uint32_t hi, uint64_t* d_alph
     const uint64_t threads = (uint64_t)(hi - lo) * h->ncol;
     if (threads == 0) return GZ_OK;
     const uint32_t tpb = 256;
-    k_export<<<(uint32_t)((threads + tpb - 1) / tpb), tpb, 0, h->stream>>>(view_of(h), lo, hi, h->K,
+    SketchView v = view_of(h);
+    uint8_t* tmp = nullptr;
+    if (h->tiered) {  // gather the nodes' full sketches into one device array first
+        cudaError_t e = cudaMallocAsync(&tmp, (size_t)(hi - lo) * h->node_bytes, h->stream);
+        if (e != cudaSuccess) return cuda_check(h, e, "export gather buffer");
+        gz_status s = tier_gather_nodes(h, lo, hi, tmp);
+        if (s != GZ_OK) {
+            cudaFreeAsync(tmp, h->stream);
+            return s;
+        }
+        v.base = tmp;
+        hi -= lo;
+        lo = 0;
+    }
+    k_export<<<(uint32_t)((threads + tpb - 1) / tpb), tpb, 0, h->stream>>>(v, lo, hi, h->K,
                                                                           h->R, d_alpha, d_gamma);
+    if (tmp) cudaFreeAsync(tmp, h->stream);
     return cuda_check(h, cudaGetLastError(), "export launch");
 }
 
@@ -993,6 +1082,8 @@ extern "C" gz_status gz_sketch_update_noalloc(void* sketch, uint32_t V, uint64_t
         a.Rs = Rs;
         a.tile = tile;
         a.small_seg = 4;
+        a.node_lo = 0;
+        a.node_hi = V;
         const size_t smem = (size_t)Rs * block * 12 + (size_t)tile * (12 + (wide ? 32 : 16));
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_fn(1, wide), (int)block, smem) !=

@@ -455,6 +455,11 @@ static QArgs query_args(gz_handle* h) {
     q.s.node_bytes = h->node_bytes;
     q.s.per_k_bytes = h->per_k_bytes;
     q.s.gamma_off = 56u * h->R;
+    if (h->tiered) {  // each round reads the gathered array: CubeSketch r of node x at x * per_k_bytes
+        q.s.base = h->d_gather;
+        q.s.node_bytes = h->per_k_bytes;
+        q.s.per_k_bytes = 0;
+    }
     q.kc = h->d_keys + 2 * (size_t)h->ncol;
     q.V = h->V;
     q.K = h->K;
@@ -603,17 +608,29 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
     const uint32_t V = h->V;
     cudaError_t e = cudaSuccess;
 
-    if (!want_forest && !h->trace) {
+    if (!want_forest && !h->trace && !h->tiered) {
         if (!h->q_graph_exec && (s = build_query_graph(h)) != GZ_OK) return s;
         e = cudaGraphLaunch(h->q_graph_exec, stm);
     } else {
-        // forest or trace: the same rounds driven from the host, which reads
-        // the round's counters after the sampler (the forest kernels are sized
-        // by the number of components)
+        // forest, trace or sketches beyond HBM: the same rounds driven from
+        // the host, which reads the round's counters after the sampler (the
+        // forest kernels are sized by the number of components) and, for a
+        // tiered handle, first gathers CubeSketch r of every node
+        if ((s = tier_settle(h)) != GZ_OK) return s;
         enqueue_start(h, q, stm);
         if (q.trace) k_fill64<<<grid_for(h, (uint64_t)h->K * V, kTpb), kTpb, 0, stm>>>(q.trace, (uint64_t)h->K * V, -4);
         h->launches += 1 + (q.trace ? 1 : 0);
         for (uint32_t r = 0; r < h->K && e == cudaSuccess; ++r) {
+            if (h->tiered) {
+                const size_t pk = h->per_k_bytes;
+                if (h->res_nodes)
+                    e = cudaMemcpy2DAsync(h->d_gather, pk, h->d_sketch + (size_t)r * pk, h->node_bytes, pk,
+                                          h->res_nodes, cudaMemcpyDeviceToDevice, stm);
+                if (e == cudaSuccess)
+                    e = cudaMemcpy2DAsync(h->d_gather + (size_t)h->res_nodes * pk, pk, h->h_sketch + (size_t)r * pk,
+                                          h->node_bytes, pk, V - h->res_nodes, cudaMemcpyHostToDevice, stm);
+                if (e != cudaSuccess) break;
+            }
             if (r > 0) {
                 enqueue_grouping(h, q, stm);
                 h->launches += 6;
