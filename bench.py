@@ -45,7 +45,7 @@ CHUNK_LOG2 = 24
 # dram__bytes_read.sum + dram__bytes_write.sum) of this bench's own step; valid
 # only for the kernel source it was taken with (kernel_sha) and its configuration.
 TRAFFIC = {
-    "kron17": {"sha": "12b49f74df1987c5",
+    "kron17": {"sha": "a2e9e708759668e0",
                "cfg": {"smem_mode": 1, "tile_records": 512, "smem_rows": 12, "ctas_per_sm": 0, "chunk_log2": 26},
                "bytes_per_launch": 10.272e9, "updates_per_launch": 66592033,
                "source": "profiles/k_batched_kron17_dram.md"},
@@ -550,7 +550,7 @@ def run_ours(args, rank: int, world: int):
                 "sketches_beyond_hbm": None if not args.device_sketch_mb else
                 f"{args.device_sketch_mb} MiB of sketches in HBM, the rest "
                 f"({spec.V * K * 84 * R / 1e9 - args.device_sketch_mb * 2 ** 20 / 1e9:.1f} GB or more) in pinned host "
-                "memory, streamed through two device shard slots per chunk",
+                "memory, streamed through three device shard slots per chunk",
             },
             "roofline": roofline,
             "query_ms": query,

@@ -80,9 +80,9 @@ typedef struct {
  * the first shards that fit the budget stay in HBM and the others live in
  * pinned host memory.  Each chunk of updates is partitioned once; the batched
  * update then runs on the resident shards in place and on each host shard
- * after copying it into one of two device slots, the copy-in of the next shard
- * and the copy-out of the previous one overlapping the update of the current
- * one (so large chunks amortise the transfers, as large buffers amortise disk
+ * after copying it into one of three device slots, the copy-in of the next
+ * shard and the copy-out of the previous one overlapping the update of the
+ * current one (so large chunks amortise the transfers, as large buffers amortise disk
  * I/O in the paper).  Queries copy CubeSketch r of every node into one device
  * array per Boruvka round.  Results are identical to an all-HBM handle. */
 

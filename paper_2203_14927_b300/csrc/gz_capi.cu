@@ -104,8 +104,8 @@ gz_status gz_memory_bytes(uint32_t V, const gz_config* cfg, size_t* bytes) {
     uint32_t shard_nodes = 0, res_nodes = 0;
     tier_geometry(V, node_bytes, cfg ? cfg->device_sketch_mb : 0, &shard_nodes, &res_nodes);
     size_t tier = 0;
-    if (res_nodes < V)  // two shard slots and the per-round query gather array
-        tier = 2 * (size_t)shard_nodes * node_bytes + (size_t)V * 84ull * R;
+    if (res_nodes < V)  // the shard slots and the per-round query gather array
+        tier = gz_handle::kTierSlots * (size_t)shard_nodes * node_bytes + (size_t)V * 84ull * R;
     *bytes = (size_t)res_nodes * node_bytes + tier + (size_t)K * 7 * 24 + scratch_bytes(V, chunk);
     return GZ_OK;
 }
@@ -172,7 +172,7 @@ gz_status gz_create(uint32_t V, uint64_t seed, const gz_config* cfg, void* strea
         const size_t slot = (size_t)h->shard_nodes * h->node_bytes;
         if (e == cudaSuccess) e = cudaMallocHost(&h->h_sketch, hb);
         if (e == cudaSuccess) std::memset(h->h_sketch, 0, hb);
-        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        for (int b = 0; b < gz_handle::kTierSlots && e == cudaSuccess; ++b) {
             e = cudaMallocAsync(&h->d_slot[b], slot, as);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_tin[b], cudaEventDisableTiming);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_tdone[b], cudaEventDisableTiming);
@@ -192,11 +192,11 @@ gz_status gz_create(uint32_t V, uint64_t seed, const gz_config* cfg, void* strea
     if (e == cudaSuccess) e = cudaMallocAsync(&h->d_cursor, (size_t)(V + 1) * 4, as);
     if (e == cudaSuccess && h->cfg.kernel == GZ_KERNEL_BATCHED)
         e = cudaMallocAsync(&h->d_records, (size_t)2 * h->chunk * 4, as);
-    if (e == cudaSuccess) e = cudaMallocAsync(&h->d_flags, 16, as);
+    if (e == cudaSuccess) e = cudaMallocAsync(&h->d_flags, 32, as);  // [4], [5]: node window
     if (e == cudaSuccess) e = cudaMallocAsync(&h->d_scan_tmp, ((size_t)(V + 1) / 1024 + 2) * 4, as);
     if (e == cudaSuccess) e = cudaMallocAsync(&h->d_stats, 2 * sizeof(uint64_t), as);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_stats, 0, 2 * sizeof(uint64_t), h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, 16, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, 32, h->stream);
     s = cuda_check(h, e, "gz_create allocation");
     if (s == GZ_OK) s = ingest_setup(h);
     // allocations are stream-ordered: complete them before the handle is
@@ -222,7 +222,7 @@ gz_status gz_destroy(gz_handle* h) {
                     h->q_F, h->q_F2,
                     h->q_M, h->q_M2, h->q_flag, h->q_pos, h->q_forest, h->q_ctr, h->q_res,
                     h->q_acc, h->q_trace, h->d_stats, h->d_scan_tmp, h->d_tile_node, h->d_decode,
-                    h->d_slot[0], h->d_slot[1], h->d_gather};
+                    h->d_slot[0], h->d_slot[1], h->d_slot[2], h->d_gather};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, h->stream);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);
@@ -234,7 +234,7 @@ gz_status gz_destroy(gz_handle* h) {
         if (h->ev_free[b]) cudaEventDestroy(h->ev_free[b]);
     }
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < gz_handle::kTierSlots; ++b) {
         if (h->ev_tin[b]) cudaEventDestroy(h->ev_tin[b]);
         if (h->ev_tdone[b]) cudaEventDestroy(h->ev_tdone[b]);
         if (h->ev_tout[b]) cudaEventDestroy(h->ev_tout[b]);

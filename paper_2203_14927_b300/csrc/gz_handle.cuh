@@ -37,7 +37,7 @@ struct gz_handle {
     uint32_t* d_decode = nullptr;  // (u, v) x chunk decoded from packed indices (lazy)
     cudaStream_t copy_stream = nullptr;  // H2D copies of host input (lazy)
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
-    uint32_t* d_flags = nullptr;   // [0] batch invalid, [1] work counter, [2] sticky invalid
+    uint32_t* d_flags = nullptr;   // [0] batch invalid, [1] work counter, [2] sticky invalid, [4..5] node window
     uint32_t* d_scan_tmp = nullptr; // ceil((V+1)/1024) tile sums of the scans
     uint32_t block = 0;            // columns padded to a warp multiple
     uint32_t smem_rows = 0, tile = 0, small_seg = 0, batched_grid = 0;
@@ -50,10 +50,10 @@ struct gz_handle {
     bool tiered = false;
     uint32_t shard_nodes = 0, res_nodes = 0;
     uint8_t* h_sketch = nullptr;
-    uint8_t* d_slot[2] = {nullptr, nullptr};
+    static constexpr int kTierSlots = 3;  // copy-in, update and copy-out of three shards in flight
+    uint8_t* d_slot[kTierSlots] = {};
     cudaStream_t tier_in = nullptr, tier_out = nullptr;
-    cudaEvent_t ev_tin[2] = {nullptr, nullptr}, ev_tdone[2] = {nullptr, nullptr},
-                ev_tout[2] = {nullptr, nullptr};
+    cudaEvent_t ev_tin[kTierSlots] = {}, ev_tdone[kTierSlots] = {}, ev_tout[kTierSlots] = {};
     uint8_t* d_gather = nullptr;   // query: CubeSketch r of every node, V * per_k_bytes
 
     // query scratch (allocated on first query)

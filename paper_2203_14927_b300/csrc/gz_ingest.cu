@@ -168,10 +168,19 @@ struct BatchedArgs {
     uint32_t* work;  // tile counter
     unsigned long long* stats;  // [0] rows flushed, [1] deep column updates
     uint32_t V, K, R, ncol, Rs, tile, small_seg;
-    // node window: only records of nodes [node_lo, node_hi) are applied, and
-    // node x's sketch is at s.base + (x - node_lo) * s.node_bytes
-    uint32_t node_lo, node_hi;
 };
+
+// The windowed variant (sketches beyond HBM) applies only the records of nodes
+// [flags[4], flags[5]); node x's sketch is at s.base + x * s.node_bytes, so for
+// a window whose sketches start at address a the host passes
+// s.base = a - node_lo * node_bytes (computed as an integer; only window nodes
+// are addressed).  The window lives in device memory, not in BatchedArgs, so
+// that the all-HBM kernel's arguments stay as small as they are.
+__global__ void k_set_window(uint32_t* flags, uint32_t node_lo, uint32_t node_hi) {
+    flags[1] = 0;  // tile counter
+    flags[4] = node_lo;
+    flags[5] = node_hi;
+}
 
 // tile_node[t] = the node x with offsets[x] <= t*tile < offsets[x+1]: node x
 // owns the tiles whose first record falls inside its segment.
@@ -263,7 +272,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // stage buffers make those the only ones.  (Warps that claim and stage tiles
 // on their own, with no barrier at all, measured slower: the staging is then
 // repeated per warp and the larger per-warp buffers cost occupancy.)
-template <int kMode, bool kWide>
+template <int kMode, bool kWide, bool kWin>
 __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
     extern __shared__ __align__(16) uint64_t smem[];
     if (p.flags[0]) return;
@@ -284,9 +293,16 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
     for (uint32_t i = c; i < 3 * RC; i += CP) sw[i] = 0;
     const uint32_t total = p.offsets[p.V];
     // the window's records [rec_lo, rec_hi) lie in tiles t_lo .. t_lo+ntiles-1
-    const uint32_t rec_lo = p.offsets[p.node_lo], rec_hi = p.offsets[p.node_hi];
-    const uint32_t t_lo = rec_lo / T;
-    const uint32_t ntiles = rec_hi > rec_lo ? (rec_hi + T - 1) / T - t_lo : 0u;
+    // (kWin false: the whole chunk, with the bounds known at compile time)
+    uint32_t rec_lo = 0, rec_hi = total, t_lo = 0, ntiles = (total + T - 1) / T;
+    uint32_t node_lo = 0;
+    if constexpr (kWin) {
+        node_lo = p.flags[4];
+        rec_lo = p.offsets[node_lo];
+        rec_hi = p.offsets[p.flags[5]];
+        t_lo = rec_lo / T;
+        ntiles = rec_hi > rec_lo ? (rec_hi + T - 1) / T - t_lo : 0u;
+    }
     unsigned long long n_rows = 0, n_deep = 0;
 
     // records of tile t -> raw[buf]: 16-byte granules, the tail zero-filled
@@ -314,7 +330,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
     uint32_t x_next = 0;
     if (s_t[0] < ntiles) {
         fetch(t_lo + s_t[0], 0);
-        x_next = max(p.tile_node[t_lo + s_t[0]], p.node_lo);
+        x_next = kWin ? max(p.tile_node[t_lo + s_t[0]], node_lo) : p.tile_node[s_t[0]];
     }
     uint32_t sbuf = 0;
     for (uint32_t it = 0;; ++it) {
@@ -326,7 +342,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
         if (c == 0) claimed = atomicAdd(p.work, 1u);
         if (tn < ntiles) {
             fetch(t_lo + tn, (it + 1) % 3);  // that buffer was last read in iteration it-2
-            x_next = max(p.tile_node[t_lo + tn], p.node_lo);
+            x_next = kWin ? max(p.tile_node[t_lo + tn], node_lo) : p.tile_node[tn];
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
@@ -335,12 +351,18 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
         __syncthreads();  // raw[it%3] complete and visible; s_t up to date
         const uint32_t* rb = raw + (it % 3) * T;
         const uint32_t tile_lo = (t_lo + t) * T;  // raw[] holds records from tile_lo on
-        const uint32_t hi = min(tile_lo + T, rec_hi);
-        uint32_t x = x_first, pos = max(tile_lo, rec_lo);
+        uint32_t hi, pos;
+        if constexpr (kWin) {
+            hi = min(tile_lo + T, rec_hi);
+            pos = max(tile_lo, rec_lo);
+        } else {
+            hi = min(tile_lo + T, total);
+            pos = tile_lo;
+        }
+        uint32_t x = x_first;
         while (pos < hi) {
             const uint32_t seg_end = min(p.offsets[x + 1], hi);
             const uint32_t nseg = seg_end - pos;
-            const uint32_t xs = x - p.node_lo;  // node's place in the sketch window
             if (nseg > 0) {
                 // this stage buffer was last read two segments ago, before the
                 // previous segment's barrier
@@ -374,9 +396,9 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                                 fp = q.y;
                             }
                             const uint32_t d = exact_depth(depth_word(ka, kb, idx), R);
-                            atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(xs, k, d, j)),
+                            atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, d, j)),
                                       (unsigned long long)idx);
-                            atomicXor(p.s.gamma(xs, k, d, j), checksum_w(key, fp));
+                            atomicXor(p.s.gamma(x, k, d, j), checksum_w(key, fp));
                         }
                     }
                 } else if (active) {
@@ -398,9 +420,9 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                         ++n_deep;
                         const uint64_t idx = ((uint64_t)xhi << 32) | xlo;
                         const uint32_t dd = exact_depth(depth_word(p.keys.a[c], p.keys.b[c], idx), R);
-                        atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(xs, k, dd, j)),
+                        atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, dd, j)),
                                   (unsigned long long)idx);
-                        atomicXor(p.s.gamma(xs, k, dd, j), g);
+                        atomicXor(p.s.gamma(x, k, dd, j), g);
                     };
                     uint32_t i = 0;
                     // four records at a time in straight-line code, so the
@@ -480,9 +502,9 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                         const uint64_t a = kMode == 1 ? (((uint64_t)w[32] << 32) | w[0]) : ca[row * 48];
                         const uint32_t g = w[64];
                         if (a | g) {
-                            atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(xs, k, row, j)),
+                            atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, row, j)),
                                       (unsigned long long)a);
-                            atomicXor(p.s.gamma(xs, k, row, j), g);
+                            atomicXor(p.s.gamma(x, k, row, j), g);
                             if (kMode == 1) {
                                 w[0] = 0;
                                 w[32] = 0;
@@ -506,10 +528,14 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
 
 using BatchedFn = void (*)(BatchedArgs);
 
-// mode: 0 load-xor-store, 1 32-bit shared atomics
-static BatchedFn batched_fn(uint32_t mode, bool wide) {
-    if (mode == 1) return wide ? k_batched<1, true> : k_batched<1, false>;
-    return wide ? k_batched<0, true> : k_batched<0, false>;
+// mode: 0 load-xor-store, 1 32-bit shared atomics; win: a node window (sketches beyond HBM)
+static BatchedFn batched_fn(uint32_t mode, bool wide, bool win = false) {
+    if (win) {
+        if (mode == 1) return wide ? k_batched<1, true, true> : k_batched<1, false, true>;
+        return wide ? k_batched<0, true, true> : k_batched<0, false, true>;
+    }
+    if (mode == 1) return wide ? k_batched<1, true, false> : k_batched<1, false, false>;
+    return wide ? k_batched<0, true, false> : k_batched<0, false, false>;
 }
 
 // Raise the dynamic shared-memory cap of every batched-kernel variant to the
@@ -518,8 +544,8 @@ static cudaError_t set_smem_cap(int device) {
     int cap = 0;
     cudaError_t e = cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     for (int mode = 0; mode < 2 && e == cudaSuccess; ++mode)
-        for (int wide = 0; wide < 2 && e == cudaSuccess; ++wide) {
-            const void* fn = (const void*)batched_fn(mode, wide != 0);
+        for (int v = 0; v < 4 && e == cudaSuccess; ++v) {
+            const void* fn = (const void*)batched_fn(mode, (v & 1) != 0, (v & 2) != 0);
             cudaFuncAttributes fa;
             e = cudaFuncGetAttributes(&fa, fn);  // the kernel's static shared memory counts too
             if (e == cudaSuccess)
@@ -648,52 +674,52 @@ static BatchedArgs batched_args(gz_handle* h) {
     a.tile = h->tile;
     a.small_seg = h->small_seg;
     a.stats = reinterpret_cast<unsigned long long*>(h->d_stats);
-    a.node_lo = 0;
-    a.node_hi = h->V;
     return a;
 }
 
 // Sketches beyond HBM: the batched update of one partitioned chunk, window by
-// window.  Resident nodes are updated in place; each host shard is copied into
-// device slot (i & 1) on tier_in, updated on st, and copied back on tier_out.
+// window.  Resident nodes are updated in place; host shard i is copied into
+// device slot i mod kTierSlots on tier_in, updated on st, and copied back on
+// tier_out.
 // A slot's copy-in waits for its previous copy-out, and tier_out runs its
 // copies in issue order, so a shard's copy-in also follows its copy-out of the
 // previous chunk.  The tile counter is cleared before every launch.
 static void enqueue_tiered_updates(gz_handle* h, cudaStream_t st) {
     const bool wide = (uint64_t)h->V * h->V > (1ull << 32);
-    const BatchedFn fn = batched_fn(h->delta_mode, wide);
+    const BatchedFn fn = batched_fn(h->delta_mode, wide, true);
     BatchedArgs a = batched_args(h);
     if (h->res_nodes) {
-        a.node_lo = 0;
-        a.node_hi = h->res_nodes;
+        k_set_window<<<1, 1, 0, st>>>(h->d_flags, 0, h->res_nodes);
         fn<<<h->batched_grid, h->block, h->batched_smem, st>>>(a);
     }
     uint32_t i = 0;
     for (uint32_t lo = h->res_nodes; lo < h->V; lo += h->shard_nodes, ++i) {
-        const uint32_t hi = std::min<uint32_t>(h->V, lo + h->shard_nodes), b = i & 1u;
+        const uint32_t hi = std::min<uint32_t>(h->V, lo + h->shard_nodes), b = i % gz_handle::kTierSlots;
         const size_t bytes = (size_t)(hi - lo) * h->node_bytes;
         uint8_t* host = h->h_sketch + (size_t)(lo - h->res_nodes) * h->node_bytes;
         cudaStreamWaitEvent(h->tier_in, h->ev_tout[b], 0);  // an event never recorded is complete
         cudaMemcpyAsync(h->d_slot[b], host, bytes, cudaMemcpyHostToDevice, h->tier_in);
         cudaEventRecord(h->ev_tin[b], h->tier_in);
         cudaStreamWaitEvent(st, h->ev_tin[b], 0);
-        cudaMemsetAsync(h->d_flags + 1, 0, sizeof(uint32_t), st);  // tile counter
-        a.s.base = h->d_slot[b];
-        a.node_lo = lo;
-        a.node_hi = hi;
+        k_set_window<<<1, 1, 0, st>>>(h->d_flags, lo, hi);
+        // node lo lives at the slot's start: base = slot - lo * node_bytes, as an integer
+        a.s.base = reinterpret_cast<uint8_t*>(reinterpret_cast<uintptr_t>(h->d_slot[b]) -
+                                              (uintptr_t)lo * h->node_bytes);
         fn<<<h->batched_grid, h->block, h->batched_smem, st>>>(a);
         cudaEventRecord(h->ev_tdone[b], st);
         cudaStreamWaitEvent(h->tier_out, h->ev_tdone[b], 0);
         cudaMemcpyAsync(host, h->d_slot[b], bytes, cudaMemcpyDeviceToHost, h->tier_out);
         cudaEventRecord(h->ev_tout[b], h->tier_out);
     }
-    h->launches += i + (h->res_nodes ? 1 : 0) - 1;  // beyond the one batched launch counted per chunk
+    // beyond the one batched launch counted per chunk: the other windows and the window setters
+    h->launches += 2 * (i + (h->res_nodes ? 1 : 0)) - 1;
 }
 
 gz_status tier_settle(gz_handle* h) {
     if (!h->tiered) return GZ_OK;
-    cudaError_t e = cudaStreamWaitEvent(h->stream, h->ev_tout[0], 0);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_tout[1], 0);
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < gz_handle::kTierSlots && e == cudaSuccess; ++b)
+        e = cudaStreamWaitEvent(h->stream, h->ev_tout[b], 0);
     return cuda_check(h, e, "tier settle");
 }
 
@@ -1082,8 +1108,6 @@ extern "C" gz_status gz_sketch_update_noalloc(void* sketch, uint32_t V, uint64_t
         a.Rs = Rs;
         a.tile = tile;
         a.small_seg = 4;
-        a.node_lo = 0;
-        a.node_hi = V;
         const size_t smem = (size_t)Rs * block * 12 + (size_t)tile * (12 + (wide ? 32 : 16));
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_fn(1, wide), (int)block, smem) !=
