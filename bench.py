@@ -635,9 +635,11 @@ def run_serve(args, rank: int, world: int):
         events.sort(key=lambda x: x[0])
         return events
 
+    graph_cfg = json.loads(args.cfg) if args.cfg else {}
+
     def serve(events, slots, one_at_a_time=False, paced=False):
         srv = gz.Server(hbm_budget=int(args.serve_budget_gb * 1e9), slots=slots, max_batch=8)
-        gids = [srv.add_graph(g["V"], g["seed"]) for g in graphs]
+        gids = [srv.add_graph(g["V"], g["seed"], **graph_cfg) for g in graphs]
         torch.cuda.synchronize()
 
         def submit(ev):
@@ -678,6 +680,7 @@ def run_serve(args, rank: int, world: int):
                 "peak_resident_gb": st["peak_resident_bytes"] / 1e9}
 
     events0 = schedule(1.0)
+    serve(events0, args.serve_slots)  # warm-up: lazy module loads, graph captures, memory pool
     mixed = serve(events0, args.serve_slots)  # all requests at once, arrival order
     seq = serve(events0, 1, one_at_a_time=True)
     window = max(1.0, total_updates / (0.5 * mixed["updates_per_s"]))

@@ -65,8 +65,10 @@ typedef struct {
     uint32_t small_segment; /* node segments shorter than this skip shared-memory staging (default 4) */
     uint32_t smem_mode;     /* delta update in shared memory: 0 default (= 1), 1 32-bit shared
                                atomics, 2 load-xor-store */
-    uint32_t no_graph;      /* 1: launch a chunk's kernels one by one instead of replaying the
-                               CUDA graph captured for the handle after its 8th chunk (default 0) */
+    uint32_t no_graph;      /* 1: no CUDA graphs: launch a chunk's kernels one by one instead of
+                               replaying the graph captured after the handle's 8th chunk, and drive
+                               a CC query's rounds from the host instead of one captured graph
+                               with a device-side loop (default 0) */
     uint32_t device_sketch_mb; /* HBM for node sketches, MiB (0: all of them in HBM).  When the
                                sketches need more, nodes beyond the budget live in pinned host
                                memory (sketches beyond HBM, below) */
@@ -287,7 +289,10 @@ typedef struct {
     uint64_t completed_requests;
 } gz_server_stats;
 
-/* Start a server on the current device (cfg may be NULL). */
+/* Start a server on the current device (cfg may be NULL).  The server raises
+ * the release threshold of the device's default stream-ordered memory pool to
+ * its HBM budget, so memory of released graphs is kept for later admissions
+ * (the setting is the device's, shared with the rest of the process). */
 gz_status gz_server_create(const gz_server_config *cfg, gz_server **out);
 
 /* Finish every accepted request, then stop the workers and free everything. */

@@ -225,7 +225,7 @@ gz_status gz_destroy(gz_handle* h) {
                     h->d_slot[0], h->d_slot[1], h->d_slot[2], h->d_gather};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, h->stream);
-    if (h->h_ctr) cudaFreeHost(h->h_ctr);
+    delete[] h->h_ctr;
     if (h->q_graph_exec) cudaGraphExecDestroy(h->q_graph_exec);
     if (h->q_graph) cudaGraphDestroy(h->q_graph);
     for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);

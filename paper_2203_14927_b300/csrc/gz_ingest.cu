@@ -15,6 +15,9 @@
 // also lets two CTAs share one heavy node whose segment spans tiles.
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <mutex>
+
 #include <algorithm>
 #include <vector>
 
@@ -539,8 +542,22 @@ static BatchedFn batched_fn(uint32_t mode, bool wide, bool win = false) {
 }
 
 // Raise the dynamic shared-memory cap of every batched-kernel variant to the
-// device's opt-in maximum (idempotent; safe to call from any thread).
+// device's opt-in maximum, once per device (idempotent; safe to call from any
+// thread: a server creates handles from several worker threads).
+static cudaError_t set_smem_cap_once(int device);
 static cudaError_t set_smem_cap(int device) {
+    constexpr int kDevices = 64;
+    static std::atomic<bool> done[kDevices];
+    static std::mutex mu;
+    if (device >= 0 && device < kDevices && done[device].load(std::memory_order_acquire)) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(mu);
+    if (device >= 0 && device < kDevices && done[device].load(std::memory_order_relaxed)) return cudaSuccess;
+    const cudaError_t e = set_smem_cap_once(device);
+    if (e == cudaSuccess && device >= 0 && device < kDevices) done[device].store(true, std::memory_order_release);
+    return e;
+}
+
+static cudaError_t set_smem_cap_once(int device) {
     int cap = 0;
     cudaError_t e = cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     for (int mode = 0; mode < 2 && e == cudaSuccess; ++mode)

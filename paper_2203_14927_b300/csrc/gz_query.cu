@@ -438,7 +438,12 @@ gz_status query_setup(gz_handle* h) {
     if (e == cudaSuccess) e = alloc32(&h->q_ctr, C_N);
     if (e == cudaSuccess) e = cudaMallocAsync(&h->q_res, V * sizeof(int64_t), h->stream);
     if (e == cudaSuccess) e = cudaMallocAsync(&h->q_acc, (size_t)h->q_slots_cap * h->per_k_bytes, h->stream);
-    if (e == cudaSuccess) e = cudaMallocHost(&h->h_ctr, C_N * sizeof(uint32_t));  // pinned: read in a graph
+    if (e == cudaSuccess) {
+        // pageable: pinned allocations are expensive to make and free for
+        // short-lived handles (a server creates and releases many)
+        h->h_ctr = new (std::nothrow) uint32_t[C_N];
+        if (!h->h_ctr) return set_error(h, GZ_ENOMEM, "query counters");
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_check(h, e, "query scratch allocation");
     h->query_ready = true;
@@ -523,7 +528,7 @@ static void enqueue_relabel(gz_handle* h, const QArgs& q, cudaStream_t stm) {
 }
 
 // kernels of a query run as one CUDA graph: start, round 0, WHILE(another
-// round) { round }, component count and counters to the host
+// round) { round }, component count
 constexpr uint64_t kLaunchesStartEnd = 2, kLaunchesRound0 = 5, kLaunchesRound = 11;
 
 // The CC query as one CUDA graph, captured once per handle: round 0, then a
@@ -571,10 +576,7 @@ static gz_status build_query_graph(gz_handle* h) {
                 e = cudaStreamEndCapture(bs, &body);
             }
         }
-        if (e == cudaSuccess) {
-            k_q_ncc<<<grid_for(h, h->V, kTpb), kTpb, 0, cs>>>(q);
-            e = cudaMemcpyAsync(h->h_ctr, h->q_ctr, C_N * sizeof(uint32_t), cudaMemcpyDeviceToHost, cs);
-        }
+        if (e == cudaSuccess) k_q_ncc<<<grid_for(h, h->V, kTpb), kTpb, 0, cs>>>(q);
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         if (e == cudaSuccess) e = e2;
@@ -608,9 +610,12 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
     const uint32_t V = h->V;
     cudaError_t e = cudaSuccess;
 
-    if (!want_forest && !h->trace && !h->tiered) {
+    if (!want_forest && !h->trace && !h->tiered && !h->cfg.no_graph) {
         if (!h->q_graph_exec && (s = build_query_graph(h)) != GZ_OK) return s;
         e = cudaGraphLaunch(h->q_graph_exec, stm);
+        // counters after the graph: pageable host memory stays out of the graph
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->h_ctr, h->q_ctr, C_N * sizeof(uint32_t), cudaMemcpyDeviceToHost, stm);
     } else {
         // forest, trace or sketches beyond HBM: the same rounds driven from
         // the host, which reads the round's counters after the sampler (the

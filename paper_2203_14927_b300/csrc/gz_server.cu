@@ -257,6 +257,18 @@ gz_status gz_server_create(const gz_server_config* cfg, gz_server** out) {
         }
         s->cfg.hbm_budget = (uint64_t)(0.8 * fr);
     }
+    // Graphs are admitted and released all the time; keep up to the budget of
+    // freed memory in the device's stream-ordered pool instead of returning it
+    // to the driver at every synchronisation (the pool's default), so an
+    // admission reuses memory a released graph left.  This is a property of
+    // the device's default pool, shared with the rest of the process.
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess) {
+        uint64_t keep = s->cfg.hbm_budget;
+        uint64_t cur = 0;
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) == cudaSuccess && cur < keep)
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     s->t0 = Clock::now();
     for (uint32_t i = 0; i < s->cfg.slots; ++i) {
         cudaStream_t st;
