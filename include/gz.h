@@ -45,7 +45,8 @@ typedef enum {
     GZ_ENOMEM = 2,       /* device or host allocation failed */
     GZ_ECUDA = 3,        /* a CUDA call failed; see gz_last_error */
     GZ_ESKETCH_FAIL = 4, /* query finished but a sketch failed (result may be wrong) */
-    GZ_ETIMEOUT = 5,     /* reserved: a bounded device wait ran out */
+    GZ_ETIMEOUT = 5,     /* a bounded wait in the update kernel ran out (reported,
+                            like a discarded batch, by the next sync, query or export) */
     GZ_EBUSY = 6         /* reserved */
 } gz_status;
 
@@ -153,7 +154,8 @@ gz_status gz_edge_update(gz_handle *h, const uint32_t *u, const uint32_t *v,
 gz_status gz_edge_update_idx(gz_handle *h, const uint64_t *idx, size_t n, int on_device);
 
 /* Wait for all queued work of the handle; returns GZ_EINVAL once if a batch
- * was rejected since the last report. */
+ * was rejected since the last report, GZ_ETIMEOUT once if a bounded wait of
+ * the update kernel ran out (its sketches are then incomplete). */
 gz_status gz_sync(gz_handle *h);
 
 /* Zero every node sketch (the empty graph). */
@@ -352,7 +354,8 @@ const char *gz_server_last_error(gz_server *s);
  *            validation as gz_edge_update: a self loop or an id >= V discards
  *            the whole batch.
  *   status : device u32 or NULL; set on the stream to 1 when the batch was
- *            discarded, else 0.
+ *            discarded, 2 when a bounded wait of the update kernel ran out
+ *            (the sketches are then incomplete), else 0.
  *   stream : cudaStream_t of all the work (NULL = default stream).
  * Returns GZ_EINVAL (nothing queued) for V or n beyond the limits or null
  * pointers, GZ_ECUDA when a CUDA call fails.  The first call on a device sets

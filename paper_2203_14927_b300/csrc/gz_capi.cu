@@ -354,15 +354,17 @@ gz_status gz_edge_update_idx(gz_handle* h, const uint64_t* idx, size_t n, int on
     return GZ_OK;
 }
 
+// flags[2]: sticky "a batch was discarded"; flags[3]: sticky "a bounded wait
+// of the update kernel ran out" (its tile may be partly applied)
 static gz_status check_rejected(gz_handle* h) {
-    uint32_t f = 0;
-    cudaError_t e = cudaMemcpyAsync(&f, h->d_flags + 2, 4, cudaMemcpyDeviceToHost, h->stream);
+    uint32_t f[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(f, h->d_flags + 2, 8, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_check(h, e, "sync");
-    if (f) {
-        cudaMemsetAsync(h->d_flags + 2, 0, 4, h->stream);
+    if (f[0] || f[1]) cudaMemsetAsync(h->d_flags + 2, 0, 8, h->stream);
+    if (f[1]) return set_error(h, GZ_ETIMEOUT, "a bounded wait in the update kernel ran out; the sketches are incomplete");
+    if (f[0])
         return set_error(h, GZ_EINVAL, "an update batch held a self loop or a vertex id >= V and was discarded");
-    }
     return GZ_OK;
 }
 

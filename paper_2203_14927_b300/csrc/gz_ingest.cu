@@ -240,23 +240,49 @@ __device__ __forceinline__ uint32_t checksum_w(const ColKey& k, uint32_t fpre) {
     return h;
 }
 
-// cp.async (16-byte granules, L2 only): global -> shared without a register
-// round trip; bytes past src_bytes are zero-filled and not read.
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, uint32_t src_bytes) {
-    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(src_bytes)
+// mbarrier handover between the producer warp and the column warps.  Every
+// wait is bounded: after kTryLimit polls (each may suspend the thread for up
+// to about a microsecond) the waiter records a timeout in flags[3] and leaves
+// the kernel, which the host reports as GZ_ETIMEOUT.
+constexpr uint32_t kTryLimit = 1u << 22;
+constexpr uint32_t kRing = 3;             // staged tiles in flight per CTA
+constexpr uint32_t kDone = 0xffffffffu;   // ring entry: no tiles left
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar))
                  : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+// true once the phase of the given parity has completed; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kTryLimit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
 }
 
-// One CTA = 32*ceil(7K/32) threads; thread c owns CubeSketch column c = 7k + j
-// (one "Graph Worker" per column; no two threads write one bucket, so each
-// thread also flushes its own delta rows and no barrier separates hashing from
-// flushing).
+// One CTA = CP + 32 threads, CP = 32*ceil(7K/32).  Thread c < CP owns CubeSketch
+// column c = 7k + j (one "Graph Worker" per column; no two threads write one
+// bucket, so each thread also flushes its own delta rows).  The last warp is
+// the producer: it claims tiles (equal record counts) from an atomic counter,
+// turns each record of a tile into its edge index and checksum part, and
+// stages the tile in a kRing-slot shared-memory ring; the column warps consume
+// the ring in order.  full[b] (one arrival, the producer) says slot b holds a
+// staged tile; empty[b] (one arrival per column warp) says every column warp
+// has finished with it.  So no CTA-wide barrier sits in the loop: a column
+// warp starts on the next tile as soon as it is done with the current one.
 // Dynamic shared memory:
 //   delta rows: one 96-word block per (warp of columns, row d < Rs), warp w's
 //               block of row d at word (w*Rs + d)*96.  kMode 1 (32-bit
@@ -265,35 +291,29 @@ __device__ __forceinline__ void cp_async_wait() {
 //               u64 (+0), gamma' (+64).  A warp's 32 lanes hit 32 distinct
 //               banks whatever rows they update, and the words of a column
 //               update share one address register.
-//   raw records  [3][tile] u32, filled by cp.async one tile ahead
-//   staged records [2][tile] (kWide: uint4 {idx_lo, idx_hi, fold_pre, 0};
-//                  else uint2 {idx, fold_pre}), one buffer per node segment in turn
-// Tiles (equal record counts) are claimed from an atomic counter one tile
-// ahead, so the next tile's records and first node are fetched while the
-// current tile is being hashed.  Barriers: one per tile (its records have
-// landed) and one per node segment (its records are staged); three raw and two
-// stage buffers make those the only ones.  (Warps that claim and stage tiles
-// on their own, with no barrier at all, measured slower: the staging is then
-// repeated per warp and the larger per-warp buffers cost occupancy.)
+//   ring        [kRing][tile] staged records (kWide: uint4 {idx_lo, idx_hi,
+//               fold_pre, 0}; else uint2 {idx, fold_pre}), record r of the
+//               tile at entry r.
 template <int kMode, bool kWide, bool kWin>
 __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
     extern __shared__ __align__(16) uint64_t smem[];
+    __shared__ uint64_t full_bar[kRing], empty_bar[kRing];
+    __shared__ uint32_t s_tile[kRing], s_node[kRing];
     if (p.flags[0]) return;
-    const uint32_t CP = blockDim.x, c = threadIdx.x;
+    const uint32_t CP = blockDim.x - 32, c = threadIdx.x;
     const uint32_t Rs = p.Rs, R = p.R, RC = Rs * CP, T = p.tile;
     constexpr uint32_t kStageWords = kWide ? 4u : 2u;
     uint32_t* sw = reinterpret_cast<uint32_t*>(smem);  // delta blocks, 3*RC words
-    uint32_t* raw = sw + 3 * RC;  // [3][T], 16-byte aligned (RC multiple of 32, T multiple of 4)
-    uint32_t* stage_base = raw + 3 * T;  // [2][kStageWords*T]
-
-    const bool active = c < p.ncol;
-    const uint32_t k = c / GZ_COLS, j = c - k * GZ_COLS;
-    // word of (row 0, column c) in plane 0; row d adds d*96
-    uint32_t* cw = sw + (c >> 5) * Rs * 96 + (c & 31);
-    uint64_t* ca = reinterpret_cast<uint64_t*>(sw + (c >> 5) * Rs * 96) + (c & 31);  // kMode 0 alpha
-    ColKey key{};
-    if (active) key = make_colkey(p.keys.a[c], p.keys.b[c], p.keys.c[c]);
-    for (uint32_t i = c; i < 3 * RC; i += CP) sw[i] = 0;
+    uint32_t* ring = sw + 3 * RC;  // 16-byte aligned: RC is a multiple of 32, T of 4
+    uint32_t* timeout = const_cast<uint32_t*>(p.flags) + 3;
+    for (uint32_t i = c; i < 3 * RC; i += blockDim.x) sw[i] = 0;
+    if (c == 0) {
+        for (uint32_t b = 0; b < kRing; ++b) {
+            mbar_init(&full_bar[b], 1);
+            mbar_init(&empty_bar[b], CP / 32);
+        }
+    }
+    __syncthreads();
     const uint32_t total = p.offsets[p.V];
     // the window's records [rec_lo, rec_hi) lie in tiles t_lo .. t_lo+ntiles-1
     // (kWin false: the whole chunk, with the bounds known at compile time)
@@ -306,54 +326,90 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
         t_lo = rec_lo / T;
         ntiles = rec_hi > rec_lo ? (rec_hi + T - 1) / T - t_lo : 0u;
     }
+
+    if (c >= CP) {
+        // ---------------------------------------------------------- producer
+        const uint32_t lane = c - CP;
+        for (uint32_t it = 0;; ++it) {
+            const uint32_t b = it % kRing, ph = (it / kRing) & 1u;
+            if (!mbar_wait(&empty_bar[b], ph ^ 1u)) {  // a fresh slot passes at once
+                if (lane == 0) atomicOr(timeout, 1u);
+                return;
+            }
+            uint32_t t = 0;
+            if (lane == 0) t = atomicAdd(p.work, 1u);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t >= ntiles) {
+                if (lane == 0) {
+                    s_tile[b] = kDone;
+                    mbar_arrive(&full_bar[b]);
+                }
+                return;
+            }
+            const uint32_t tile_lo = (t_lo + t) * T;
+            uint32_t lo, hi;
+            if constexpr (kWin) {
+                lo = max(tile_lo, rec_lo);
+                hi = min(tile_lo + T, rec_hi);
+            } else {
+                lo = tile_lo;
+                hi = min(tile_lo + T, total);
+            }
+            uint32_t x = kWin ? max(p.tile_node[t_lo + t], node_lo) : p.tile_node[t];
+            if (lane == 0) {
+                s_tile[b] = t;
+                s_node[b] = x;
+            }
+            uint32_t* slot = ring + b * kStageWords * T;
+            // lane takes records lo + 32q + lane: coalesced loads, conflict-free
+            // stores, and a per-lane walk over the tile's node segments
+            uint32_t xend = p.offsets[x + 1];
+            for (uint32_t g = lo; g < hi; g += 256) {
+                uint32_t r[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const uint32_t i = g + 32 * q + lane;
+                    r[q] = i < hi ? __ldcs(p.records + i) : 0u;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const uint32_t i = g + 32 * q + lane;
+                    if (i < hi) {
+                        while (xend <= i) xend = p.offsets[++x + 1];
+                        const uint64_t idx = edge_index(x, r[q], p.V);
+                        if (kWide) {
+                            reinterpret_cast<uint4*>(slot)[i - tile_lo] =
+                                make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), fold_pre(idx), 0u);
+                        } else {
+                            reinterpret_cast<uint2*>(slot)[i - tile_lo] = make_uint2((uint32_t)idx, fold_pre(idx));
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full_bar[b]);
+        }
+    }
+
+    // ------------------------------------------------------------ column warps
+    const bool active = c < p.ncol;
+    const uint32_t k = c / GZ_COLS, j = c - k * GZ_COLS;
+    // word of (row 0, column c) in plane 0; row d adds d*96
+    uint32_t* cw = sw + (c >> 5) * Rs * 96 + (c & 31);
+    uint64_t* ca = reinterpret_cast<uint64_t*>(sw + (c >> 5) * Rs * 96) + (c & 31);  // kMode 0 alpha
+    ColKey key{};
+    if (active) key = make_colkey(p.keys.a[c], p.keys.b[c], p.keys.c[c]);
     unsigned long long n_rows = 0, n_deep = 0;
-
-    // records of tile t -> raw[buf]: 16-byte granules, the tail zero-filled
-    auto fetch = [&](uint32_t t, uint32_t buf) {
-        const uint32_t lo = t * T;
-        const uint32_t bytes = (min(lo + T, total) - lo) * 4u;
-        for (uint32_t q = c; q * 16 < T * 4; q += CP) {
-            const uint32_t off = q * 16;
-            const uint32_t n = off < bytes ? min(16u, bytes - off) : 0u;
-            cp_async16(raw + buf * T + q * 4, p.records + lo + (n ? q * 4 : 0), n);
-        }
-        cp_async_commit();
-    };
-
-    // Tile ring s_t: iteration it processes s_t[it%3], prefetches s_t[(it+1)%3]
-    // and thread 0 writes the tile claimed for iteration it+2 into
-    // s_t[(it+2)%3] before the iteration's barrier; every thread read that slot
-    // (as iteration it-1's tile) before the previous barrier.
-    __shared__ uint32_t s_t[3];
-    if (c == 0) {
-        s_t[0] = atomicAdd(p.work, 1u);
-        s_t[1] = atomicAdd(p.work, 1u);
-    }
-    __syncthreads();
-    uint32_t x_next = 0;
-    if (s_t[0] < ntiles) {
-        fetch(t_lo + s_t[0], 0);
-        x_next = kWin ? max(p.tile_node[t_lo + s_t[0]], node_lo) : p.tile_node[s_t[0]];
-    }
-    uint32_t sbuf = 0;
     for (uint32_t it = 0;; ++it) {
-        const uint32_t t = s_t[it % 3];
-        if (t >= ntiles) break;
-        const uint32_t x_first = x_next;
-        const uint32_t tn = s_t[(it + 1) % 3];
-        uint32_t claimed = 0;
-        if (c == 0) claimed = atomicAdd(p.work, 1u);
-        if (tn < ntiles) {
-            fetch(t_lo + tn, (it + 1) % 3);  // that buffer was last read in iteration it-2
-            x_next = kWin ? max(p.tile_node[t_lo + tn], node_lo) : p.tile_node[tn];
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
+        const uint32_t b = it % kRing, ph = (it / kRing) & 1u;
+        if (!mbar_wait(&full_bar[b], ph)) {
+            atomicOr(timeout, 1u);
+            break;
         }
-        if (c == 0) s_t[(it + 2) % 3] = claimed;
-        __syncthreads();  // raw[it%3] complete and visible; s_t up to date
-        const uint32_t* rb = raw + (it % 3) * T;
-        const uint32_t tile_lo = (t_lo + t) * T;  // raw[] holds records from tile_lo on
+        const uint32_t t = s_tile[b];
+        if (t == kDone) break;
+        uint32_t x = s_node[b];
+        const uint32_t tile_lo = (t_lo + t) * T;
         uint32_t hi, pos;
         if constexpr (kWin) {
             hi = min(tile_lo + T, rec_hi);
@@ -362,49 +418,35 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
             hi = min(tile_lo + T, total);
             pos = tile_lo;
         }
-        uint32_t x = x_first;
+        const uint32_t* slot = ring + b * kStageWords * T;
         while (pos < hi) {
             const uint32_t seg_end = min(p.offsets[x + 1], hi);
             const uint32_t nseg = seg_end - pos;
-            if (nseg > 0) {
-                // this stage buffer was last read two segments ago, before the
-                // previous segment's barrier
-                uint32_t* stage = stage_base + sbuf * kStageWords * T;
-                uint4* stage4 = reinterpret_cast<uint4*>(stage);
-                uint2* stage2 = reinterpret_cast<uint2*>(stage);
-                sbuf ^= 1u;
-                for (uint32_t i = c; i < nseg; i += CP) {
-                    const uint64_t idx = edge_index(x, rb[pos - tile_lo + i], p.V);
-                    if (kWide) {
-                        stage4[i] = make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), fold_pre(idx), 0u);
-                    } else {
-                        stage2[i] = make_uint2((uint32_t)idx, fold_pre(idx));
-                    }
-                }
-                __syncthreads();
+            if (nseg > 0 && active) {
+                const uint32_t sb = pos - tile_lo;  // the segment's first ring entry
+                const uint4* stage4 = reinterpret_cast<const uint4*>(slot) + sb;
+                const uint2* stage2 = reinterpret_cast<const uint2*>(slot) + sb;
                 if (nseg < p.small_seg) {
                     // short segment: straight to global memory
-                    if (active) {
-                        const uint64_t ka = p.keys.a[c], kb = p.keys.b[c];
-                        for (uint32_t i = 0; i < nseg; ++i) {
-                            uint64_t idx;
-                            uint32_t fp;
-                            if (kWide) {
-                                const uint4 q = stage4[i];
-                                idx = (uint64_t)q.y << 32 | q.x;
-                                fp = q.z;
-                            } else {
-                                const uint2 q = stage2[i];
-                                idx = q.x;
-                                fp = q.y;
-                            }
-                            const uint32_t d = exact_depth(depth_word(ka, kb, idx), R);
-                            atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, d, j)),
-                                      (unsigned long long)idx);
-                            atomicXor(p.s.gamma(x, k, d, j), checksum_w(key, fp));
+                    const uint64_t ka = p.keys.a[c], kb = p.keys.b[c];
+                    for (uint32_t i = 0; i < nseg; ++i) {
+                        uint64_t idx;
+                        uint32_t fp;
+                        if (kWide) {
+                            const uint4 q = stage4[i];
+                            idx = (uint64_t)q.y << 32 | q.x;
+                            fp = q.z;
+                        } else {
+                            const uint2 q = stage2[i];
+                            idx = q.x;
+                            fp = q.y;
                         }
+                        const uint32_t d = exact_depth(depth_word(ka, kb, idx), R);
+                        atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, d, j)),
+                                  (unsigned long long)idx);
+                        atomicXor(p.s.gamma(x, k, d, j), checksum_w(key, fp));
                     }
-                } else if (active) {
+                } else {
                     uint32_t md = 0;  // deepest delta row this column touched
                     // one column update staged in shared memory (d < Rs)
                     auto put = [&](uint32_t d, uint32_t xlo, uint32_t xhi, uint32_t g) {
@@ -427,7 +469,33 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                                   (unsigned long long)idx);
                         atomicXor(p.s.gamma(x, k, dd, j), g);
                     };
+                    // one staged record
+                    auto one = [&](uint32_t i) {
+                        uint32_t xlo, xhi, fp;
+                        if (kWide) {
+                            const uint4 q = stage4[i];
+                            xlo = q.x;
+                            xhi = q.y;
+                            fp = q.z;
+                        } else {
+                            const uint2 q = stage2[i];
+                            xlo = q.x;
+                            xhi = 0;
+                            fp = q.y;
+                        }
+                        const uint32_t d = __clz(depth_hi<kWide>(key, xlo, xhi));
+                        const uint32_t g = checksum_w(key, fp);
+                        if (d < Rs) {
+                            put(d, xlo, xhi, g);
+                            md = max(md, d);
+                        } else {
+                            deep(xlo, xhi, g);
+                        }
+                    };
                     uint32_t i = 0;
+                    // narrow records: pairs are read as one 16-byte word, so
+                    // start the loop on an even ring entry
+                    if (!kWide && (sb & 1u)) one(i++);
                     // four records at a time in straight-line code, so the
                     // four hash chains interleave; one rare branch for deep rows
                     for (; i + 4 <= nseg; i += 4) {
@@ -441,8 +509,8 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                                 fp[r] = q.z;
                             }
                         } else {
-                            const uint4 q0 = reinterpret_cast<const uint4*>(stage2)[i >> 1];
-                            const uint4 q1 = reinterpret_cast<const uint4*>(stage2)[(i >> 1) + 1];
+                            const uint4 q0 = *reinterpret_cast<const uint4*>(stage2 + i);
+                            const uint4 q1 = *reinterpret_cast<const uint4*>(stage2 + i + 2);
                             xlo[0] = q0.x;
                             fp[0] = q0.y;
                             xlo[1] = q0.z;
@@ -477,28 +545,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                             }
                         }
                     }
-                    for (; i < nseg; ++i) {
-                        uint32_t xlo, xhi, fp;
-                        if (kWide) {
-                            const uint4 q = stage4[i];
-                            xlo = q.x;
-                            xhi = q.y;
-                            fp = q.z;
-                        } else {
-                            const uint2 q = stage2[i];
-                            xlo = q.x;
-                            xhi = 0;
-                            fp = q.y;
-                        }
-                        const uint32_t d = __clz(depth_hi<kWide>(key, xlo, xhi));
-                        const uint32_t g = checksum_w(key, fp);
-                        if (d < Rs) {
-                            put(d, xlo, xhi, g);
-                            md = max(md, d);
-                        } else {
-                            deep(xlo, xhi, g);
-                        }
-                    }
+                    for (; i < nseg; ++i) one(i);
                     // flush this column's touched rows into the node sketch
                     for (uint32_t row = 0; row <= md; ++row) {
                         uint32_t* w = cw + row * 96;
@@ -523,8 +570,9 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
             pos = seg_end;
             ++x;
         }
+        __syncwarp();  // the whole warp is done with slot b
+        if ((c & 31) == 0) mbar_arrive(&empty_bar[b]);
     }
-    cp_async_wait<0>();
     if (n_rows) atomicAdd(&p.stats[0], n_rows);
     if (n_deep) atomicAdd(&p.stats[1], n_deep);
 }
@@ -642,7 +690,7 @@ static Keys keys_of(const gz_handle* h) {
 
 gz_status ingest_setup(gz_handle* h) {
     h->block = (h->ncol + 31) / 32 * 32;
-    if (h->block > 1024) return set_error(h, GZ_EINVAL, "too many CubeSketch columns for one CTA");
+    if (h->block + 32 > 1024) return set_error(h, GZ_EINVAL, "too many CubeSketch columns for one CTA");
     uint32_t rs = h->cfg.smem_rows ? h->cfg.smem_rows : 12;
     rs = std::min<uint32_t>(rs, 32);
     rs = std::min<uint32_t>(rs, h->R);
@@ -651,7 +699,7 @@ gz_status ingest_setup(gz_handle* h) {
     h->small_seg = h->cfg.small_segment ? h->cfg.small_segment : 4;
     const bool wide = (uint64_t)h->V * h->V > (1ull << 32);
     if (h->tile % 4 != 0) return set_error(h, GZ_EINVAL, "tile_records must be a multiple of 4");
-    h->batched_smem = (size_t)rs * h->block * 12 + (size_t)h->tile * (12 + (wide ? 32 : 16));
+    h->batched_smem = (size_t)rs * h->block * 12 + (size_t)h->tile * kRing * (wide ? 16 : 8);
     if (h->cfg.smem_mode > 2) return set_error(h, GZ_EINVAL, "smem_mode must be 0, 1 or 2");
     h->delta_mode = h->cfg.smem_mode == 2 ? 0u : 1u;  // kernel mode: 1 shared atomics, 0 load-xor-store
     const void* fn = (const void*)batched_fn(h->delta_mode, wide);
@@ -661,7 +709,7 @@ gz_status ingest_setup(gz_handle* h) {
     cudaError_t e = set_smem_cap(h->device);
     if (e != cudaSuccess) return cuda_check(h, e, "cudaFuncSetAttribute(k_batched)");
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, (int)h->block, h->batched_smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, (int)h->block + 32, h->batched_smem);
     if (e != cudaSuccess) return cuda_check(h, e, "occupancy(k_batched)");
     if (nb < 1) return set_error(h, GZ_EINVAL, "batched kernel does not fit on an SM");
     uint32_t per_sm = h->cfg.ctas_per_sm ? std::min<uint32_t>(h->cfg.ctas_per_sm, nb) : nb;
@@ -707,7 +755,7 @@ static void enqueue_tiered_updates(gz_handle* h, cudaStream_t st) {
     BatchedArgs a = batched_args(h);
     if (h->res_nodes) {
         k_set_window<<<1, 1, 0, st>>>(h->d_flags, 0, h->res_nodes);
-        fn<<<h->batched_grid, h->block, h->batched_smem, st>>>(a);
+        fn<<<h->batched_grid, h->block + 32, h->batched_smem, st>>>(a);
     }
     uint32_t i = 0;
     for (uint32_t lo = h->res_nodes; lo < h->V; lo += h->shard_nodes, ++i) {
@@ -722,7 +770,7 @@ static void enqueue_tiered_updates(gz_handle* h, cudaStream_t st) {
         // node lo lives at the slot's start: base = slot - lo * node_bytes, as an integer
         a.s.base = reinterpret_cast<uint8_t*>(reinterpret_cast<uintptr_t>(h->d_slot[b]) -
                                               (uintptr_t)lo * h->node_bytes);
-        fn<<<h->batched_grid, h->block, h->batched_smem, st>>>(a);
+        fn<<<h->batched_grid, h->block + 32, h->batched_smem, st>>>(a);
         cudaEventRecord(h->ev_tdone[b], st);
         cudaStreamWaitEvent(h->tier_out, h->ev_tdone[b], 0);
         cudaMemcpyAsync(host, h->d_slot[b], bytes, cudaMemcpyDeviceToHost, h->tier_out);
@@ -777,7 +825,8 @@ static void enqueue_batched(gz_handle* h, const uint32_t* d_u, const uint32_t* d
     if (ev1) record(ev1);
     const bool wide = (uint64_t)h->V * h->V > (1ull << 32);
     if (!h->tiered) {
-        batched_fn(h->delta_mode, wide)<<<h->batched_grid, h->block, h->batched_smem, st>>>(batched_args(h));
+        batched_fn(h->delta_mode, wide)<<<h->batched_grid, h->block + 32, h->batched_smem, st>>>(
+            batched_args(h));
     } else {
         enqueue_tiered_updates(h, st);
     }
@@ -995,8 +1044,7 @@ namespace noalloc {
 constexpr uint32_t kMaxV = GZ_NOALLOC_MAX_V;
 constexpr uint64_t kMaxUpdates = GZ_NOALLOC_MAX_UPDATES;
 constexpr uint32_t kMaxCols = 7u * 30u;  // K(2^17) = 30 CubeSketches per node
-// layout in 32-bit words; every region starts on a 256-byte boundary (the
-// records are read with 16-byte cp.async copies)
+// layout in 32-bit words; every region starts on a 256-byte boundary
 constexpr size_t up64(size_t w) { return (w + 63) / 64 * 64; }
 constexpr size_t kKeys = 0;                                         // 3 x kMaxCols u64
 constexpr size_t kStats = up64(kKeys + 2 * 3 * kMaxCols);           // 2 u64
@@ -1038,7 +1086,10 @@ __global__ void k_keys(uint64_t seed, uint32_t ncol, uint64_t* a, uint64_t* b, u
     c[col] = out[2];
 }
 
-__global__ void k_status(const uint32_t* flags, uint32_t* status) { *status = flags[0] ? 1u : 0u; }
+// 1: the batch was discarded; 2: a bounded wait of the update kernel ran out
+__global__ void k_status(const uint32_t* flags, uint32_t* status) {
+    *status = flags[0] ? 1u : (flags[3] ? 2u : 0u);
+}
 
 // Once per device, with that device current: the device address of the
 // scratch array (its name is only a host-side stand-in in host code).
@@ -1125,13 +1176,13 @@ extern "C" gz_status gz_sketch_update_noalloc(void* sketch, uint32_t V, uint64_t
         a.Rs = Rs;
         a.tile = tile;
         a.small_seg = 4;
-        const size_t smem = (size_t)Rs * block * 12 + (size_t)tile * (12 + (wide ? 32 : 16));
+        const size_t smem = (size_t)Rs * block * 12 + (size_t)tile * kRing * (wide ? 16 : 8);
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_fn(1, wide), (int)block, smem) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_fn(1, wide), (int)block + 32, smem) !=
                 cudaSuccess ||
             per_sm < 1)
             return GZ_ECUDA;
-        batched_fn(1, wide)<<<per_sm * sms, block, smem, st>>>(a);
+        batched_fn(1, wide)<<<per_sm * sms, block + 32, smem, st>>>(a);
     }
     if (status) k_status<<<1, 1, 0, st>>>(flags, status);
     return cudaGetLastError() == cudaSuccess ? GZ_OK : GZ_ECUDA;
