@@ -291,9 +291,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 //               u64 (+0), gamma' (+64).  A warp's 32 lanes hit 32 distinct
 //               banks whatever rows they update, and the words of a column
 //               update share one address register.
-//   ring        [kRing][tile] staged records (kWide: uint4 {idx_lo, idx_hi,
-//               fold_pre, 0}; else uint2 {idx, fold_pre}), record r of the
-//               tile at entry r.
+//   ring        [kRing] slots of one staged tile: uint2 {idx_lo, fold_pre}
+//               per record, record r of the tile at entry r; kWide: then u32
+//               idx_hi per record (12 bytes a record in all).  A consumer
+//               reads four records' words with 16-byte loads.
 template <int kMode, bool kWide, bool kWin>
 __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
     extern __shared__ __align__(16) uint64_t smem[];
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
     if (p.flags[0]) return;
     const uint32_t CP = blockDim.x - 32, c = threadIdx.x;
     const uint32_t Rs = p.Rs, R = p.R, RC = Rs * CP, T = p.tile;
-    constexpr uint32_t kStageWords = kWide ? 4u : 2u;
+    constexpr uint32_t kStageWords = kWide ? 3u : 2u;
     uint32_t* sw = reinterpret_cast<uint32_t*>(smem);  // delta blocks, 3*RC words
     uint32_t* ring = sw + 3 * RC;  // 16-byte aligned: RC is a multiple of 32, T of 4
     uint32_t* timeout = const_cast<uint32_t*>(p.flags) + 3;
@@ -377,12 +378,8 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                     if (i < hi) {
                         while (xend <= i) xend = p.offsets[++x + 1];
                         const uint64_t idx = edge_index(x, r[q], p.V);
-                        if (kWide) {
-                            reinterpret_cast<uint4*>(slot)[i - tile_lo] =
-                                make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), fold_pre(idx), 0u);
-                        } else {
-                            reinterpret_cast<uint2*>(slot)[i - tile_lo] = make_uint2((uint32_t)idx, fold_pre(idx));
-                        }
+                        reinterpret_cast<uint2*>(slot)[i - tile_lo] = make_uint2((uint32_t)idx, fold_pre(idx));
+                        if (kWide) slot[2 * T + i - tile_lo] = (uint32_t)(idx >> 32);
                     }
                 }
             }
@@ -424,23 +421,15 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
             const uint32_t nseg = seg_end - pos;
             if (nseg > 0 && active) {
                 const uint32_t sb = pos - tile_lo;  // the segment's first ring entry
-                const uint4* stage4 = reinterpret_cast<const uint4*>(slot) + sb;
                 const uint2* stage2 = reinterpret_cast<const uint2*>(slot) + sb;
+                const uint32_t* stageh = slot + 2 * T + sb;  // kWide: idx_hi
                 if (nseg < p.small_seg) {
                     // short segment: straight to global memory
                     const uint64_t ka = p.keys.a[c], kb = p.keys.b[c];
                     for (uint32_t i = 0; i < nseg; ++i) {
-                        uint64_t idx;
-                        uint32_t fp;
-                        if (kWide) {
-                            const uint4 q = stage4[i];
-                            idx = (uint64_t)q.y << 32 | q.x;
-                            fp = q.z;
-                        } else {
-                            const uint2 q = stage2[i];
-                            idx = q.x;
-                            fp = q.y;
-                        }
+                        const uint2 q = stage2[i];
+                        const uint64_t idx = kWide ? ((uint64_t)stageh[i] << 32 | q.x) : q.x;
+                        const uint32_t fp = q.y;
                         const uint32_t d = exact_depth(depth_word(ka, kb, idx), R);
                         atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, d, j)),
                                   (unsigned long long)idx);
@@ -471,18 +460,8 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                     };
                     // one staged record
                     auto one = [&](uint32_t i) {
-                        uint32_t xlo, xhi, fp;
-                        if (kWide) {
-                            const uint4 q = stage4[i];
-                            xlo = q.x;
-                            xhi = q.y;
-                            fp = q.z;
-                        } else {
-                            const uint2 q = stage2[i];
-                            xlo = q.x;
-                            xhi = 0;
-                            fp = q.y;
-                        }
+                        const uint2 q = stage2[i];
+                        const uint32_t xlo = q.x, xhi = kWide ? stageh[i] : 0u, fp = q.y;
                         const uint32_t d = __clz(depth_hi<kWide>(key, xlo, xhi));
                         const uint32_t g = checksum_w(key, fp);
                         if (d < Rs) {
@@ -493,32 +472,32 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                         }
                     };
                     uint32_t i = 0;
-                    // narrow records: pairs are read as one 16-byte word, so
-                    // start the loop on an even ring entry
-                    if (!kWide && (sb & 1u)) one(i++);
+                    // the loop reads 16-byte words (two records' uint2, four
+                    // records' idx_hi), so it starts on an aligned ring entry
+                    constexpr uint32_t kAlign = kWide ? 4u : 2u;
+                    const uint32_t peel = min(nseg, (kAlign - (sb & (kAlign - 1))) & (kAlign - 1));
+                    for (; i < peel; ++i) one(i);
                     // four records at a time in straight-line code, so the
                     // four hash chains interleave; one rare branch for deep rows
                     for (; i + 4 <= nseg; i += 4) {
                         uint32_t xlo[4], xhi[4], fp[4];
+                        const uint4 q0 = *reinterpret_cast<const uint4*>(stage2 + i);
+                        const uint4 q1 = *reinterpret_cast<const uint4*>(stage2 + i + 2);
+                        xlo[0] = q0.x;
+                        fp[0] = q0.y;
+                        xlo[1] = q0.z;
+                        fp[1] = q0.w;
+                        xlo[2] = q1.x;
+                        fp[2] = q1.y;
+                        xlo[3] = q1.z;
+                        fp[3] = q1.w;
                         if (kWide) {
-#pragma unroll
-                            for (int r = 0; r < 4; ++r) {
-                                const uint4 q = stage4[i + r];
-                                xlo[r] = q.x;
-                                xhi[r] = q.y;
-                                fp[r] = q.z;
-                            }
+                            const uint4 h = *reinterpret_cast<const uint4*>(stageh + i);
+                            xhi[0] = h.x;
+                            xhi[1] = h.y;
+                            xhi[2] = h.z;
+                            xhi[3] = h.w;
                         } else {
-                            const uint4 q0 = *reinterpret_cast<const uint4*>(stage2 + i);
-                            const uint4 q1 = *reinterpret_cast<const uint4*>(stage2 + i + 2);
-                            xlo[0] = q0.x;
-                            fp[0] = q0.y;
-                            xlo[1] = q0.z;
-                            fp[1] = q0.w;
-                            xlo[2] = q1.x;
-                            fp[2] = q1.y;
-                            xlo[3] = q1.z;
-                            fp[3] = q1.w;
 #pragma unroll
                             for (int r = 0; r < 4; ++r) xhi[r] = 0;
                         }
@@ -699,7 +678,7 @@ gz_status ingest_setup(gz_handle* h) {
     h->small_seg = h->cfg.small_segment ? h->cfg.small_segment : 4;
     const bool wide = (uint64_t)h->V * h->V > (1ull << 32);
     if (h->tile % 4 != 0) return set_error(h, GZ_EINVAL, "tile_records must be a multiple of 4");
-    h->batched_smem = (size_t)rs * h->block * 12 + (size_t)h->tile * kRing * (wide ? 16 : 8);
+    h->batched_smem = (size_t)rs * h->block * 12 + (size_t)h->tile * kRing * (wide ? 12 : 8);
     if (h->cfg.smem_mode > 2) return set_error(h, GZ_EINVAL, "smem_mode must be 0, 1 or 2");
     h->delta_mode = h->cfg.smem_mode == 2 ? 0u : 1u;  // kernel mode: 1 shared atomics, 0 load-xor-store
     const void* fn = (const void*)batched_fn(h->delta_mode, wide);
@@ -1176,7 +1155,7 @@ extern "C" gz_status gz_sketch_update_noalloc(void* sketch, uint32_t V, uint64_t
         a.Rs = Rs;
         a.tile = tile;
         a.small_seg = 4;
-        const size_t smem = (size_t)Rs * block * 12 + (size_t)tile * kRing * (wide ? 16 : 8);
+        const size_t smem = (size_t)Rs * block * 12 + (size_t)tile * kRing * (wide ? 12 : 8);
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_fn(1, wide), (int)block + 32, smem) !=
                 cudaSuccess ||
