@@ -45,9 +45,9 @@ CHUNK_LOG2 = 24
 # dram__bytes_read.sum + dram__bytes_write.sum) of this bench's own step; valid
 # only for the kernel source it was taken with (kernel_sha) and its configuration.
 TRAFFIC = {
-    "kron17": {"sha": "a2e9e708759668e0",
+    "kron17": {"sha": "1c4a7036d029efcc",
                "cfg": {"smem_mode": 1, "tile_records": 512, "smem_rows": 12, "ctas_per_sm": 0, "chunk_log2": 26},
-               "bytes_per_launch": 10.272e9, "updates_per_launch": 66592033,
+               "bytes_per_launch": 9.667e9, "updates_per_launch": 66592033,
                "source": "profiles/k_batched_kron17_dram.md"},
 }
 
