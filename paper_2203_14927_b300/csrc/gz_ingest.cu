@@ -7,10 +7,13 @@
 // partitioned by endpoint on the device (histogram, exclusive scan, scatter: each
 // update lands in the segment of both endpoints with the other endpoint as the
 // record), and a persistent kernel walks fixed-size tiles of the partitioned
-// records.  For every node segment in its tile a CTA keeps a zeroed delta sketch
-// of the first `Rs` exact-depth rows in shared memory (one thread per CubeSketch
-// column, so no shared-memory atomics), applies the segment, then XORs the
-// touched rows into the node's sketch in global memory with red.global.xor --
+// records, staged by a producer warp per CTA.  For every node segment in its
+// tile a CTA keeps a zeroed delta sketch of the first `Rs` exact-depth rows in
+// shared memory (one thread per CubeSketch column, so no two threads share a
+// bucket; the default mode still applies each XOR with one shared-memory
+// atomic, a single-instruction read-modify-write), applies the segment, then
+// XORs the touched rows into the node's sketch in global memory with
+// red.global.xor --
 // the "apply to an empty sketch, then add" step of Section 5.1 (linearity), which
 // also lets two CTAs share one heavy node whose segment spans tiles.
 #include <cuda_runtime.h>
