@@ -389,6 +389,22 @@ def random_stream(V: int, n: int, seed: int, n_distinct: int | None = None):
     return a[pick].astype(np.uint32), b[pick].astype(np.uint32)
 
 
+def hub_stream(V: int, n: int, seed: int, hubs):
+    """n updates (about): half `random_stream` pairs (repeats toggle), half
+    with one endpoint drawn from `hubs` and the other uniform, shuffled; the
+    hubs' node segments span many record tiles."""
+    hubs = np.asarray(hubs, np.uint32)
+    u1, v1 = random_stream(V, n // 2, seed=seed, n_distinct=n // 3)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    hu = hubs[rng.integers(0, len(hubs), n - n // 2)]
+    hv = rng.integers(0, V, n - n // 2).astype(np.uint32)
+    keep = hu != hv
+    u = np.concatenate([u1, hu[keep]])
+    v = np.concatenate([v1, hv[keep]])
+    perm = rng.permutation(len(u))
+    return u[perm], v[perm]
+
+
 def net_graph(V: int, u, v):
     """Edges with an odd number of updates, as (u, v) with u < v, ascending idx."""
     u = np.asarray(u, np.uint64)

@@ -220,6 +220,34 @@ def test_full_size_kronecker_2p13_sampled_nodes():
     assert np.array_equal(labels, want)
 
 
+WIDE_HUBS = [0, 1, 2, 65536, 70000]
+
+
+def test_wide_indices_ragged_stream_sampled_nodes():
+    # V^2 > 2^32 (64-bit edge indices, the kernel's wide record path), V not a
+    # power of two, 2^18-update batches with a ragged last batch, the device
+    # and host input paths; sampled node sketches (hubs spanning many tiles,
+    # random nodes, the last node) equal the oracle's, labels the exact
+    # components of the net graph
+    V, seed = 70001, 9
+    u, v = S.hub_stream(V, 600000, seed, WIDE_HUBS)
+    eu, ev = S.net_graph(V, u, v)
+    g = gz.Graph(V, seed, chunk_log2=18)
+    g.edge_update(_dev(u[:400000]), _dev(v[:400000]))
+    g.edge_update(u[400000:], v[400000:])
+    g.sync()
+    rng = np.random.default_rng(1)
+    nodes = sorted(set(WIDE_HUBS) | set(rng.integers(0, V, 20).tolist()) | {3, V - 2})
+    for x in nodes:
+        A, G = oracle.sketch_node(V, seed, x, S.neighbors_from_edges(V, eu, ev, x))
+        a, gg = g.export_sketch(x, x + 1)
+        assert np.array_equal(a[0], A) and np.array_equal(gg[0], G), x
+    labels, ncc, st = g.connected_components()
+    assert st["fails_last"] == 0 and st["exhausted"] == 0
+    assert np.array_equal(labels, oracle.cc_edges(V, eu.astype(np.uint32), ev.astype(np.uint32)))
+    g.close()
+
+
 def test_full_size_kronecker_2p17_sampled_nodes():
     # The benchmark's main workload at full size: V = 2^17 (64-bit edge
     # indices, so the kernel's wide record path), ~4e9 updates with 10% churn

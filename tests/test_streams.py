@@ -94,3 +94,13 @@ def test_planted_stream_net_graph_stays_inside_components():
 def test_random_stream_any_v():
     u, v = S.random_stream(3, 100, seed=1)
     assert np.all(u != v) and u.max() < 3 and v.max() < 3
+
+
+def test_hub_stream_is_seeded_valid_and_hub_heavy():
+    V, hubs = 70001, [0, 1, 2, 65536, 70000]
+    u, v = S.hub_stream(V, 20000, 4, hubs)
+    u2, v2 = S.hub_stream(V, 20000, 4, hubs)
+    assert np.array_equal(u, u2) and np.array_equal(v, v2)
+    assert len(u) > 19990 and (u != v).all() and u.max() < V and v.max() < V
+    at_hub = np.isin(u, hubs) | np.isin(v, hubs)
+    assert 0.45 < at_hub.mean() < 0.55

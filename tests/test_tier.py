@@ -58,3 +58,38 @@ def test_tiered_kronecker_checkpoint_and_reset():
     g.reset()
     a, gg = g.export_sketch()
     assert not a.any() and not gg.any()
+
+
+def test_tiered_wide_indices_match_all_hbm_and_oracle():
+    # the windowed kernel on 64-bit edge indices (V^2 > 2^32): ~6,700 nodes
+    # resident, the rest in pinned host memory; sampled node sketches from
+    # both tiers equal the oracle's, labels and per-round samples equal an
+    # all-HBM handle's
+    V, seed = 70001, 9
+    hubs = [0, 1, 2, 65536, 70000]
+    u, v = S.hub_stream(V, 600000, seed, hubs)
+    eu, ev = S.net_graph(V, u, v)
+    g = gz.Graph(V, seed, chunk_log2=18, device_sketch_mb=512)
+    g.edge_update(_dev(u[:400000]), _dev(v[:400000]))
+    g.edge_update(u[400000:], v[400000:])
+    g.sync()
+    rng = np.random.default_rng(2)
+    nodes = sorted(set(hubs) | set(rng.integers(0, V, 12).tolist()))
+    for x in nodes:
+        A, G = oracle.sketch_node(V, seed, x, S.neighbors_from_edges(V, eu, ev, x))
+        a, gg = g.export_sketch(x, x + 1)
+        assert np.array_equal(a[0], A) and np.array_equal(gg[0], G), x
+    h = gz.Graph(V, seed, chunk_log2=18)
+    h.edge_update(_dev(u), _dev(v))
+    h.sync()
+    a1, g1 = g.export_sketch(6000, 7500)  # across the resident boundary
+    a2, g2 = h.export_sketch(6000, 7500)
+    assert np.array_equal(a1, a2) and np.array_equal(g1, g2)
+    g.enable_trace(True)
+    h.enable_trace(True)
+    f1, l1, s1 = g.list_spanning_forest()
+    f2, l2, s2 = h.list_spanning_forest()
+    assert np.array_equal(l1, l2) and np.array_equal(f1, f2)
+    assert np.array_equal(g.query_trace(), h.query_trace())
+    g.close()
+    h.close()
