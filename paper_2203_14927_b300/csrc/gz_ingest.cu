@@ -22,6 +22,7 @@
 #include <mutex>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "gz_handle.cuh"
@@ -399,6 +400,8 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
     uint64_t* ca = reinterpret_cast<uint64_t*>(sw + (c >> 5) * Rs * 96) + (c & 31);  // kMode 0 alpha
     ColKey key{};
     if (active) key = make_colkey(p.keys.a[c], p.keys.b[c], p.keys.c[c]);
+    // first node whose records can hold an edge index of 2^32 or more
+    const uint32_t xn = kWide ? (uint32_t)((0x100000000ull - p.V) / p.V) + 1u : 0u;
     unsigned long long n_rows = 0, n_deep = 0;
     for (uint32_t it = 0;; ++it) {
         const uint32_t b = it % kRing, ph = (it / kRing) & 1u;
@@ -439,113 +442,126 @@ __global__ void __launch_bounds__(1024) k_batched(BatchedArgs p) {
                         atomicXor(p.s.gamma(x, k, d, j), checksum_w(key, fp));
                     }
                 } else {
-                    uint32_t md = 0;  // deepest delta row this column touched
-                    // one column update staged in shared memory (d < Rs)
-                    auto put = [&](uint32_t d, uint32_t xlo, uint32_t xhi, uint32_t g) {
-                        if (kMode == 1) {
-                            uint32_t* w = cw + d * 96;
-                            atomicXor(w, xlo);
-                            if (kWide) atomicXor(w + 32, xhi);
-                            atomicXor(w + 64, g);
-                        } else {
-                            ca[d * 48] ^= ((uint64_t)xhi << 32) | xlo;
-                            cw[d * 96 + 64] ^= g;
-                        }
-                    };
-                    // a column update whose exact depth is Rs or more goes to HBM
-                    auto deep = [&](uint32_t xlo, uint32_t xhi, uint32_t g) {
-                        ++n_deep;
-                        const uint64_t idx = ((uint64_t)xhi << 32) | xlo;
-                        const uint32_t dd = exact_depth(depth_word(p.keys.a[c], p.keys.b[c], idx), R);
-                        atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, dd, j)),
-                                  (unsigned long long)idx);
-                        atomicXor(p.s.gamma(x, k, dd, j), g);
-                    };
-                    // one staged record
-                    auto one = [&](uint32_t i) {
-                        const uint2 q = stage2[i];
-                        const uint32_t xlo = q.x, xhi = kWide ? stageh[i] : 0u, fp = q.y;
-                        const uint32_t d = __clz(depth_hi<kWide>(key, xlo, xhi));
-                        const uint32_t g = checksum_w(key, fp);
-                        if (d < Rs) {
-                            put(d, xlo, xhi, g);
-                            md = max(md, d);
-                        } else {
-                            deep(xlo, xhi, g);
-                        }
-                    };
-                    uint32_t i = 0;
-                    // the loop reads 16-byte words (two records' uint2, four
-                    // records' idx_hi), so it starts on an aligned ring entry
-                    constexpr uint32_t kAlign = kWide ? 4u : 2u;
-                    const uint32_t peel = min(nseg, (kAlign - (sb & (kAlign - 1))) & (kAlign - 1));
-                    for (; i < peel; ++i) one(i);
-                    // four records at a time in straight-line code, so the
-                    // four hash chains interleave; one rare branch for deep rows
-                    for (; i + 4 <= nseg; i += 4) {
-                        uint32_t xlo[4], xhi[4], fp[4];
-                        const uint4 q0 = *reinterpret_cast<const uint4*>(stage2 + i);
-                        const uint4 q1 = *reinterpret_cast<const uint4*>(stage2 + i + 2);
-                        xlo[0] = q0.x;
-                        fp[0] = q0.y;
-                        xlo[1] = q0.z;
-                        fp[1] = q0.w;
-                        xlo[2] = q1.x;
-                        fp[2] = q1.y;
-                        xlo[3] = q1.z;
-                        fp[3] = q1.w;
-                        if (kWide) {
-                            const uint4 h = *reinterpret_cast<const uint4*>(stageh + i);
-                            xhi[0] = h.x;
-                            xhi[1] = h.y;
-                            xhi[2] = h.z;
-                            xhi[3] = h.w;
-                        } else {
-#pragma unroll
-                            for (int r = 0; r < 4; ++r) xhi[r] = 0;
-                        }
-                        uint32_t d[4], g[4];
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            d[r] = __clz(depth_hi<kWide>(key, xlo[r], xhi[r]));
-                            g[r] = checksum_w(key, fp[r]);
-                        }
-                        const uint32_t dmax = max(max(d[0], d[1]), max(d[2], d[3]));
-                        if (dmax < Rs) {
-#pragma unroll
-                            for (int r = 0; r < 4; ++r) put(d[r], xlo[r], xhi[r], g[r]);
-                            md = max(md, dmax);
-                        } else {
-#pragma unroll
+                    // node x's edge indices are at most x*V + V-1, below 2^32
+                    // when x < xn: its records then take the 32-bit code
+                    auto batched = [&](auto wide_tag) {
+                        constexpr bool W = decltype(wide_tag)::value;
+                        uint32_t md = 0;  // deepest delta row this column touched
+                        // one column update staged in shared memory (d < Rs)
+                        auto put = [&](uint32_t d, uint32_t xlo, uint32_t xhi, uint32_t g) {
+                            if (kMode == 1) {
+                                uint32_t* w = cw + d * 96;
+                                atomicXor(w, xlo);
+                                if (W) atomicXor(w + 32, xhi);
+                                atomicXor(w + 64, g);
+                            } else {
+                                ca[d * 48] ^= ((uint64_t)xhi << 32) | xlo;
+                                cw[d * 96 + 64] ^= g;
+                            }
+                        };
+                        // a column update whose exact depth is Rs or more goes to HBM
+                        auto deep = [&](uint32_t xlo, uint32_t xhi, uint32_t g) {
+                            ++n_deep;
+                            const uint64_t idx = ((uint64_t)xhi << 32) | xlo;
+                            const uint32_t dd = exact_depth(depth_word(p.keys.a[c], p.keys.b[c], idx), R);
+                            atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, dd, j)),
+                                      (unsigned long long)idx);
+                            atomicXor(p.s.gamma(x, k, dd, j), g);
+                        };
+                        // one staged record
+                        auto one = [&](uint32_t i) {
+                            const uint2 q = stage2[i];
+                            const uint32_t xlo = q.x, xhi = W ? stageh[i] : 0u, fp = q.y;
+                            const uint32_t d = __clz(depth_hi<W>(key, xlo, xhi));
+                            const uint32_t g = checksum_w(key, fp);
+                            if (d < Rs) {
+                                put(d, xlo, xhi, g);
+                                md = max(md, d);
+                            } else {
+                                deep(xlo, xhi, g);
+                            }
+                        };
+                        uint32_t i = 0;
+                        // the loop reads 16-byte words (two records' uint2, four
+                        // records' idx_hi), so it starts on an aligned ring entry
+                        constexpr uint32_t kAlign = W ? 4u : 2u;
+                        const uint32_t peel = min(nseg, (kAlign - (sb & (kAlign - 1))) & (kAlign - 1));
+                        for (; i < peel; ++i) one(i);
+                        // four records at a time in straight-line code, so the
+                        // four hash chains interleave; one rare branch for deep rows
+                        for (; i + 4 <= nseg; i += 4) {
+                            uint32_t xlo[4], xhi[4], fp[4];
+                            const uint4 q0 = *reinterpret_cast<const uint4*>(stage2 + i);
+                            const uint4 q1 = *reinterpret_cast<const uint4*>(stage2 + i + 2);
+                            xlo[0] = q0.x;
+                            fp[0] = q0.y;
+                            xlo[1] = q0.z;
+                            fp[1] = q0.w;
+                            xlo[2] = q1.x;
+                            fp[2] = q1.y;
+                            xlo[3] = q1.z;
+                            fp[3] = q1.w;
+                            if (W) {
+                                const uint4 h = *reinterpret_cast<const uint4*>(stageh + i);
+                                xhi[0] = h.x;
+                                xhi[1] = h.y;
+                                xhi[2] = h.z;
+                                xhi[3] = h.w;
+                            } else {
+    #pragma unroll
+                                for (int r = 0; r < 4; ++r) xhi[r] = 0;
+                            }
+                            uint32_t d[4], g[4];
+    #pragma unroll
                             for (int r = 0; r < 4; ++r) {
-                                if (d[r] < Rs) {
-                                    put(d[r], xlo[r], xhi[r], g[r]);
-                                    md = max(md, d[r]);
-                                } else {
-                                    deep(xlo[r], xhi[r], g[r]);
+                                d[r] = __clz(depth_hi<W>(key, xlo[r], xhi[r]));
+                                g[r] = checksum_w(key, fp[r]);
+                            }
+                            const uint32_t dmax = max(max(d[0], d[1]), max(d[2], d[3]));
+                            if (dmax < Rs) {
+    #pragma unroll
+                                for (int r = 0; r < 4; ++r) put(d[r], xlo[r], xhi[r], g[r]);
+                                md = max(md, dmax);
+                            } else {
+    #pragma unroll
+                                for (int r = 0; r < 4; ++r) {
+                                    if (d[r] < Rs) {
+                                        put(d[r], xlo[r], xhi[r], g[r]);
+                                        md = max(md, d[r]);
+                                    } else {
+                                        deep(xlo[r], xhi[r], g[r]);
+                                    }
                                 }
                             }
                         }
-                    }
-                    for (; i < nseg; ++i) one(i);
-                    // flush this column's touched rows into the node sketch
-                    for (uint32_t row = 0; row <= md; ++row) {
-                        uint32_t* w = cw + row * 96;
-                        const uint64_t a = kMode == 1 ? (((uint64_t)w[32] << 32) | w[0]) : ca[row * 48];
-                        const uint32_t g = w[64];
-                        if (a | g) {
-                            atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, row, j)),
-                                      (unsigned long long)a);
-                            atomicXor(p.s.gamma(x, k, row, j), g);
-                            if (kMode == 1) {
-                                w[0] = 0;
-                                w[32] = 0;
-                            } else {
-                                ca[row * 48] = 0;
+                        for (; i < nseg; ++i) one(i);
+                        // flush this column's touched rows into the node sketch
+                        for (uint32_t row = 0; row <= md; ++row) {
+                            uint32_t* w = cw + row * 96;
+                            // (32-bit code: the alpha-hi word was never written, so it is 0)
+                            const uint64_t a = kMode == 1 ? (W ? (((uint64_t)w[32] << 32) | w[0]) : w[0])
+                                                          : ca[row * 48];
+                            const uint32_t g = w[64];
+                            if (a | g) {
+                                atomicXor(reinterpret_cast<unsigned long long*>(p.s.alpha(x, k, row, j)),
+                                          (unsigned long long)a);
+                                atomicXor(p.s.gamma(x, k, row, j), g);
+                                if (kMode == 1) {
+                                    w[0] = 0;
+                                    if (W) w[32] = 0;
+                                } else {
+                                    ca[row * 48] = 0;
+                                }
+                                w[64] = 0;
+                                ++n_rows;
                             }
-                            w[64] = 0;
-                            ++n_rows;
                         }
+                    };
+                    if constexpr (kWide) {
+                        if (x >= xn) batched(std::true_type{});
+                        else batched(std::false_type{});
+                    } else {
+                        batched(std::false_type{});
                     }
                 }
             }
