@@ -270,6 +270,22 @@ def max_over_ranks(ms: float, dist=None, device="cpu") -> float:
     return float(t.item())
 
 
+def wide_index_fraction(u, v, V: int, torch, block: int = 1 << 26) -> float:
+    """Fraction of updates whose edge index min(u,v)*V + max(u,v) is 2^32 or
+    more: the depth hash of such an index needs the 64-bit multiply (16 integer
+    operations per column update instead of 14)."""
+    n = u.numel()
+    if V * V <= (1 << 32) or n == 0:
+        return 0.0
+    wide = 0
+    for s in range(0, n, block):
+        a = u[s:s + block].long()
+        b = v[s:s + block].long()
+        idx = torch.minimum(a, b) * V + torch.maximum(a, b)
+        wide += int((idx >= (1 << 32)).sum())
+    return wide / n
+
+
 def whole_job_rate(updates_per_rank_step: int, steps: int, world: int, ms_max: float) -> float:
     """Updates of all ranks over the slowest rank's time (weak scaling: every
     rank ingests its own graph of the same size)."""
@@ -313,6 +329,7 @@ def run_ours(args, rank: int, world: int):
     torch.cuda.synchronize()
     log(f"[bench] rank {rank}: generated {total} updates on device in {time.time() - t0:.1f}s")
     u_all, v_all = U[:total], Vv[:total]
+    f_wide = wide_index_fraction(u_all, v_all, spec.V, torch)
     int_peaks = {k: gz.int_peak(k) for k in ("imad", "lop3", "mixed")}
     log("[bench] integer ceilings (T thread-instr/s): "
         + ", ".join(f"{k} {v / 1e12:.2f}" for k, v in int_peaks.items()))
@@ -380,7 +397,6 @@ def run_ours(args, rank: int, world: int):
     upd_per_launch = prof["updates"] / launches
     sec = avg_ms / 1000.0
     s_total = spec.V * K * 84 * R
-    wide = spec.V * spec.V > (1 << 32)
     col_updates = upd_per_launch * 2 * 7 * K
     # HBM, by the bytes the batched update must move per launch: its two
     # records per update (8 B) and a read-modify-write of every exact-depth
@@ -395,10 +411,12 @@ def run_ours(args, rank: int, world: int):
            "bytes_per_launch": hbm_bytes, "touched_buckets_per_launch": rows_per_launch,
            "full_sketch_bytes_per_launch": 8.0 * upd_per_launch + 2.0 * s_total}
     hbm["frac"] = hbm["achieved"] / peak
-    # integer issue: 16 (V > 2^16) or 14 32-bit operations per column update,
+    # integer issue: 16 32-bit operations per column update of an edge index
+    # of 2^32 or more, 14 below (a fraction f_wide of the stream's updates),
     # against the measured integer ceilings of this GPU (gz_int_peak: chains of
     # multiply-add, of three-input logic, and of the two interleaved)
-    ops = col_updates * (16 if wide else 14)
+    ops_per_cu = 16.0 * f_wide + 14.0 * (1.0 - f_wide)
+    ops = col_updates * ops_per_cu
     issue_nominal = 148 * 4 * 32 * 2.032e9 / 1e12
     issue_peak = max(int_peaks.values()) / 1e12
     alu = {"bound": "alu", "achieved": ops / sec / 1e12, "peak": issue_peak, "unit": "Tops/s",
@@ -406,15 +424,17 @@ def run_ours(args, rank: int, world: int):
                           + ", ".join(f"{k} {v / 1e12:.2f}" for k, v in int_peaks.items())
                           + f" T thread-instr/s (nominal issue {issue_nominal:.2f}: 148 SMs x 4 schedulers"
                             " x 32 lanes x 2.032 GHz)",
-           "ops_per_launch": ops, "ops_per_column_update": 16 if wide else 14}
+           "ops_per_launch": ops, "ops_per_column_update": ops_per_cu,
+           "wide_index_fraction": f_wide}
     alu["frac"] = alu["achieved"] / issue_peak
-    imads = col_updates * (5 if wide else 4)
+    imad_per_cu = 5.0 * f_wide + 4.0 * (1.0 - f_wide)
+    imads = col_updates * imad_per_cu
     imad_nominal = 148 * 4 * 16 * 2.032e9 / 1e12
     imad_peak = int_peaks["imad"] / 1e12
     imad = {"bound": "alu (integer multiply-add pipe)", "achieved": imads / sec / 1e12, "peak": imad_peak,
             "unit": "T IMAD/s", "peak_source": f"measured multiply-add chains (nominal {imad_nominal:.2f}:"
                                                 " 148 SMs x 4 x 16-lane pipes x 2.032 GHz)",
-            "imad_per_column_update": 5 if wide else 4}
+            "imad_per_column_update": imad_per_cu}
     imad["frac"] = imad["achieved"] / imad_peak
     binding = max((hbm, alu, imad), key=lambda r: r["frac"])
     roofline = dict(binding)
