@@ -53,20 +53,14 @@ def lib():
         u64, u32, sz, p = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_size_t, ctypes.c_void_p
         L.gzo_splitmix64_at.restype = u64
         L.gzo_splitmix64_at.argtypes = [u64, u64]
-        L.gzo_fmix64.restype = u64
-        L.gzo_fmix64.argtypes = [u64]
-        L.gzo_fmix32.restype = u32
-        L.gzo_fmix32.argtypes = [u32]
-        L.gzo_fold.restype = u32
-        L.gzo_fold.argtypes = [u64]
         L.gzo_h1.restype = u64
         L.gzo_h1.argtypes = [u64, u64, u64]
         L.gzo_h2.restype = u32
-        L.gzo_h2.argtypes = [u64, u64]
+        L.gzo_h2.argtypes = [u64, u64, u64, u64]
         L.gzo_geometry.restype = ctypes.c_int
         L.gzo_geometry.argtypes = [u32, p, p]
         L.gzo_keys.restype = None
-        L.gzo_keys.argtypes = [u64, u32, p, p, p]
+        L.gzo_keys.argtypes = [u64, u32, p, p, p, p, p]
         L.gzo_ingest.restype = ctypes.c_int
         L.gzo_ingest.argtypes = [u32, u64, sz, p, p, p, p]
         L.gzo_sketch_node.restype = ctypes.c_int
@@ -112,35 +106,29 @@ def geometry(V: int) -> tuple[int, int]:
 
 
 def keys(seed: int, K: int):
+    """Hash keys of the 7K columns: a, b (h1) as arrays of 7K, and c, a
+    (7K, 3) array holding the h2 keys (c0, c1, c2) of each column."""
     a = np.zeros(K * COLS, np.uint64)
     b = np.zeros(K * COLS, np.uint64)
-    c = np.zeros(K * COLS, np.uint64)
-    lib().gzo_keys(seed, K, _ptr(a), _ptr(b), _ptr(c))
-    return a, b, c
+    c0 = np.zeros(K * COLS, np.uint64)
+    c1 = np.zeros(K * COLS, np.uint64)
+    c2 = np.zeros(K * COLS, np.uint64)
+    lib().gzo_keys(seed, K, _ptr(a), _ptr(b), _ptr(c0), _ptr(c1), _ptr(c2))
+    return a, b, np.stack([c0, c1, c2], axis=1)
 
 
 def splitmix64_at(seed: int, n: int) -> int:
     return int(lib().gzo_splitmix64_at(seed, n))
 
 
-def fmix64(x: int) -> int:
-    return int(lib().gzo_fmix64(x))
-
-
-def fmix32(x: int) -> int:
-    return int(lib().gzo_fmix32(x))
-
-
-def fold(x: int) -> int:
-    return int(lib().gzo_fold(x))
-
-
 def h1(a: int, b: int, x: int) -> int:
     return int(lib().gzo_h1(a, b, x))
 
 
-def h2(c: int, x: int) -> int:
-    return int(lib().gzo_h2(c, x))
+def h2(c, x: int) -> int:
+    """Checksum h2 of index x under the key triple c = (c0, c1, c2)."""
+    c0, c1, c2 = (int(t) for t in c)
+    return int(lib().gzo_h2(c0, c1, c2, x))
 
 
 def empty_sketches(V: int, nodes: int | None = None):

@@ -23,11 +23,13 @@
 #define GZB_COLS 7
 
 uint64_t gzo_h1(uint64_t a, uint64_t b, uint64_t x);
-uint32_t gzo_h2(uint64_t c, uint64_t x);
+uint32_t gzo_h2(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t x);
 int gzo_geometry(uint32_t V, uint32_t *K, uint32_t *R);
-void gzo_keys(uint64_t seed, uint32_t K, uint64_t *a, uint64_t *b, uint64_t *c);
+void gzo_keys(uint64_t seed, uint32_t K, uint64_t *a, uint64_t *b, uint64_t *c0, uint64_t *c1,
+              uint64_t *c2);
 
-/* Fig. cube_code update_sketch for every CubeSketch of one node sketch */
+/* Fig. cube_code update_sketch for every CubeSketch of one node sketch; kc
+ * holds the three h2 keys of column col at kc[3col .. 3col+2] */
 static void node_apply(uint32_t K, uint32_t R, const uint64_t *ka, const uint64_t *kb,
                        const uint64_t *kc, uint64_t *alpha, uint32_t *gamma, uint64_t idx)
 {
@@ -35,7 +37,7 @@ static void node_apply(uint32_t K, uint32_t R, const uint64_t *ka, const uint64_
         for (uint32_t j = 0; j < GZB_COLS; j++) {
             size_t col = (size_t)k * GZB_COLS + j;
             uint64_t h = gzo_h1(ka[col], kb[col], idx);
-            uint32_t g = gzo_h2(kc[col], idx);
+            uint32_t g = gzo_h2(kc[3 * col], kc[3 * col + 1], kc[3 * col + 2], idx);
             uint64_t *A = alpha + col * R;
             uint32_t *G = gamma + col * R;
             uint32_t row = 0;
@@ -60,19 +62,25 @@ int gzb_ingest_batched(uint32_t V, uint64_t seed, size_t n, const uint32_t *u, c
         if (u[i] == v[i] || u[i] >= V || v[i] >= V) return -1;
     if (threads <= 0) threads = omp_get_max_threads();
     const size_t ncol = (size_t)K * GZB_COLS, nb = ncol * R, span = node_hi - node_lo;
-    uint64_t *ka = malloc(ncol * 8), *kb = malloc(ncol * 8), *kc = malloc(ncol * 8);
+    uint64_t *ka = malloc(ncol * 8), *kb = malloc(ncol * 8), *kc = malloc(3 * ncol * 8);
+    uint64_t *c0 = malloc(ncol * 8), *c1 = malloc(ncol * 8), *c2 = malloc(ncol * 8);
     uint32_t *hist = calloc((size_t)threads * span, 4);
     uint32_t *off = malloc((span + 1) * 4);
     uint64_t *rec = malloc(2 * chunk * 8);
     int rc = 0;
-    if (!ka || !kb || !kc || !hist || !off || !rec) {
+    if (!ka || !kb || !kc || !c0 || !c1 || !c2 || !hist || !off || !rec) {
         rc = -2;
         goto out;
     }
-    gzo_keys(seed, K, ka, kb, kc);
-    for (size_t c0 = 0; c0 < n; c0 += chunk) {
-        const size_t m = n - c0 < chunk ? n - c0 : chunk;
-        const uint32_t *cu = u + c0, *cv = v + c0;
+    gzo_keys(seed, K, ka, kb, c0, c1, c2);
+    for (size_t col = 0; col < ncol; col++) {
+        kc[3 * col] = c0[col];
+        kc[3 * col + 1] = c1[col];
+        kc[3 * col + 2] = c2[col];
+    }
+    for (size_t base = 0; base < n; base += chunk) {
+        const size_t m = n - base < chunk ? n - base : chunk;
+        const uint32_t *cu = u + base, *cv = v + base;
         memset(hist, 0, (size_t)threads * span * 4);
         /* per-thread histograms of both endpoints over equal slices */
 #pragma omp parallel num_threads(threads)
@@ -122,6 +130,9 @@ out:
     free(ka);
     free(kb);
     free(kc);
+    free(c0);
+    free(c1);
+    free(c2);
     free(hist);
     free(off);
     free(rec);

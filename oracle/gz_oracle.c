@@ -21,17 +21,22 @@
  *              (Section 5, total size ~280 V log^2 V bytes; Table tab:size).
  *   index      idx(u,v) = min(u,v)*V + max(u,v)  (a position of the
  *              characteristic vector, Section 2.2); never 0.
- *   keys       per (k,j): a = SM(seed, 3(7k+j)) | 1, b = SM(seed, 3(7k+j)+1),
- *              c = SM(seed, 3(7k+j)+2), SM(s,n) = the n-th output (n >= 0) of
- *              SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) started at s.
+ *   keys       per (k,j), col = 7k+j: a = SM(seed, 5col) | 1,
+ *              b = SM(seed, 5col+1), c0 = SM(seed, 5col+2),
+ *              c1 = SM(seed, 5col+3), c2 = SM(seed, 5col+4), where SM(s,n) is
+ *              the n-th output (n >= 0) of SplitMix64 (Steele, Lea & Flood,
+ *              OOPSLA 2014) started at s.
  *   h1         h1(x) = bitreverse64((a*x + b) mod 2^64): the multiply-add-shift
  *              family of Dietzfelbinger (STACS 1996); bit i of h1 is bit 63-i
  *              of the product, so "h1(x) = 0 mod 2^i" tests the TOP i bits.
  *              Bit order of col_hash in Fig. cube_code: bit 0 first.
- *   h2         h2(x) = fmix32(fold(x) XOR lo32(c)), fmix32 being the 32-bit
- *              finalizer of MurmurHash3 (Appleby, 2011) and
- *              fold(x) = lo32(x) XOR lo32(hi32(x) * 0x9E3779B9), the identity
- *              for x < 2^32.
+ *   h2         h2(x) = ((c0*x0 + c1*x1 + c2) mod 2^64) >> 32 with x0, x1 the
+ *              low and high 32-bit words of x: multiply-add-shift over a
+ *              vector of two 32-bit words (Dietzfelbinger, STACS 1996; the
+ *              vector form in Thorup, "High Speed Hashing for Integers and
+ *              Strings", 2015).  With 32-bit words, 32 output bits and 64-bit
+ *              arithmetic (64 >= 32 + 32 - 1) the family is strongly
+ *              universal, i.e. 2-wise independent, as Section 3.2 asks of h2.
  *   rows       the update loop of Fig. cube_code also stops at row R.
  *   query      Fig. cube_code's scan (columns ascending, rows ascending); a
  *              bucket is taken when gamma == h2(alpha) AND alpha decodes to
@@ -61,35 +66,6 @@ uint64_t gzo_splitmix64_at(uint64_t s, uint64_t n)
     return z ^ (z >> 31);
 }
 
-/* MurmurHash3's 64-bit finalizer (Appleby 2011). */
-uint64_t gzo_fmix64(uint64_t x)
-{
-    x ^= x >> 33;
-    x *= 0xFF51AFD7ED558CCDULL;
-    x ^= x >> 33;
-    x *= 0xC4CEB9FE1A85EC53ULL;
-    x ^= x >> 33;
-    return x;
-}
-
-/* MurmurHash3's 32-bit finalizer (Appleby 2011). */
-uint32_t gzo_fmix32(uint32_t h)
-{
-    h ^= h >> 16;
-    h *= 0x85EBCA6Bu;
-    h ^= h >> 13;
-    h *= 0xC2B2AE35u;
-    h ^= h >> 16;
-    return h;
-}
-
-/* 32-bit fold of an edge index: lo32(x) ^ lo32(hi32(x) * 0x9E3779B9). */
-uint32_t gzo_fold(uint64_t x)
-{
-    uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
-    return lo ^ (uint32_t)(hi * 0x9E3779B9u);
-}
-
 static uint64_t bitreverse64(uint64_t x)
 {
     uint64_t r = 0;
@@ -106,10 +82,12 @@ uint64_t gzo_h1(uint64_t a, uint64_t b, uint64_t x)
     return bitreverse64(a * x + b);
 }
 
-/* checksum of Fig. cube_code: h2(x) = fmix32(fold(x) ^ lo32(c)). */
-uint32_t gzo_h2(uint64_t c, uint64_t x)
+/* checksum of Fig. cube_code: h2(x) = ((c0*x0 + c1*x1 + c2) mod 2^64) >> 32,
+ * x0 = lo32(x), x1 = hi32(x). */
+uint32_t gzo_h2(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t x)
 {
-    return gzo_fmix32(gzo_fold(x) ^ (uint32_t)c);
+    uint64_t x0 = x & 0xFFFFFFFFu, x1 = x >> 32;
+    return (uint32_t)((c0 * x0 + c1 * x1 + c2) >> 32);
 }
 
 /* ---------------------------------------------------------------- geometry */
@@ -130,22 +108,26 @@ int gzo_geometry(uint32_t V, uint32_t *K, uint32_t *R)
     return 0;
 }
 
-/* Keys of all K*7 columns, one triple (a,b,c) per column (k,j). */
-void gzo_keys(uint64_t seed, uint32_t K, uint64_t *a, uint64_t *b, uint64_t *c)
+/* Keys of all K*7 columns (k,j), col = 7k+j: five consecutive SplitMix64
+ * outputs per column, a (forced odd) and b for h1, c0, c1, c2 for h2. */
+void gzo_keys(uint64_t seed, uint32_t K, uint64_t *a, uint64_t *b,
+              uint64_t *c0, uint64_t *c1, uint64_t *c2)
 {
     for (uint32_t k = 0; k < K; k++) {
         for (uint32_t j = 0; j < GZO_COLS; j++) {
             uint64_t col = (uint64_t)k * GZO_COLS + j;
-            a[col] = gzo_splitmix64_at(seed, 3 * col) | 1u;
-            b[col] = gzo_splitmix64_at(seed, 3 * col + 1);
-            c[col] = gzo_splitmix64_at(seed, 3 * col + 2);
+            a[col] = gzo_splitmix64_at(seed, 5 * col) | 1u;
+            b[col] = gzo_splitmix64_at(seed, 5 * col + 1);
+            c0[col] = gzo_splitmix64_at(seed, 5 * col + 2);
+            c1[col] = gzo_splitmix64_at(seed, 5 * col + 3);
+            c2[col] = gzo_splitmix64_at(seed, 5 * col + 4);
         }
     }
 }
 
 typedef struct {
     uint32_t V, K, R;
-    uint64_t *a, *b, *c;
+    uint64_t *a, *b, *c0, *c1, *c2;
 } gzo_ctx;
 
 static int ctx_open(gzo_ctx *x, uint32_t V, uint64_t seed)
@@ -155,15 +137,17 @@ static int ctx_open(gzo_ctx *x, uint32_t V, uint64_t seed)
     size_t ncol = (size_t)x->K * GZO_COLS;
     x->a = malloc(ncol * 8);
     x->b = malloc(ncol * 8);
-    x->c = malloc(ncol * 8);
-    if (!x->a || !x->b || !x->c) return -2;
-    gzo_keys(seed, x->K, x->a, x->b, x->c);
+    x->c0 = malloc(ncol * 8);
+    x->c1 = malloc(ncol * 8);
+    x->c2 = malloc(ncol * 8);
+    if (!x->a || !x->b || !x->c0 || !x->c1 || !x->c2) return -2;
+    gzo_keys(seed, x->K, x->a, x->b, x->c0, x->c1, x->c2);
     return 0;
 }
 
 static void ctx_close(gzo_ctx *x)
 {
-    free(x->a); free(x->b); free(x->c);
+    free(x->a); free(x->b); free(x->c0); free(x->c1); free(x->c2);
 }
 
 /* words of one node sketch: K*7*R buckets */
@@ -183,7 +167,7 @@ static void cubesketch_update(const gzo_ctx *x, uint32_t k,
     for (uint32_t j = 0; j < GZO_COLS; j++) {
         size_t col = (size_t)k * GZO_COLS + j;
         uint64_t col_hash = gzo_h1(x->a[col], x->b[col], idx);
-        uint32_t checksum = gzo_h2(x->c[col], idx);
+        uint32_t checksum = gzo_h2(x->c0[col], x->c1[col], x->c2[col], idx);
         uint64_t *A = alpha_k + (size_t)j * x->R;
         uint32_t *G = gamma_k + (size_t)j * x->R;
         uint32_t row = 0;
@@ -273,7 +257,7 @@ static int64_t cubesketch_query(const gzo_ctx *x, uint32_t k,
             uint32_t gamma = G[(size_t)j * x->R + row];
             if (alpha == 0 && gamma == 0) continue;
             nonzero = 1;
-            if (gamma != gzo_h2(x->c[col], alpha)) continue;
+            if (gamma != gzo_h2(x->c0[col], x->c1[col], x->c2[col], alpha)) continue;
             if (alpha >= VV) continue;
             uint64_t uu = alpha / x->V, vv = alpha % x->V;
             if (uu >= vv) continue;
@@ -303,7 +287,7 @@ int64_t gzo_query_vector(uint32_t V, uint64_t seed, uint32_t k,
             uint32_t gamma = G[(size_t)j * x.R + row];
             if (alpha == 0 && gamma == 0) continue;
             nonzero = 1;
-            if (gamma != gzo_h2(x.c[col], alpha)) continue;
+            if (gamma != gzo_h2(x.c0[col], x.c1[col], x.c2[col], alpha)) continue;
             if (alpha >= VV || alpha / V >= alpha % V) continue;
             out = (int64_t)alpha;
             break;

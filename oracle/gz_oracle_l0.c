@@ -10,8 +10,9 @@
  *   vector     positions 1..n (0 is never used), n >= 2; deltas are +-1.
  *   geometry   7 columns (delta = 1/100, as for the node sketches) and
  *              R = ceil(log2 n) rows, the depth cap of both samplers.
- *   keys       column j: a = SM(seed, 3j) | 1, b = SM(seed, 3j+1),
- *              c = SM(seed, 3j+2) (SplitMix64, as for the node sketches).
+ *   keys       column j: a = SM(seed, 5j) | 1, b = SM(seed, 5j+1),
+ *              c0, c1, c2 = SM(seed, 5j+2), SM(seed, 5j+3), SM(seed, 5j+4)
+ *              (SplitMix64, the node sketches' schedule for column j).
  *   membership both samplers put x into rows 0..d of column j with
  *              d = min(clz64(a*x + b), R-1): Fig. agm_code's
  *              "col_hash[row-1] == 0" loop with the bit order of
@@ -20,13 +21,13 @@
  *   standard   bucket (a, b, c): a += x*delta and b += delta in two's
  *              complement 64-bit arithmetic, c += delta * r_j^x (mod p) with
  *              p = 2^61 - 1 (a Mersenne prime above every n used) and
- *              r_j = 1 + (c mod (p - 1)).  Query (Fig. agm_code): the first
+ *              r_j = 1 + (c0 mod (p - 1)).  Query (Fig. agm_code): the first
  *              bucket, columns then rows ascending, with b != 0, b | a,
  *              1 <= a/b <= n and c == (b mod p) * r_j^(a/b) (mod p) yields
  *              (a/b, b); all buckets zero -> EMPTY, else FAIL.
  *   CubeSketch bucket (alpha u64, gamma u32): alpha ^= x, gamma ^= h2(x) with
- *              the node sketches' h2 (fmix32 over a 32-bit fold); a delta of
- *              -1 is the same toggle.
+ *              the node sketches' h2 (multiply-add-shift over the two 32-bit
+ *              words of x, keys c0, c1, c2); a delta of -1 is the same toggle.
  * Layout of one sketch: standard a[7][R], b[7][R], c[7][R] (u64 each);
  * CubeSketch alpha[7][R] (u64) then gamma[7][R] (u32).
  */
@@ -37,7 +38,7 @@
 #define P61 ((((uint64_t)1) << 61) - 1)
 
 uint64_t gzo_splitmix64_at(uint64_t s, uint64_t n);
-uint32_t gzo_h2(uint64_t c, uint64_t x);
+uint32_t gzo_h2(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t x);
 
 /* rows of a length-n vector sketch: ceil(log2 n), at least 1 */
 uint32_t gzo_l0_rows(uint64_t n)
@@ -97,14 +98,16 @@ int gzo_l0_update(int kind, uint64_t n, uint64_t seed, size_t m, const uint64_t 
     for (size_t i = 0; i < m; i++) {
         const int64_t dl = delta ? delta[i] : 1;
         for (uint32_t j = 0; j < L0_COLS; j++) {
-            uint64_t ka = gzo_splitmix64_at(seed, 3 * j) | 1u;
-            uint64_t kb = gzo_splitmix64_at(seed, 3 * j + 1);
-            uint64_t kc = gzo_splitmix64_at(seed, 3 * j + 2);
+            uint64_t ka = gzo_splitmix64_at(seed, 5 * j) | 1u;
+            uint64_t kb = gzo_splitmix64_at(seed, 5 * j + 1);
+            uint64_t kc0 = gzo_splitmix64_at(seed, 5 * j + 2);
+            uint64_t kc1 = gzo_splitmix64_at(seed, 5 * j + 3);
+            uint64_t kc2 = gzo_splitmix64_at(seed, 5 * j + 4);
             uint32_t d = l0_depth(ka, kb, x[i], R);
             if (kind == 0) {
                 uint64_t *A = (uint64_t *)buckets + (size_t)j * R;
                 uint32_t *G = (uint32_t *)((uint64_t *)buckets + nb) + (size_t)j * R;
-                uint32_t g = gzo_h2(kc, x[i]);
+                uint32_t g = gzo_h2(kc0, kc1, kc2, x[i]);
                 for (uint32_t row = 0; row <= d; row++) {
                     A[row] ^= x[i];
                     G[row] ^= g;
@@ -113,7 +116,7 @@ int gzo_l0_update(int kind, uint64_t n, uint64_t seed, size_t m, const uint64_t 
                 uint64_t *A = (uint64_t *)buckets + (size_t)j * R;
                 uint64_t *B = A + nb;
                 uint64_t *C = B + nb;
-                uint64_t chk = gzo_powmod61(std_root(kc), x[i]);
+                uint64_t chk = gzo_powmod61(std_root(kc0), x[i]);
                 uint64_t add = dl > 0 ? chk : (chk ? P61 - chk : 0);
                 for (uint32_t row = 0; row <= d; row++) {
                     A[row] += x[i] * (uint64_t)dl;
@@ -135,14 +138,16 @@ int64_t gzo_l0_query(int kind, uint64_t n, uint64_t seed, const void *buckets, i
     const size_t nb = (size_t)L0_COLS * R;
     int nonzero = 0;
     for (uint32_t j = 0; j < L0_COLS; j++) {
-        uint64_t kc = gzo_splitmix64_at(seed, 3 * j + 2);
+        uint64_t kc0 = gzo_splitmix64_at(seed, 5 * j + 2);
+        uint64_t kc1 = gzo_splitmix64_at(seed, 5 * j + 3);
+        uint64_t kc2 = gzo_splitmix64_at(seed, 5 * j + 4);
         for (uint32_t row = 0; row < R; row++) {
             if (kind == 0) {
                 uint64_t alpha = ((const uint64_t *)buckets)[(size_t)j * R + row];
                 uint32_t gamma = ((const uint32_t *)((const uint64_t *)buckets + nb))[(size_t)j * R + row];
                 if (alpha == 0 && gamma == 0) continue;
                 nonzero = 1;
-                if (alpha < 1 || alpha > n || gamma != gzo_h2(kc, alpha)) continue;
+                if (alpha < 1 || alpha > n || gamma != gzo_h2(kc0, kc1, kc2, alpha)) continue;
                 if (value) *value = 1;
                 return (int64_t)alpha;
             } else {
@@ -156,7 +161,7 @@ int64_t gzo_l0_query(int kind, uint64_t n, uint64_t seed, const void *buckets, i
                 if (v < 1 || (uint64_t)v > n) continue;
                 uint64_t bm = b > 0 ? (uint64_t)b % P61 : P61 - ((uint64_t)(-b) % P61);
                 if (bm == P61) bm = 0;
-                if (c != gzo_mulmod61(bm, gzo_powmod61(std_root(kc), (uint64_t)v))) continue;
+                if (c != gzo_mulmod61(bm, gzo_powmod61(std_root(kc0), (uint64_t)v))) continue;
                 if (value) *value = b;
                 return v;
             }

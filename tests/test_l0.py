@@ -16,9 +16,10 @@ MASK = (1 << 64) - 1
 
 
 def _keys(seed):
-    a = [oracle.splitmix64_at(seed, 3 * j) | 1 for j in range(7)]
-    b = [oracle.splitmix64_at(seed, 3 * j + 1) for j in range(7)]
-    c = [oracle.splitmix64_at(seed, 3 * j + 2) for j in range(7)]
+    # column j: a, b (depth hash) and the h2 key triple c0, c1, c2
+    a = [oracle.splitmix64_at(seed, 5 * j) | 1 for j in range(7)]
+    b = [oracle.splitmix64_at(seed, 5 * j + 1) for j in range(7)]
+    c = [tuple(oracle.splitmix64_at(seed, 5 * j + w) for w in (2, 3, 4)) for j in range(7)]
     return a, b, c
 
 
@@ -59,7 +60,7 @@ def test_standard_buckets_equal_their_definition(n):
     A, B, C = got[: 7 * R], got[7 * R: 14 * R], got[14 * R:]
     ka, kb, kc = _keys(seed)
     for j in range(7):
-        r = 1 + kc[j] % (P - 1)
+        r = 1 + kc[j][0] % (P - 1)
         want_a, want_b, want_c = [0] * R, [0] * R, [0] * R
         for xi, di in zip(x.tolist(), dl.tolist()):
             d = _depth(ka[j], kb[j], xi, R)

@@ -2,10 +2,12 @@
 
 Each test checks the oracle against something other than itself: values the
 paper prints (Table tab:size, the "one-tenth of sketch size" buffer), the
-published SplitMix64 outputs, the finalizers' invertibility, the set definition of a bucket (Eq. 1-2) against
-the update loop (Fig. cube_code), linearity (Definition def:l0), Lemma
-goodcheck, the membership law behind Lemma goodset, and brute-force connected
-components checked in turn against scipy's graph routine.
+published SplitMix64 outputs, closed forms and pairwise independence of the
+checksum h2, the scan order of Fig. cube_code's query on hand-built sketches,
+the set definition of a bucket (Eq. 1-2) against the update loop (Fig.
+cube_code), linearity (Definition def:l0), Lemma goodcheck, the membership law
+behind Lemma goodset, and brute-force connected components checked in turn
+against scipy's graph routine.
 """
 import itertools
 import os
@@ -43,49 +45,53 @@ def test_splitmix64_published_outputs():
     assert got == want
 
 
-def test_fmix32_is_a_bijection_with_zero_fixed_point():
-    # every step of MurmurHash3's 32-bit finalizer is invertible (xorshift and
-    # multiplication by an odd constant), and 0 maps to 0
-    assert oracle.fmix32(0) == 0
+def test_h2_special_keys_select_words_and_carry():
+    # With degenerate keys the multiply-add-shift checksum reduces to closed
+    # forms: a constant (the top word of c2), the low or the high word of the
+    # index, the parity of the high word, and a low-word sum whose carry
+    # reaches the output word.  A dropped term, a transposed key or word, a
+    # wrong shift or a lost carry fails one of these.
     rng = np.random.default_rng(5)
-    inv1 = pow(0x85EBCA6B, -1, 2**32)
-    inv2 = pow(0xC2B2AE35, -1, 2**32)
-
-    def unxs16(y):
-        return y ^ (y >> 16)
-
-    def unxs13(y):
-        return y ^ (y >> 13) ^ (y >> 26)
-
-    for x in (int(t) for t in rng.integers(0, 2**32, 3000, dtype=np.uint64)):
-        y = unxs16(oracle.fmix32(x))
-        y = (y * inv2) % 2**32
-        y = unxs13(y)
-        y = (y * inv1) % 2**32
-        y = unxs16(y)
-        assert y == x
+    xs = [1, 2, 12345, 2**32 - 1, 2**32, 2**33 + 7, 2**34 - 1, 2**63 + 5, 2**64 - 1]
+    xs += [int(t) for t in rng.integers(1, 2**63, 40, dtype=np.uint64)]
+    for x in xs:
+        x0, x1 = x & 0xFFFFFFFF, x >> 32
+        assert oracle.h2((0, 0, 0xAAAABBBB_12345678), x) == 0xAAAABBBB
+        assert oracle.h2((2**32, 0, 0), x) == x0
+        assert oracle.h2((0, 2**32, 0), x) == x1
+        assert oracle.h2((0, 2**63, 0), x) == (x1 & 1) << 31
+        assert oracle.h2((1, 1, 0), x) == (x0 + x1) >> 32  # only the carry of x0 + x1
+        assert oracle.h2((2**32 + 1, 0, 2**32 - 1), x) == (x0 + (x0 >= 1)) % 2**32
+        assert oracle.h2((0, 2**32 + 3, 0), x) == (x1 + (3 * x1 >> 32)) % 2**32
 
 
-def test_fold_is_identity_below_2_32_and_mixes_the_high_word():
-    for x in (0, 1, 12345, 2**32 - 1):
-        assert oracle.fold(x) == x
-    assert oracle.fold(2**32) == 0x9E3779B9
-    assert oracle.fold(3 * 2**32 + 5) == 5 ^ ((3 * 0x9E3779B9) % 2**32)
-    # at V = 2^17 the edges at one vertex fold together at most a few times
-    # (only where that vertex is the smaller end of one edge and the larger
-    # end of the other); the fold feeds the checksum only, so such a pair
-    # merely shares checksums -- bucket membership uses the full index
-    V = 1 << 17
-    rng = np.random.default_rng(9)
-    for x in (int(t) for t in rng.integers(0, V, 8)):
-        ys = np.setdiff1d(np.arange(V, dtype=np.uint64), [x])
-        idx = np.minimum(ys, x) * np.uint64(V) + np.maximum(ys, x)
-        f = [oracle.fold(int(i)) for i in idx[:: max(1, len(idx) // 4096)]]
-        lo = idx & np.uint64(0xFFFFFFFF)
-        hi = idx >> np.uint64(32)
-        full = lo ^ ((hi * np.uint64(0x9E3779B9)) & np.uint64(0xFFFFFFFF))
-        assert f == [int(t) for t in full[:: max(1, len(idx) // 4096)]]
-        assert len(full) - len(np.unique(full)) <= 4
+def _chi2_uniform(counts):
+    e = counts.sum() / counts.size
+    return float(((counts - e) ** 2 / e).sum())
+
+
+def test_h2_is_pairwise_independent():
+    # Section 3.2 asks for h2 from a 2-wise independent family: for any two
+    # distinct indices x, y and uniform keys, (h2(x), h2(y)) is uniform on
+    # pairs of 32-bit words.  Checked on the top three and the low three
+    # output bits of each, for pairs that differ in the low word only, by a
+    # power of two, in the high word only, or in both words (an index can
+    # reach 2^34 at V = 2^17).
+    rng = np.random.default_rng(17)
+    pairs = [(1, 2), (5, 5 + 2**16), (3, 3 + 2**31), (77, 77 + 2**32), (2**33 + 9, 9),
+             (2**31, 2**32 + 2**31), (123456789, 2**34 - 1)]
+    n = 6400
+    keys = rng.integers(0, 2**64, (n, 3), dtype=np.uint64)
+    limit = 63 + 6 * np.sqrt(2 * 63)  # chi-square, 63 degrees of freedom, far tail
+    for x, y in pairs:
+        top = np.zeros((8, 8))
+        low = np.zeros((8, 8))
+        for c in keys:
+            hx, hy = oracle.h2(c, x), oracle.h2(c, y)
+            top[hx >> 29, hy >> 29] += 1
+            low[hx & 7, hy & 7] += 1
+        assert _chi2_uniform(top) < limit, (x, y, "top bits")
+        assert _chi2_uniform(low) < limit, (x, y, "low bits")
 
 
 def test_checksum_is_not_xor_linear():
@@ -94,11 +100,12 @@ def test_checksum_is_not_xor_linear():
     rng = np.random.default_rng(11)
     a, b, c = oracle.keys(3, 1)
     hits = 0
-    for _ in range(20000):
-        x, y = (int(t) for t in rng.integers(1, 2**34, 2))
+    for t in range(20000):
+        x, y = (int(z) for z in rng.integers(1, 2**34, 2))
         if x == y:
             continue
-        hits += (oracle.h2(int(c[0]), x) ^ oracle.h2(int(c[0]), y)) == oracle.h2(int(c[0]), x ^ y)
+        ck = c[t % 7]
+        hits += (oracle.h2(ck, x) ^ oracle.h2(ck, y)) == oracle.h2(ck, x ^ y)
     assert hits == 0
 
 
@@ -182,7 +189,7 @@ def _bucket_definition(V, seed, edges):
             for j in range(7):
                 col = k * 7 + j
                 h = oracle.h1(int(a[col]), int(b[col]), e)
-                g = oracle.h2(int(c[col]), e)
+                g = oracle.h2(c[col], e)
                 for i in range(R):
                     if h % (1 << i) == 0:
                         for node in (u, v):
@@ -281,7 +288,7 @@ def test_support_one_buckets_pass_checksum_lemma_goodcheck():
                     members = [e for e in elems if depth[e] >= i]
                     if len(members) == 1:
                         assert int(A[x, k, j, i]) == members[0]
-                        assert int(G[x, k, j, i]) == oracle.h2(int(c[col]), members[0])
+                        assert int(G[x, k, j, i]) == oracle.h2(c[col], members[0])
                         checked += 1
     assert checked > 500
 
@@ -295,6 +302,73 @@ def test_query_single_element_and_empty_vector():
             assert oracle.query_vector(V, 3, k, A[u, k], G[u, k]) == _idx(V, u, w)
     A, G = oracle.empty_sketches(V, 1)
     assert oracle.query_vector(V, 3, 0, A[0, 0], G[0, 0]) == oracle.EMPTY
+
+
+def _good_bucket(V, c, u, w):
+    """(alpha, gamma) of a bucket holding only edge {u, w}: it passes the
+    checksum of its column (Lemma goodcheck, support one)."""
+    e = _idx(V, u, w)
+    return e, oracle.h2(c, e)
+
+
+def _scan_fixture(V, seed, k, placed):
+    """One CubeSketch (layout [j][row]) holding the good buckets `placed`
+    {(j, row): (u, w)} and zeros elsewhere."""
+    K, R = oracle.geometry(V)
+    a, b, c = oracle.keys(seed, K)
+    A = np.zeros((7, R), np.uint64)
+    G = np.zeros((7, R), np.uint32)
+    for (j, row), (u, w) in placed.items():
+        A[j, row], G[j, row] = _good_bucket(V, c[k * 7 + j], u, w)
+    return A, G
+
+
+def test_query_scan_order_is_columns_then_rows_ascending():
+    # Fig. cube_code's query loops over columns, and within a column over
+    # its buckets from row 0 up; the first good bucket wins.  A row-major
+    # scan, a deepest-row-first scan or a last-match scan picks another edge.
+    V, seed = 1000, 12
+    K, R = oracle.geometry(V)
+    cases = [
+        ({(0, 9): (1, 2), (1, 0): (3, 4)}, (1, 2)),            # column 0 before column 1
+        ({(2, 1): (5, 6), (2, 6): (7, 8), (4, 0): (9, 10)}, (5, 6)),  # row 1 before row 6
+        ({(3, R - 1): (11, 12), (3, 2): (13, 14)}, (13, 14)),  # the deepest row last
+        ({(6, 0): (15, 16)}, (15, 16)),
+    ]
+    for k in (0, K - 1):
+        for placed, want in cases:
+            A, G = _scan_fixture(V, seed, k, placed)
+            assert oracle.query_vector(V, seed, k, A, G) == _idx(V, *want), (k, placed)
+    # a bucket that fails its checksum, or holds a non-edge, is passed over
+    A, G = _scan_fixture(V, seed, 0, {(1, 3): (20, 21), (1, 5): (22, 23)})
+    G[1, 3] ^= 1
+    assert oracle.query_vector(V, seed, 0, A, G) == _idx(V, 22, 23)
+    _, _, c = oracle.keys(seed, K)
+    A[1, 5] = 7 * V + 3  # decodes to u > v
+    G[1, 5] = oracle.h2(c[1], 7 * V + 3)
+    assert oracle.query_vector(V, seed, 0, A, G) == oracle.FAIL
+
+
+def test_boruvka_sample_follows_the_scan_order():
+    # The same order inside Boruvka: round 0 of a graph whose only nonzero
+    # sketch is vertex 0's CubeSketch 0, with three good buckets whose edges
+    # all leave {0}; the trace must hold the first in Fig. cube_code's order.
+    V, seed = 64, 31
+    K, R = oracle.geometry(V)
+    alpha, gamma = oracle.empty_sketches(V)
+    A, G = _scan_fixture(V, seed, 0, {(2, 1): (0, 5), (2, 6): (0, 3), (4, 0): (0, 7)})
+    alpha[0, 0], gamma[0, 0] = A, G
+    res = oracle.boruvka(V, seed, alpha, gamma)
+    samples, labels = res["samples"], res["labels"]
+    assert samples[0, 0] == _idx(V, 0, 5)
+    assert all(samples[0, x] == oracle.EMPTY for x in range(1, V))
+    assert labels[5] == 0 and labels[3] == 3 and labels[7] == 7
+    # a good bucket whose edge stays inside the component is passed over
+    # (the cut check): with {0, 5} merged, round 1 must skip (0, 5)
+    A1, G1 = _scan_fixture(V, seed, 1, {(0, 0): (0, 5), (0, 4): (0, 9)})
+    alpha[0, 1], gamma[0, 1] = A1, G1
+    samples = oracle.boruvka(V, seed, alpha, gamma)["samples"]
+    assert samples[1, 0] == _idx(V, 0, 9)
 
 
 def test_query_returns_a_member_and_fails_rarely():
