@@ -54,13 +54,15 @@ def lib():
         L.gzo_splitmix64_at.restype = u64
         L.gzo_splitmix64_at.argtypes = [u64, u64]
         L.gzo_h1.restype = u64
-        L.gzo_h1.argtypes = [u64, u64, u64]
+        L.gzo_h1.argtypes = [u32, p, u64]
         L.gzo_h2.restype = u32
-        L.gzo_h2.argtypes = [u64, u64, u64, u64]
+        L.gzo_h2.argtypes = [u32, p, u64]
+        L.gzo_pieces.restype = None
+        L.gzo_pieces.argtypes = [u32, p, p, p]
         L.gzo_geometry.restype = ctypes.c_int
         L.gzo_geometry.argtypes = [u32, p, p]
         L.gzo_keys.restype = None
-        L.gzo_keys.argtypes = [u64, u32, p, p, p, p, p]
+        L.gzo_keys.argtypes = [u64, u32, p]
         L.gzo_ingest.restype = ctypes.c_int
         L.gzo_ingest.argtypes = [u32, u64, sz, p, p, p, p]
         L.gzo_sketch_node.restype = ctypes.c_int
@@ -105,30 +107,39 @@ def geometry(V: int) -> tuple[int, int]:
     return int(K[0]), int(R[0])
 
 
-def keys(seed: int, K: int):
-    """Hash keys of the 7K columns: a, b (h1) as arrays of 7K, and c, a
-    (7K, 3) array holding the h2 keys (c0, c1, c2) of each column."""
-    a = np.zeros(K * COLS, np.uint64)
-    b = np.zeros(K * COLS, np.uint64)
-    c0 = np.zeros(K * COLS, np.uint64)
-    c1 = np.zeros(K * COLS, np.uint64)
-    c2 = np.zeros(K * COLS, np.uint64)
-    lib().gzo_keys(seed, K, _ptr(a), _ptr(b), _ptr(c0), _ptr(c1), _ptr(c2))
-    return a, b, np.stack([c0, c1, c2], axis=1)
+KEY_WORDS = 256  # 32-bit key words per column: h1 pieces at [0, 128), h2 pieces at [128, 256)
+
+
+def keys(seed: int, K: int) -> np.ndarray:
+    """Hash keys of the 7K columns: a (7K, 256) uint32 array, row col holding
+    the h1 pieces' keys in [0, 128) and the h2 pieces' keys in [128, 256)."""
+    k = np.zeros((K * COLS, KEY_WORDS), np.uint32)
+    lib().gzo_keys(seed, K, _ptr(k))
+    return k
+
+
+def pieces(V: int) -> tuple[int, int, int]:
+    """(p, m1, m2): piece width 33 - ceil(log2 V) and the pieces of h1 and h2."""
+    out = np.zeros(3, np.uint32)
+    lib().gzo_pieces(V, _ptr(out[0:]), _ptr(out[1:]), _ptr(out[2:]))
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def splitmix64_at(seed: int, n: int) -> int:
     return int(lib().gzo_splitmix64_at(seed, n))
 
 
-def h1(a: int, b: int, x: int) -> int:
-    return int(lib().gzo_h1(a, b, x))
+def h1(V: int, kcol, e: int) -> int:
+    """col_hash of edge index e (u < v < V) under the keys of one column (a row
+    of keys()): bit i is the i-th bit of H1 from its most significant end."""
+    k = np.ascontiguousarray(kcol, np.uint32)
+    return int(lib().gzo_h1(V, _ptr(k), e))
 
 
-def h2(c, x: int) -> int:
-    """Checksum h2 of index x under the key triple c = (c0, c1, c2)."""
-    c0, c1, c2 = (int(t) for t in c)
-    return int(lib().gzo_h2(c0, c1, c2, x))
+def h2(V: int, kcol, e: int) -> int:
+    """Checksum of edge index e (u < v < V) under the keys of one column."""
+    k = np.ascontiguousarray(kcol[128:], np.uint32)
+    return int(lib().gzo_h2(V, _ptr(k), e))
 
 
 def empty_sketches(V: int, nodes: int | None = None):

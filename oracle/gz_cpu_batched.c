@@ -22,22 +22,21 @@
 
 #define GZB_COLS 7
 
-uint64_t gzo_h1(uint64_t a, uint64_t b, uint64_t x);
-uint32_t gzo_h2(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t x);
+uint64_t gzo_h1(uint32_t V, const uint32_t *k1, uint64_t e);
+uint32_t gzo_h2(uint32_t V, const uint32_t *k2, uint64_t e);
 int gzo_geometry(uint32_t V, uint32_t *K, uint32_t *R);
-void gzo_keys(uint64_t seed, uint32_t K, uint64_t *a, uint64_t *b, uint64_t *c0, uint64_t *c1,
-              uint64_t *c2);
+void gzo_keys(uint64_t seed, uint32_t K, uint32_t *keys);
+#define GZB_KEYS 256 /* key words per column: h1 pieces at [0, 128), h2 at [128, 256) */
 
-/* Fig. cube_code update_sketch for every CubeSketch of one node sketch; kc
- * holds the three h2 keys of column col at kc[3col .. 3col+2] */
-static void node_apply(uint32_t K, uint32_t R, const uint64_t *ka, const uint64_t *kb,
-                       const uint64_t *kc, uint64_t *alpha, uint32_t *gamma, uint64_t idx)
+/* Fig. cube_code update_sketch for every CubeSketch of one node sketch */
+static void node_apply(uint32_t V, uint32_t K, uint32_t R, const uint32_t *keys, uint64_t *alpha,
+                       uint32_t *gamma, uint64_t idx)
 {
     for (uint32_t k = 0; k < K; k++) {
         for (uint32_t j = 0; j < GZB_COLS; j++) {
             size_t col = (size_t)k * GZB_COLS + j;
-            uint64_t h = gzo_h1(ka[col], kb[col], idx);
-            uint32_t g = gzo_h2(kc[3 * col], kc[3 * col + 1], kc[3 * col + 2], idx);
+            uint64_t h = gzo_h1(V, keys + col * GZB_KEYS, idx);
+            uint32_t g = gzo_h2(V, keys + col * GZB_KEYS + 128, idx);
             uint64_t *A = alpha + col * R;
             uint32_t *G = gamma + col * R;
             uint32_t row = 0;
@@ -62,22 +61,16 @@ int gzb_ingest_batched(uint32_t V, uint64_t seed, size_t n, const uint32_t *u, c
         if (u[i] == v[i] || u[i] >= V || v[i] >= V) return -1;
     if (threads <= 0) threads = omp_get_max_threads();
     const size_t ncol = (size_t)K * GZB_COLS, nb = ncol * R, span = node_hi - node_lo;
-    uint64_t *ka = malloc(ncol * 8), *kb = malloc(ncol * 8), *kc = malloc(3 * ncol * 8);
-    uint64_t *c0 = malloc(ncol * 8), *c1 = malloc(ncol * 8), *c2 = malloc(ncol * 8);
+    uint32_t *keys = malloc(ncol * GZB_KEYS * 4);
     uint32_t *hist = calloc((size_t)threads * span, 4);
     uint32_t *off = malloc((span + 1) * 4);
     uint64_t *rec = malloc(2 * chunk * 8);
     int rc = 0;
-    if (!ka || !kb || !kc || !c0 || !c1 || !c2 || !hist || !off || !rec) {
+    if (!keys || !hist || !off || !rec) {
         rc = -2;
         goto out;
     }
-    gzo_keys(seed, K, ka, kb, c0, c1, c2);
-    for (size_t col = 0; col < ncol; col++) {
-        kc[3 * col] = c0[col];
-        kc[3 * col + 1] = c1[col];
-        kc[3 * col + 2] = c2[col];
-    }
+    gzo_keys(seed, K, keys);
     for (size_t base = 0; base < n; base += chunk) {
         const size_t m = n - base < chunk ? n - base : chunk;
         const uint32_t *cu = u + base, *cv = v + base;
@@ -123,16 +116,11 @@ int gzb_ingest_batched(uint32_t V, uint64_t seed, size_t n, const uint32_t *u, c
         for (size_t x = 0; x < span; x++) {
             uint64_t *A = alpha + x * nb;
             uint32_t *G = gamma + x * nb;
-            for (uint32_t r = off[x]; r < off[x + 1]; r++) node_apply(K, R, ka, kb, kc, A, G, rec[r]);
+            for (uint32_t r = off[x]; r < off[x + 1]; r++) node_apply(V, K, R, keys, A, G, rec[r]);
         }
     }
 out:
-    free(ka);
-    free(kb);
-    free(kc);
-    free(c0);
-    free(c1);
-    free(c2);
+    free(keys);
     free(hist);
     free(off);
     free(rec);

@@ -21,27 +21,34 @@
  *              (Section 5, total size ~280 V log^2 V bytes; Table tab:size).
  *   index      idx(u,v) = min(u,v)*V + max(u,v)  (a position of the
  *              characteristic vector, Section 2.2); never 0.
- *   keys       per (k,j), col = 7k+j: a = SM(seed, 5col) | 1,
- *              b = SM(seed, 5col+1), c0 = SM(seed, 5col+2),
- *              c1 = SM(seed, 5col+3), c2 = SM(seed, 5col+4), where SM(s,n) is
- *              the n-th output (n >= 0) of SplitMix64 (Steele, Lea & Flood,
- *              OOPSLA 2014) started at s.
- *   h1         h1(x) = bitreverse64((a*x + b) mod 2^64): the multiply-add-shift
- *              family of Dietzfelbinger (STACS 1996); bit i of h1 is bit 63-i
- *              of the product, so "h1(x) = 0 mod 2^i" tests the TOP i bits.
- *              Bit order of col_hash in Fig. cube_code: bit 0 first.
- *   h2         h2(x) = ((c0*x0 + c1*x1 + c2) mod 2^64) >> 32 with x0, x1 the
- *              low and high 32-bit words of x: multiply-add-shift over a
- *              vector of two 32-bit words (Dietzfelbinger, STACS 1996; the
- *              vector form in Thorup, "High Speed Hashing for Integers and
- *              Strings", 2015).  With 32-bit words, 32 output bits and 64-bit
- *              arithmetic (64 >= 32 + 32 - 1) the family is strongly
- *              universal, i.e. 2-wise independent, as Section 3.2 asks of h2.
+ *   pieces     the hashes are built from "pieces" on the endpoint pair of an
+ *              edge e = (u, v), u < v < V.  With L = ceil(log2 V) (so u, v < 2^L)
+ *              and piece width p = 33 - L, a piece with keys (k0, k1, k2) is
+ *              the top p bits of (k0*u + k1*v + k2) mod 2^32: multiply-add-shift
+ *              over a vector of two L-bit words (Dietzfelbinger, STACS 1996;
+ *              the vector form in Thorup, "High Speed Hashing for Integers and
+ *              Strings", 2015), strongly universal (2-wise independent, as
+ *              Section 3.2 asks of h1 and h2) because 32 >= L + p - 1.  Pieces
+ *              with independent keys are concatenated (the first piece gives
+ *              the most significant bits); the concatenation is strongly
+ *              universal too.  e <-> (u, v) is a bijection, so these are hashes
+ *              of the index e.
+ *   keys       32-bit words: for column col = 7k+j, hash h (1 or 2), piece i
+ *              and coefficient c, lo32(SM(seed, 256*col + 128*(h-1) + 3i + c)),
+ *              SM(s,n) being the n-th output (n >= 0) of SplitMix64 (Steele,
+ *              Lea & Flood, OOPSLA 2014) started at s.
+ *   h1         col_hash of Fig. cube_code: H1 = m1 = ceil((R-1)/p) pieces,
+ *              read from its most significant bit: bit i of col_hash is the
+ *              i-th bit of H1, so "h1(e) = 0 mod 2^i" means the first i bits
+ *              of H1 are zero.  Bit order of col_hash: bit 0 first.
+ *   h2         checksum of Fig. cube_code: the first 32 bits of
+ *              m2 = ceil(32/p) pieces.
  *   rows       the update loop of Fig. cube_code also stops at row R.
  *   query      Fig. cube_code's scan (columns ascending, rows ascending); a
- *              bucket is taken when gamma == h2(alpha) AND alpha decodes to
- *              u < v < V AND exactly one endpoint lies in the queried
- *              component.  All buckets zero -> EMPTY, else no taker -> FAIL.
+ *              bucket is taken when alpha decodes to u < v < V (h2 is defined
+ *              on edges) AND gamma == h2(alpha) AND exactly one endpoint lies
+ *              in the queried component.  All buckets zero -> EMPTY, else no
+ *              taker -> FAIL.
  *   Boruvka    Section 2.2 / Lemma (CC I/O) proof: round r uses CubeSketch r;
  *              components are processed by ascending minimum vertex id; the
  *              union keeps the smaller root, so every label is the minimum
@@ -76,18 +83,54 @@ static uint64_t bitreverse64(uint64_t x)
     return r;
 }
 
-/* col_hash of Fig. cube_code: h1(x) = bitreverse64(a*x + b mod 2^64). */
-uint64_t gzo_h1(uint64_t a, uint64_t b, uint64_t x)
+/* L = ceil(log2 V): every vertex id is below 2^L */
+static uint32_t id_bits(uint32_t V)
 {
-    return bitreverse64(a * x + b);
+    uint32_t L = 0;
+    while (((uint64_t)1 << L) < (uint64_t)V) L++;
+    return L;
 }
 
-/* checksum of Fig. cube_code: h2(x) = ((c0*x0 + c1*x1 + c2) mod 2^64) >> 32,
- * x0 = lo32(x), x1 = hi32(x). */
-uint32_t gzo_h2(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t x)
+/* Piece width p = 33 - L and the pieces of h1 (ceil((R-1)/p), R = 2L) and of
+ * h2 (ceil(32/p)). */
+void gzo_pieces(uint32_t V, uint32_t *p, uint32_t *m1, uint32_t *m2)
 {
-    uint64_t x0 = x & 0xFFFFFFFFu, x1 = x >> 32;
-    return (uint32_t)((c0 * x0 + c1 * x1 + c2) >> 32);
+    uint32_t L = id_bits(V), w = 33 - L, need1 = 2 * L - 1;
+    *p = w;
+    *m1 = (need1 + w - 1) / w;
+    *m2 = (32 + w - 1) / w;
+}
+
+/* The concatenation of m pieces with keys k[3i], k[3i+1], k[3i+2] on (u, v),
+ * left-aligned in 64 bits (m*p <= 62 for every V <= 2^31). */
+static uint64_t pieces(const uint32_t *k, uint32_t m, uint32_t p, uint32_t u, uint32_t v)
+{
+    uint64_t acc = 0;
+    for (uint32_t i = 0; i < m; i++) {
+        uint32_t t = k[3 * i] * u + k[3 * i + 1] * v + k[3 * i + 2];   /* mod 2^32 */
+        uint64_t top = t >> (32 - p);
+        acc |= top << (64 - p * (i + 1));
+    }
+    return acc;
+}
+
+/* col_hash of Fig. cube_code for edge index e (u = e / V < v = e % V):
+ * bit i is the i-th bit of H1 counted from its most significant end.  k1
+ * holds the h1 keys of one column (3 words per piece). */
+uint64_t gzo_h1(uint32_t V, const uint32_t *k1, uint64_t e)
+{
+    uint32_t p, m1, m2;
+    gzo_pieces(V, &p, &m1, &m2);
+    return bitreverse64(pieces(k1, m1, p, (uint32_t)(e / V), (uint32_t)(e % V)));
+}
+
+/* checksum of Fig. cube_code for edge index e: the first 32 bits of the h2
+ * pieces.  k2 holds the h2 keys of one column. */
+uint32_t gzo_h2(uint32_t V, const uint32_t *k2, uint64_t e)
+{
+    uint32_t p, m1, m2;
+    gzo_pieces(V, &p, &m1, &m2);
+    return (uint32_t)(pieces(k2, m2, p, (uint32_t)(e / V), (uint32_t)(e % V)) >> 32);
 }
 
 /* ---------------------------------------------------------------- geometry */
@@ -108,26 +151,20 @@ int gzo_geometry(uint32_t V, uint32_t *K, uint32_t *R)
     return 0;
 }
 
-/* Keys of all K*7 columns (k,j), col = 7k+j: five consecutive SplitMix64
- * outputs per column, a (forced odd) and b for h1, c0, c1, c2 for h2. */
-void gzo_keys(uint64_t seed, uint32_t K, uint64_t *a, uint64_t *b,
-              uint64_t *c0, uint64_t *c1, uint64_t *c2)
+/* Hash keys of all K*7 columns (k,j), col = 7k+j: GZO_KEYS 32-bit words per
+ * column, the h1 pieces' keys at [0, 128) and the h2 pieces' at [128, 256);
+ * word w of column col is lo32(SM(seed, 256*col + w)). */
+#define GZO_KEYS 256
+void gzo_keys(uint64_t seed, uint32_t K, uint32_t *keys)
 {
-    for (uint32_t k = 0; k < K; k++) {
-        for (uint32_t j = 0; j < GZO_COLS; j++) {
-            uint64_t col = (uint64_t)k * GZO_COLS + j;
-            a[col] = gzo_splitmix64_at(seed, 5 * col) | 1u;
-            b[col] = gzo_splitmix64_at(seed, 5 * col + 1);
-            c0[col] = gzo_splitmix64_at(seed, 5 * col + 2);
-            c1[col] = gzo_splitmix64_at(seed, 5 * col + 3);
-            c2[col] = gzo_splitmix64_at(seed, 5 * col + 4);
-        }
-    }
+    for (uint64_t col = 0; col < (uint64_t)K * GZO_COLS; col++)
+        for (uint32_t w = 0; w < GZO_KEYS; w++)
+            keys[col * GZO_KEYS + w] = (uint32_t)gzo_splitmix64_at(seed, GZO_KEYS * col + w);
 }
 
 typedef struct {
     uint32_t V, K, R;
-    uint64_t *a, *b, *c0, *c1, *c2;
+    uint32_t *keys;   /* GZO_KEYS words per column */
 } gzo_ctx;
 
 static int ctx_open(gzo_ctx *x, uint32_t V, uint64_t seed)
@@ -135,19 +172,15 @@ static int ctx_open(gzo_ctx *x, uint32_t V, uint64_t seed)
     if (gzo_geometry(V, &x->K, &x->R)) return -1;
     x->V = V;
     size_t ncol = (size_t)x->K * GZO_COLS;
-    x->a = malloc(ncol * 8);
-    x->b = malloc(ncol * 8);
-    x->c0 = malloc(ncol * 8);
-    x->c1 = malloc(ncol * 8);
-    x->c2 = malloc(ncol * 8);
-    if (!x->a || !x->b || !x->c0 || !x->c1 || !x->c2) return -2;
-    gzo_keys(seed, x->K, x->a, x->b, x->c0, x->c1, x->c2);
+    x->keys = malloc(ncol * GZO_KEYS * 4);
+    if (!x->keys) return -2;
+    gzo_keys(seed, x->K, x->keys);
     return 0;
 }
 
 static void ctx_close(gzo_ctx *x)
 {
-    free(x->a); free(x->b); free(x->c0); free(x->c1); free(x->c2);
+    free(x->keys);
 }
 
 /* words of one node sketch: K*7*R buckets */
@@ -166,8 +199,9 @@ static void cubesketch_update(const gzo_ctx *x, uint32_t k,
 {
     for (uint32_t j = 0; j < GZO_COLS; j++) {
         size_t col = (size_t)k * GZO_COLS + j;
-        uint64_t col_hash = gzo_h1(x->a[col], x->b[col], idx);
-        uint32_t checksum = gzo_h2(x->c0[col], x->c1[col], x->c2[col], idx);
+        const uint32_t *kc = x->keys + col * GZO_KEYS;
+        uint64_t col_hash = gzo_h1(x->V, kc, idx);
+        uint32_t checksum = gzo_h2(x->V, kc + 128, idx);
         uint64_t *A = alpha_k + (size_t)j * x->R;
         uint32_t *G = gamma_k + (size_t)j * x->R;
         uint32_t row = 0;
@@ -257,10 +291,11 @@ static int64_t cubesketch_query(const gzo_ctx *x, uint32_t k,
             uint32_t gamma = G[(size_t)j * x->R + row];
             if (alpha == 0 && gamma == 0) continue;
             nonzero = 1;
-            if (gamma != gzo_h2(x->c0[col], x->c1[col], x->c2[col], alpha)) continue;
+            /* h2 is defined on edge indices: alpha must decode to u < v < V */
             if (alpha >= VV) continue;
             uint64_t uu = alpha / x->V, vv = alpha % x->V;
             if (uu >= vv) continue;
+            if (gamma != gzo_h2(x->V, x->keys + col * GZO_KEYS + 128, alpha)) continue;
             int in_u = label[uu] == comp, in_v = label[vv] == comp;
             if (in_u == in_v) continue;
             return (int64_t)alpha;
@@ -287,8 +322,8 @@ int64_t gzo_query_vector(uint32_t V, uint64_t seed, uint32_t k,
             uint32_t gamma = G[(size_t)j * x.R + row];
             if (alpha == 0 && gamma == 0) continue;
             nonzero = 1;
-            if (gamma != gzo_h2(x.c0[col], x.c1[col], x.c2[col], alpha)) continue;
             if (alpha >= VV || alpha / V >= alpha % V) continue;
+            if (gamma != gzo_h2(V, x.keys + col * GZO_KEYS + 128, alpha)) continue;
             out = (int64_t)alpha;
             break;
         }

@@ -12,7 +12,7 @@
  *              R = ceil(log2 n) rows, the depth cap of both samplers.
  *   keys       column j: a = SM(seed, 5j) | 1, b = SM(seed, 5j+1),
  *              c0, c1, c2 = SM(seed, 5j+2), SM(seed, 5j+3), SM(seed, 5j+4)
- *              (SplitMix64, the node sketches' schedule for column j).
+ *              (SplitMix64).
  *   membership both samplers put x into rows 0..d of column j with
  *              d = min(clz64(a*x + b), R-1): Fig. agm_code's
  *              "col_hash[row-1] == 0" loop with the bit order of
@@ -26,8 +26,10 @@
  *              1 <= a/b <= n and c == (b mod p) * r_j^(a/b) (mod p) yields
  *              (a/b, b); all buckets zero -> EMPTY, else FAIL.
  *   CubeSketch bucket (alpha u64, gamma u32): alpha ^= x, gamma ^= h2(x) with
- *              the node sketches' h2 (multiply-add-shift over the two 32-bit
- *              words of x, keys c0, c1, c2); a delta of -1 is the same toggle.
+ *              h2(x) = ((c0*x0 + c1*x1 + c2) mod 2^64) >> 32 over the two
+ *              32-bit words x0, x1 of the position (positions are not edges,
+ *              so the node sketches' pair hashes do not apply); a delta of -1
+ *              is the same toggle.
  * Layout of one sketch: standard a[7][R], b[7][R], c[7][R] (u64 each);
  * CubeSketch alpha[7][R] (u64) then gamma[7][R] (u32).
  */
@@ -38,7 +40,15 @@
 #define P61 ((((uint64_t)1) << 61) - 1)
 
 uint64_t gzo_splitmix64_at(uint64_t s, uint64_t n);
-uint32_t gzo_h2(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t x);
+/* CubeSketch checksum of a vector position x: multiply-add-shift over the two
+ * 32-bit words x0, x1 of x with 64-bit arithmetic (Dietzfelbinger 1996; the
+ * vector form in Thorup 2015), ((c0*x0 + c1*x1 + c2) mod 2^64) >> 32,
+ * strongly universal for 32-bit words and 32 output bits. */
+static uint32_t l0_checksum(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t x)
+{
+    uint64_t x0 = x & 0xFFFFFFFFu, x1 = x >> 32;
+    return (uint32_t)((c0 * x0 + c1 * x1 + c2) >> 32);
+}
 
 /* rows of a length-n vector sketch: ceil(log2 n), at least 1 */
 uint32_t gzo_l0_rows(uint64_t n)
@@ -107,7 +117,7 @@ int gzo_l0_update(int kind, uint64_t n, uint64_t seed, size_t m, const uint64_t 
             if (kind == 0) {
                 uint64_t *A = (uint64_t *)buckets + (size_t)j * R;
                 uint32_t *G = (uint32_t *)((uint64_t *)buckets + nb) + (size_t)j * R;
-                uint32_t g = gzo_h2(kc0, kc1, kc2, x[i]);
+                uint32_t g = l0_checksum(kc0, kc1, kc2, x[i]);
                 for (uint32_t row = 0; row <= d; row++) {
                     A[row] ^= x[i];
                     G[row] ^= g;
@@ -147,7 +157,7 @@ int64_t gzo_l0_query(int kind, uint64_t n, uint64_t seed, const void *buckets, i
                 uint32_t gamma = ((const uint32_t *)((const uint64_t *)buckets + nb))[(size_t)j * R + row];
                 if (alpha == 0 && gamma == 0) continue;
                 nonzero = 1;
-                if (alpha < 1 || alpha > n || gamma != gzo_h2(kc0, kc1, kc2, alpha)) continue;
+                if (alpha < 1 || alpha > n || gamma != l0_checksum(kc0, kc1, kc2, alpha)) continue;
                 if (value) *value = 1;
                 return (int64_t)alpha;
             } else {

@@ -45,24 +45,61 @@ def test_splitmix64_published_outputs():
     assert got == want
 
 
-def test_h2_special_keys_select_words_and_carry():
-    # With degenerate keys the multiply-add-shift checksum reduces to closed
-    # forms: a constant (the top word of c2), the low or the high word of the
-    # index, the parity of the high word, and a low-word sum whose carry
-    # reaches the output word.  A dropped term, a transposed key or word, a
-    # wrong shift or a lost carry fails one of these.
+def _key_row(h1_pieces=(), h2_pieces=()):
+    """One column's 256 key words with the given (k0, k1, k2) per piece."""
+    k = np.zeros(oracle.KEY_WORDS, np.uint32)
+    for i, t in enumerate(h1_pieces):
+        k[3 * i:3 * i + 3] = t
+    for i, t in enumerate(h2_pieces):
+        k[128 + 3 * i:128 + 3 * i + 3] = t
+    return k
+
+
+def test_piece_geometry():
+    # p = 33 - ceil(log2 V); h1 covers the R - 1 = 2L - 1 depth bits, h2 32 bits
+    for V, want in [(2, (32, 1, 1)), (1000, (23, 1, 2)), (1 << 13, (20, 2, 2)), (70001, (16, 3, 2)),
+                    (1 << 17, (16, 3, 2)), (1 << 20, (13, 3, 3)), (1 << 31, (2, 31, 16))]:
+        assert oracle.pieces(V) == want, V
+
+
+def test_hash_pieces_closed_forms():
+    # With degenerate keys every piece reduces to a closed form: a constant
+    # (the top p bits of k2), the low p bits of u or of v moved to the top, or
+    # a sum whose carry crosses into the piece.  The concatenation
+    # order (first piece most significant), the piece width, a transposed
+    # pair, a wrong shift or a lost carry fails one of these.
     rng = np.random.default_rng(5)
-    xs = [1, 2, 12345, 2**32 - 1, 2**32, 2**33 + 7, 2**34 - 1, 2**63 + 5, 2**64 - 1]
-    xs += [int(t) for t in rng.integers(1, 2**63, 40, dtype=np.uint64)]
-    for x in xs:
-        x0, x1 = x & 0xFFFFFFFF, x >> 32
-        assert oracle.h2((0, 0, 0xAAAABBBB_12345678), x) == 0xAAAABBBB
-        assert oracle.h2((2**32, 0, 0), x) == x0
-        assert oracle.h2((0, 2**32, 0), x) == x1
-        assert oracle.h2((0, 2**63, 0), x) == (x1 & 1) << 31
-        assert oracle.h2((1, 1, 0), x) == (x0 + x1) >> 32  # only the carry of x0 + x1
-        assert oracle.h2((2**32 + 1, 0, 2**32 - 1), x) == (x0 + (x0 >= 1)) % 2**32
-        assert oracle.h2((0, 2**32 + 3, 0), x) == (x1 + (3 * x1 >> 32)) % 2**32
+    for V in (1000, 70001, 1 << 17, 1 << 20):
+        p, m1, m2 = oracle.pieces(V)
+        L = 33 - p
+        edges = [(0, 1), (1, 2), (V - 2, V - 1), (0, V - 1)]
+        edges += [tuple(sorted(rng.choice(V, 2, replace=False).tolist())) for _ in range(30)]
+        consts = [int(t) for t in rng.integers(0, 2**32, 16, dtype=np.uint64)]
+        for u, v in edges:
+            e = u * V + v
+            # constants only: h2 = the top p bits of each k2, concatenated, first 32 bits
+            k = _key_row(h2_pieces=[(0, 0, c) for c in consts[:m2]])
+            bits = "".join(format(c >> (32 - p), f"0{p}b") for c in consts[:m2])[:32]
+            assert oracle.h2(V, k, e) == int(bits, 2)
+            # word selection: k0 = 2^(32-p) puts u's low p bits at the top of piece 0
+            k = _key_row(h2_pieces=[(1 << (32 - p), 0, 0), (0, 1 << (32 - p), 0)] + [(0, 0, 0)] * (m2 - 2))
+            bits = (format(u % (1 << p), f"0{p}b") + format(v % (1 << p), f"0{p}b"))[:32].ljust(32, "0")
+            assert oracle.h2(V, k, e) == int(bits, 2)
+            # carry: top p bits of (u + 2^32 - 1) mod 2^32 are all ones iff u == 0
+            k = _key_row(h2_pieces=[(1, 0, 2**32 - 1)] + [(0, 0, 0)] * (m2 - 1))
+            top = ((u + 2**32 - 1) % 2**32) >> (32 - p)
+            assert oracle.h2(V, k, e) >> (32 - p) == top
+            # h1: col_hash bit i = the i-th bit of the H1 pieces from the top
+            k = _key_row(h1_pieces=[(0, 0, c) for c in consts[:m1]])
+            bits = "".join(format(c >> (32 - p), f"0{p}b") for c in consts[:m1])
+            ch = oracle.h1(V, k, e)
+            assert all((ch >> i) & 1 == int(bits[i]) for i in range(len(bits)))
+            assert ch >> len(bits) == 0
+            k = _key_row(h1_pieces=[(0, 1 << (32 - p), 0)] + [(0, 0, 0)] * (m1 - 1))
+            ch = oracle.h1(V, k, e)
+            bits = format(v % (1 << p), f"0{p}b")
+            assert all((ch >> i) & 1 == int(bits[i]) for i in range(p)), (V, u, v)
+        assert L == (V - 1).bit_length()
 
 
 def _chi2_uniform(counts):
@@ -70,70 +107,94 @@ def _chi2_uniform(counts):
     return float(((counts - e) ** 2 / e).sum())
 
 
-def test_h2_is_pairwise_independent():
-    # Section 3.2 asks for h2 from a 2-wise independent family: for any two
-    # distinct indices x, y and uniform keys, (h2(x), h2(y)) is uniform on
-    # pairs of 32-bit words.  Checked on the top three and the low three
-    # output bits of each, for pairs that differ in the low word only, by a
-    # power of two, in the high word only, or in both words (an index can
-    # reach 2^34 at V = 2^17).
+@pytest.mark.parametrize("V", [1000, 1 << 17, 1 << 20])
+def test_h2_is_pairwise_independent(V):
+    # Section 3.2 asks for h2 from a 2-wise independent family: for two
+    # distinct edges and uniform keys, (h2(e), h2(f)) is uniform on pairs of
+    # 32-bit words.  Checked on the top three and the low three output bits
+    # (the latter fall in the last piece), for edges sharing u, sharing v,
+    # sharing nothing, and differing by one or by a power of two.
     rng = np.random.default_rng(17)
-    pairs = [(1, 2), (5, 5 + 2**16), (3, 3 + 2**31), (77, 77 + 2**32), (2**33 + 9, 9),
-             (2**31, 2**32 + 2**31), (123456789, 2**34 - 1)]
+    pairs = [((0, 1), (0, 2)), ((5, 9), (7, 9)), ((3, V - 1), (4, V - 2)), ((1, 2), (1, 2 + 256)),
+             ((0, V // 2), (V // 2, V - 1)), ((11, 12), (13, 14))]
     n = 6400
-    keys = rng.integers(0, 2**64, (n, 3), dtype=np.uint64)
+    keys = rng.integers(0, 2**32, (n, oracle.KEY_WORDS), dtype=np.uint64).astype(np.uint32)
     limit = 63 + 6 * np.sqrt(2 * 63)  # chi-square, 63 degrees of freedom, far tail
-    for x, y in pairs:
+    for (a, b), (c, d) in pairs:
+        e, f = a * V + b, c * V + d
         top = np.zeros((8, 8))
         low = np.zeros((8, 8))
-        for c in keys:
-            hx, hy = oracle.h2(c, x), oracle.h2(c, y)
-            top[hx >> 29, hy >> 29] += 1
-            low[hx & 7, hy & 7] += 1
-        assert _chi2_uniform(top) < limit, (x, y, "top bits")
-        assert _chi2_uniform(low) < limit, (x, y, "low bits")
+        for k in keys:
+            he, hf = oracle.h2(V, k, e), oracle.h2(V, k, f)
+            top[he >> 29, hf >> 29] += 1
+            low[he & 7, hf & 7] += 1
+        assert _chi2_uniform(top) < limit, (V, e, f, "top bits")
+        assert _chi2_uniform(low) < limit, (V, e, f, "low bits")
+
+
+@pytest.mark.parametrize("V", [1000, 1 << 17, 1 << 20])
+def test_depth_bits_are_pairwise_independent(V):
+    # Lemma goodset uses P[e in B_i] = 2^-i and pairwise independence of
+    # membership (2-wise independent h1).  The first three H1 bits and the
+    # three bits that straddle the first piece boundary (where a word or
+    # carry mistake would correlate two edges) are jointly uniform.
+    p, m1, _ = oracle.pieces(V)
+    rng = np.random.default_rng(23)
+    pairs = [((0, 1), (0, 2)), ((5, 9), (7, 9)), ((1, 2), (3, 4)), ((2, V - 1), (3, V - 1))]
+    n = 6400
+    keys = rng.integers(0, 2**32, (n, oracle.KEY_WORDS), dtype=np.uint64).astype(np.uint32)
+    limit = 63 + 6 * np.sqrt(2 * 63)
+    span = [0, 1, 2] if m1 == 1 else [p - 2, p - 1, p]
+    for (a, b), (c, d) in pairs:
+        e, f = a * V + b, c * V + d
+        first = np.zeros((8, 8))
+        cross = np.zeros((8, 8))
+        for k in keys:
+            he, hf = oracle.h1(V, k, e), oracle.h1(V, k, f)
+            first[he & 7, hf & 7] += 1
+            cross[sum(((he >> i) & 1) << t for t, i in enumerate(span)),
+                  sum(((hf >> i) & 1) << t for t, i in enumerate(span))] += 1
+        assert _chi2_uniform(first) < limit, (V, e, f)
+        assert _chi2_uniform(cross) < limit, (V, e, f)
 
 
 def test_checksum_is_not_xor_linear():
     # Lemma goodcheck needs h2(x) ^ h2(y) != h2(x ^ y) except with
     # probability ~2^-32; a GF(2)-linear checksum would pass every bucket.
+    V = 1 << 17
     rng = np.random.default_rng(11)
-    a, b, c = oracle.keys(3, 1)
-    hits = 0
-    for t in range(20000):
-        x, y = (int(z) for z in rng.integers(1, 2**34, 2))
-        if x == y:
+    keys = oracle.keys(3, 1)
+    hits = tried = 0
+    for t in range(40000):
+        a, b, c, d = (int(z) for z in rng.integers(0, V, 4))
+        if a >= b or c >= d or (a, b) == (c, d):
             continue
-        ck = c[t % 7]
-        hits += (oracle.h2(ck, x) ^ oracle.h2(ck, y)) == oracle.h2(ck, x ^ y)
-    assert hits == 0
+        x, y = a * V + b, c * V + d
+        z = x ^ y
+        if z >= V * V or z // V >= z % V:
+            continue  # x ^ y is not an edge: the decode check already rejects it
+        tried += 1
+        ck = keys[t % 7]
+        hits += (oracle.h2(V, ck, x) ^ oracle.h2(V, ck, y)) == oracle.h2(V, ck, z)
+    assert tried > 4000 and hits == 0
 
 
-def test_row_membership_law_and_pairwise_independence():
-    # Lemma goodset relies on P[e in B_i] = 2^-i and on pairwise independence
-    # of membership for distinct indices (2-wise independent h1, Section 3.2).
+def test_row_membership_law():
+    # P[e in nested row i] = 2^-i under the schedule's keys (Lemma goodset)
     V = 1 << 17
     K, R = oracle.geometry(V)
-    a, b, c = oracle.keys(99, K)
+    keys = oracle.keys(99, K)
     rng = np.random.default_rng(2)
     n = 6000
     counts = np.zeros(6)
-    both = np.zeros(4)
     for t in range(n):
-        col = t % (K * 7)
-        x, y = (int(z) for z in rng.integers(1, V * V, 2))
-        hx = oracle.h1(int(a[col]), int(b[col]), x)
-        hy = oracle.h1(int(a[col]), int(b[col]), y)
+        a, b = sorted(rng.choice(V, 2, replace=False).tolist())
+        h = oracle.h1(V, keys[t % (K * 7)], a * V + b)
         for i in range(6):
-            counts[i] += (hx & ((1 << i) - 1)) == 0
-        for i in range(1, 5):
-            both[i - 1] += ((hx & ((1 << i) - 1)) == 0) and ((hy & ((1 << i) - 1)) == 0)
+            counts[i] += (h & ((1 << i) - 1)) == 0
     for i in range(6):
-        p = 2.0 ** -i
-        assert abs(counts[i] / n - p) < 5 * np.sqrt(p * (1 - p) / n) + 1e-9
-    for i in range(1, 5):
-        p = 4.0 ** -i
-        assert abs(both[i - 1] / n - p) < 5 * np.sqrt(p * (1 - p) / n) + 1e-9
+        q = 2.0 ** -i
+        assert abs(counts[i] / n - q) < 5 * np.sqrt(q * (1 - q) / n) + 1e-9
 
 
 # ----------------------------------------------------------------- geometry
@@ -180,7 +241,7 @@ def _bucket_definition(V, seed, edges):
     """Nested buckets from Eq. 1-2: alpha_{i,j} = XOR of the indices e of the
     vector with h1(e) = 0 mod 2^i (capped at row R-1), gamma likewise."""
     K, R = oracle.geometry(V)
-    a, b, c = oracle.keys(seed, K)
+    keys = oracle.keys(seed, K)
     A = np.zeros((V, K, 7, R), np.uint64)
     G = np.zeros((V, K, 7, R), np.uint32)
     for (u, v) in edges:
@@ -188,8 +249,8 @@ def _bucket_definition(V, seed, edges):
         for k in range(K):
             for j in range(7):
                 col = k * 7 + j
-                h = oracle.h1(int(a[col]), int(b[col]), e)
-                g = oracle.h2(c[col], e)
+                h = oracle.h1(V, keys[col], e)
+                g = oracle.h2(V, keys[col], e)
                 for i in range(R):
                     if h % (1 << i) == 0:
                         for node in (u, v):
@@ -269,7 +330,7 @@ def test_invalid_update_is_rejected_whole():
 def test_support_one_buckets_pass_checksum_lemma_goodcheck():
     V = 300
     K, R = oracle.geometry(V)
-    a, b, c = oracle.keys(21, K)
+    keys = oracle.keys(21, K)
     u, v = S.random_stream(V, 800, seed=5, n_distinct=800)
     eu, ev = S.net_graph(V, u, v)
     A, G = oracle.ingest(V, 21, eu, ev)
@@ -282,13 +343,13 @@ def test_support_one_buckets_pass_checksum_lemma_goodcheck():
                 col = k * 7 + j
                 depth = {}
                 for e in elems:
-                    h = oracle.h1(int(a[col]), int(b[col]), e)
+                    h = oracle.h1(V, keys[col], e)
                     depth[e] = min((h & -h).bit_length() - 1 if h else 64, R - 1)
                 for i in range(R):
                     members = [e for e in elems if depth[e] >= i]
                     if len(members) == 1:
                         assert int(A[x, k, j, i]) == members[0]
-                        assert int(G[x, k, j, i]) == oracle.h2(c[col], members[0])
+                        assert int(G[x, k, j, i]) == oracle.h2(V, keys[col], members[0])
                         checked += 1
     assert checked > 500
 
@@ -304,22 +365,22 @@ def test_query_single_element_and_empty_vector():
     assert oracle.query_vector(V, 3, 0, A[0, 0], G[0, 0]) == oracle.EMPTY
 
 
-def _good_bucket(V, c, u, w):
+def _good_bucket(V, kcol, u, w):
     """(alpha, gamma) of a bucket holding only edge {u, w}: it passes the
     checksum of its column (Lemma goodcheck, support one)."""
     e = _idx(V, u, w)
-    return e, oracle.h2(c, e)
+    return e, oracle.h2(V, kcol, e)
 
 
 def _scan_fixture(V, seed, k, placed):
     """One CubeSketch (layout [j][row]) holding the good buckets `placed`
     {(j, row): (u, w)} and zeros elsewhere."""
     K, R = oracle.geometry(V)
-    a, b, c = oracle.keys(seed, K)
+    keys = oracle.keys(seed, K)
     A = np.zeros((7, R), np.uint64)
     G = np.zeros((7, R), np.uint32)
     for (j, row), (u, w) in placed.items():
-        A[j, row], G[j, row] = _good_bucket(V, c[k * 7 + j], u, w)
+        A[j, row], G[j, row] = _good_bucket(V, keys[k * 7 + j], u, w)
     return A, G
 
 
@@ -343,9 +404,8 @@ def test_query_scan_order_is_columns_then_rows_ascending():
     A, G = _scan_fixture(V, seed, 0, {(1, 3): (20, 21), (1, 5): (22, 23)})
     G[1, 3] ^= 1
     assert oracle.query_vector(V, seed, 0, A, G) == _idx(V, 22, 23)
-    _, _, c = oracle.keys(seed, K)
-    A[1, 5] = 7 * V + 3  # decodes to u > v
-    G[1, 5] = oracle.h2(c[1], 7 * V + 3)
+    A[1, 5] = 7 * V + 3  # decodes to u > v: not an edge, whatever gamma holds
+    G[1, 5] = 12345
     assert oracle.query_vector(V, seed, 0, A, G) == oracle.FAIL
 
 
