@@ -23,7 +23,7 @@
  *              characteristic vector, Section 2.2); never 0.
  *   pieces     the hashes are built from "pieces" on the endpoint pair of an
  *              edge e = (u, v), u < v < V.  With L = ceil(log2 V) (so u, v < 2^L)
- *              and piece width p = 33 - L, a piece with keys (k0, k1, k2) is
+ *              and piece width p = min(16, 33 - L), a piece with keys (k0, k1, k2) is
  *              the top p bits of (k0*u + k1*v + k2) mod 2^32: multiply-add-shift
  *              over a vector of two L-bit words (Dietzfelbinger, STACS 1996;
  *              the vector form in Thorup, "High Speed Hashing for Integers and
@@ -91,11 +91,11 @@ static uint32_t id_bits(uint32_t V)
     return L;
 }
 
-/* Piece width p = 33 - L and the pieces of h1 (ceil((R-1)/p), R = 2L) and of
- * h2 (ceil(32/p)). */
+/* Piece width p = min(16, 33 - L) and the pieces of h1 (ceil((R-1)/p),
+ * R = 2L) and of h2 (ceil(32/p)). */
 void gzo_pieces(uint32_t V, uint32_t *p, uint32_t *m1, uint32_t *m2)
 {
-    uint32_t L = id_bits(V), w = 33 - L, need1 = 2 * L - 1;
+    uint32_t L = id_bits(V), w = 33 - L < 16 ? 33 - L : 16, need1 = 2 * L - 1;
     *p = w;
     *m1 = (need1 + w - 1) / w;
     *m2 = (32 + w - 1) / w;

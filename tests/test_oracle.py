@@ -56,9 +56,11 @@ def _key_row(h1_pieces=(), h2_pieces=()):
 
 
 def test_piece_geometry():
-    # p = 33 - ceil(log2 V); h1 covers the R - 1 = 2L - 1 depth bits, h2 32 bits
-    for V, want in [(2, (32, 1, 1)), (1000, (23, 1, 2)), (1 << 13, (20, 2, 2)), (70001, (16, 3, 2)),
-                    (1 << 17, (16, 3, 2)), (1 << 20, (13, 3, 3)), (1 << 31, (2, 31, 16))]:
+    # p = min(16, 33 - ceil(log2 V)); h1 covers the R - 1 = 2L - 1 depth bits,
+    # h2 32 bits
+    for V, want in [(2, (16, 1, 2)), (1000, (16, 2, 2)), (1 << 13, (16, 2, 2)), (70001, (16, 3, 2)),
+                    (1 << 17, (16, 3, 2)), (1 << 18, (15, 3, 3)), (1 << 20, (13, 3, 3)),
+                    (1 << 31, (2, 31, 16))]:
         assert oracle.pieces(V) == want, V
 
 
@@ -71,7 +73,7 @@ def test_hash_pieces_closed_forms():
     rng = np.random.default_rng(5)
     for V in (1000, 70001, 1 << 17, 1 << 20):
         p, m1, m2 = oracle.pieces(V)
-        L = 33 - p
+        L = (V - 1).bit_length()
         edges = [(0, 1), (1, 2), (V - 2, V - 1), (0, V - 1)]
         edges += [tuple(sorted(rng.choice(V, 2, replace=False).tolist())) for _ in range(30)]
         consts = [int(t) for t in rng.integers(0, 2**32, 16, dtype=np.uint64)]
@@ -99,7 +101,7 @@ def test_hash_pieces_closed_forms():
             ch = oracle.h1(V, k, e)
             bits = format(v % (1 << p), f"0{p}b")
             assert all((ch >> i) & 1 == int(bits[i]) for i in range(p)), (V, u, v)
-        assert L == (V - 1).bit_length()
+        assert L == (V - 1).bit_length() and p == min(16, 33 - L)
 
 
 def _chi2_uniform(counts):
