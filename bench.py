@@ -272,8 +272,8 @@ def max_over_ranks(ms: float, dist=None, device="cpu") -> float:
 
 def wide_index_fraction(u, v, V: int, torch, block: int = 1 << 26) -> float:
     """Fraction of updates whose edge index min(u,v)*V + max(u,v) is 2^32 or
-    more: the depth hash of such an index needs the 64-bit multiply (16 integer
-    operations per column update instead of 14)."""
+    more: both hashes of such an index need its high word (11 integer
+    operations per column update instead of 7)."""
     n = u.numel()
     if V * V <= (1 << 32) or n == 0:
         return 0.0
@@ -284,6 +284,21 @@ def wide_index_fraction(u, v, V: int, torch, block: int = 1 << 26) -> float:
         idx = torch.minimum(a, b) * V + torch.maximum(a, b)
         wide += int((idx >= (1 << 32)).sum())
     return wide / n
+
+
+def wide_segment_fraction(u, v, V: int, torch, block: int = 1 << 26) -> float:
+    """Fraction of partition records (one per endpoint of every update) that
+    lie in the segment of a node x >= floor((2^32 - V) / V) + 1, the nodes
+    whose edge indices can reach 2^32: the batched kernel runs its 64-bit
+    column code on every record of such a segment."""
+    n = u.numel()
+    if V * V <= (1 << 32) or n == 0:
+        return 0.0
+    xn = ((1 << 32) - V) // V + 1
+    wide = 0
+    for s in range(0, n, block):
+        wide += int((u[s:s + block].long() >= xn).sum()) + int((v[s:s + block].long() >= xn).sum())
+    return wide / (2 * n)
 
 
 def whole_job_rate(updates_per_rank_step: int, steps: int, world: int, ms_max: float) -> float:
@@ -330,7 +345,8 @@ def run_ours(args, rank: int, world: int):
     log(f"[bench] rank {rank}: generated {total} updates on device in {time.time() - t0:.1f}s")
     u_all, v_all = U[:total], Vv[:total]
     f_wide = wide_index_fraction(u_all, v_all, spec.V, torch)
-    int_peaks = {k: gz.int_peak(k) for k in ("imad", "lop3", "mixed")}
+    f_wide_seg = wide_segment_fraction(u_all, v_all, spec.V, torch)
+    int_peaks = {k: gz.int_peak(k) for k in ("imad", "lop3", "mixed", "clz", "atom_shared")}
     log("[bench] integer ceilings (T thread-instr/s): "
         + ", ".join(f"{k} {v / 1e12:.2f}" for k, v in int_peaks.items()))
 
@@ -411,32 +427,49 @@ def run_ours(args, rank: int, world: int):
            "bytes_per_launch": hbm_bytes, "touched_buckets_per_launch": rows_per_launch,
            "full_sketch_bytes_per_launch": 8.0 * upd_per_launch + 2.0 * s_total}
     hbm["frac"] = hbm["achieved"] / peak
-    # integer issue: 16 32-bit operations per column update of an edge index
-    # of 2^32 or more, 14 below (a fraction f_wide of the stream's updates),
-    # against the measured integer ceilings of this GPU (gz_int_peak: chains of
-    # multiply-add, of three-input logic, and of the two interleaved)
-    ops_per_cu = 16.0 * f_wide + 14.0 * (1.0 - f_wide)
+    # Integer work, by the operations a column update needs under the piece
+    # hashes: the depth piece (1 multiply-add) and its leading-zero count, the
+    # two checksum pieces (2 multiply-adds) joined by one byte permute, and
+    # one shared-memory XOR per bucket word (alpha lo, gamma; alpha hi for an
+    # edge index of 2^32 or more, a fraction f_wide of the stream): 7 + f_wide
+    # ops.  Each goes to one pipe, with its own measured ceiling on this GPU
+    # (gz_int_peak): multiply-adds, leading-zero counts and shared atomics;
+    # the issue ceiling bounds them all together.
+    ops_per_cu = 7.0 + f_wide
     ops = col_updates * ops_per_cu
     issue_nominal = 148 * 4 * 32 * 2.032e9 / 1e12
-    issue_peak = max(int_peaks.values()) / 1e12
-    alu = {"bound": "alu", "achieved": ops / sec / 1e12, "peak": issue_peak, "unit": "Tops/s",
+    issue_peak = max(int_peaks[k] for k in ("imad", "lop3", "mixed")) / 1e12
+    alu = {"bound": "alu", "pipe": "issue (all integer pipes)", "achieved": ops / sec / 1e12, "peak": issue_peak,
+           "unit": "Tops/s",
            "peak_source": "measured: best of the integer probes "
                           + ", ".join(f"{k} {v / 1e12:.2f}" for k, v in int_peaks.items())
-                          + f" T thread-instr/s (nominal issue {issue_nominal:.2f}: 148 SMs x 4 schedulers"
+                          + f" T thread-ops/s (nominal issue {issue_nominal:.2f}: 148 SMs x 4 schedulers"
                             " x 32 lanes x 2.032 GHz)",
            "ops_per_launch": ops, "ops_per_column_update": ops_per_cu,
-           "wide_index_fraction": f_wide}
+           "wide_index_fraction": f_wide, "wide_segment_fraction": f_wide_seg,
+           "frac_of_nominal_issue": ops / sec / 1e12 / issue_nominal}
     alu["frac"] = alu["achieved"] / issue_peak
-    imad_per_cu = 5.0 * f_wide + 4.0 * (1.0 - f_wide)
-    imads = col_updates * imad_per_cu
+    imads = col_updates * 3.0
     imad_nominal = 148 * 4 * 16 * 2.032e9 / 1e12
     imad_peak = int_peaks["imad"] / 1e12
-    imad = {"bound": "alu (integer multiply-add pipe)", "achieved": imads / sec / 1e12, "peak": imad_peak,
+    imad = {"bound": "alu", "pipe": "integer multiply-add", "achieved": imads / sec / 1e12, "peak": imad_peak,
             "unit": "T IMAD/s", "peak_source": f"measured multiply-add chains (nominal {imad_nominal:.2f}:"
                                                 " 148 SMs x 4 x 16-lane pipes x 2.032 GHz)",
-            "imad_per_column_update": imad_per_cu}
+            "imad_per_column_update": 3.0}
     imad["frac"] = imad["achieved"] / imad_peak
-    binding = max((hbm, alu, imad), key=lambda r: r["frac"])
+    clz_peak = int_peaks["clz"] / 1e12
+    clz = {"bound": "alu", "pipe": "leading-zero count", "achieved": col_updates / sec / 1e12, "peak": clz_peak,
+           "unit": "T clz/s", "peak_source": "measured leading-zero-count chains (nominal 4.81: 148 SMs x"
+                                             " 16 lanes x 2.032 GHz)", "clz_per_column_update": 1.0}
+    clz["frac"] = clz["achieved"] / clz_peak
+    atom_peak = int_peaks["atom_shared"] / 1e12
+    atoms = col_updates * (2.0 + f_wide)
+    atom = {"bound": "alu", "pipe": "shared-memory atomics", "achieved": atoms / sec / 1e12, "peak": atom_peak,
+            "unit": "T atomic XOR/s", "peak_source": "measured conflict-free 32-bit shared atomic XOR"
+                                                     " (nominal 9.62: 148 SMs x 32 lanes x 2.032 GHz)",
+            "atomics_per_column_update": 2.0 + f_wide}
+    atom["frac"] = atom["achieved"] / atom_peak
+    binding = max((hbm, alu, imad, clz, atom), key=lambda r: r["frac"])
     roofline = dict(binding)
     roofline.update({
         "kernel": "k_batched" if args.kernel == "batched" else "k_plain",
@@ -446,7 +479,7 @@ def run_ours(args, rank: int, world: int):
         "column_updates_per_s": col_updates / sec,
         "share_of_step": prof["update_ms"] / ms if ms > 0 else None,
         "partition_ms_per_launch": prof["partition_ms"] / launches,
-        "all": {"hbm": hbm, "alu_issue": alu, "imad_pipe": imad},
+        "all": {"hbm": hbm, "alu_issue": alu, "imad_pipe": imad, "clz_pipe": clz, "shared_atomics": atom},
     })
 
     # --- query latency -----------------------------------------------------------

@@ -26,6 +26,15 @@
  *     node sketch takes K*7*R*12 bytes.
  *   - Edge index of an unordered pair {u,v}: idx = min*V + max (a position
  *     of the characteristic vector of Section 2.2).
+ *   - Hashes (readings of Section 3.2, which asks for 2-wise independent h1
+ *     and h2), functions of an edge's endpoints u < v: with L = ceil(log2 V)
+ *     and p = 33 - L, a piece with 32-bit keys (k0, k1, k2) is the top p bits
+ *     of (k0*u + k1*v + k2) mod 2^32 (strongly universal); pieces are
+ *     concatenated, the first most significant.  The edge lies in nested
+ *     rows 0..d, d = min(leading zeros of ceil((R-1)/p) pieces, R-1); its
+ *     checksum h2 is the first 32 bits of ceil(32/p) pieces.  Key word w of
+ *     column col = 7k+j is the low half of SplitMix64 output 256*col + w of
+ *     the seed; words 0..127 feed the depth pieces, 128..255 the checksum's.
  */
 #ifndef GZ_H
 #define GZ_H
@@ -59,8 +68,9 @@ enum {
 /* Tuning knobs; a zero field takes the built-in default. */
 typedef struct {
     uint32_t chunk_log2;    /* updates processed per partition pass = 2^chunk_log2 (default 24) */
-    uint32_t kernel;        /* GZ_KERNEL_BATCHED or GZ_KERNEL_PLAIN */
-    uint32_t smem_rows;     /* exact-depth rows staged in shared memory (default 12, max 32) */
+    uint32_t kernel;        /* GZ_KERNEL_BATCHED (V <= 2^21) or GZ_KERNEL_PLAIN (any V) */
+    uint32_t smem_rows;     /* exact-depth rows staged in shared memory (default 16; at most 16
+                               and R-1) */
     uint32_t tile_records;  /* records per work tile of the batched kernel (default 512) */
     uint32_t ctas_per_sm;   /* resident CTAs per SM of the persistent batched kernel (default: max) */
     uint32_t small_segment; /* node segments shorter than this skip shared-memory staging (default 4) */
@@ -73,7 +83,12 @@ typedef struct {
     uint32_t device_sketch_mb; /* HBM for node sketches, MiB (0: all of them in HBM).  When the
                                sketches need more, nodes beyond the budget live in pinned host
                                memory (sketches beyond HBM, below) */
-    uint32_t reserved[3];
+    uint32_t no_pipeline;   /* 1: partition and update every chunk on the handle's stream.  By
+                               default (0) the batched kernel's handles partition chunk i+1 on a
+                               second stream while chunk i's sketch update runs, in a second set
+                               of partition buffers (2 * 2^chunk_log2 * 4 bytes of records more);
+                               handles with sketches beyond HBM never do */
+    uint32_t reserved[2];
 } gz_config;
 
 /* Sketches beyond HBM (the paper's hybrid streaming model of Section 4, with
@@ -202,7 +217,7 @@ gz_status gz_export_sketch(gz_handle *h, uint32_t node_lo, uint32_t node_hi,
 
 /* Checkpoint / resume.  By linearity the node sketches are the whole state of
  * a graph (Section 2.2: the stream is summarised by them), so a checkpoint is
- * a 64-byte header -- magic "GZB3CKP1", version (2), V, K, R, seed, bytes per
+ * a 64-byte header -- magic "GZB3CKP1", version (3), V, K, R, seed, bytes per
  * node sketch -- followed by the raw sketch array (the device form of
  * gz_info).  Both calls
  * are synchronous; buf is host memory owned by the caller.
@@ -219,11 +234,10 @@ gz_status gz_restore(const void *buf, size_t size, const gz_config *cfg, void *s
 /* Geometry and device pointer of the raw sketch array of a handle.  Device
  * form: exact-depth rows (an index is XORed into the one row of its depth; the
  * paper's nested row i is the XOR of rows i..R-1), layout per node: for each
- * k, alpha[row][j] (u64) then gamma'[row][j] (u32), where gamma' keeps the
- * checksum sums before MurmurHash3's final step g ^= g >> 16 (a linear map, so
- * a bucket's checksum sum is gamma' ^ (gamma' >> 16)).  For a handle with
- * sketches beyond HBM the array holds the resident nodes only (a prefix of the
- * node range; NULL when none is resident).  Any output pointer may be NULL. */
+ * k, alpha[row][j] (u64) then gamma[row][j] (u32, the XOR of the checksums
+ * h2 of the row's indices).  For a handle with sketches beyond HBM the device
+ * array holds only part of the nodes, so *sketch_device is set to NULL there.
+ * Any output pointer may be NULL. */
 gz_status gz_info(gz_handle *h, uint32_t *V, uint32_t *K, uint32_t *R,
                   size_t *node_bytes, void **sketch_device);
 
@@ -335,19 +349,22 @@ gz_status gz_server_stats_read(gz_server *s, gz_server_stats *out);
  * call of this function by the same thread. */
 const char *gz_server_last_error(gz_server *s);
 
-/* Allocation-free ingestion (the paper has no counterpart: this serves
- * callers that cannot allocate device memory).  Code running while a stream is
- * captured into a CUDA graph cannot call cudaMalloc without breaking the
- * capture; a host whose device memory belongs to another allocator cannot let
- * a library allocate behind its back; a latency-bound loop may not take the
- * driver's allocation lock.  This call applies a batch of updates like
+/* Allocation-free ingestion (the paper has no counterpart).  Some callers
+ * cannot let a library call cudaMalloc: a host framework whose caching
+ * allocator owns the device memory and must account for every byte (an
+ * allocation behind its back can fail, or fragment its pool); a latency-bound
+ * loop in which cudaMalloc, which may synchronise the device and takes a
+ * driver lock, is not allowed.  This call applies a batch of updates like
  * gz_edge_update but allocates and frees nothing: its scratch is a fixed
  * array of about 10 MB in the library's static device memory, which every GPU
  * that loads the library holds until the process exits.
- *   sketch : device, V*K*84*R bytes of node sketches in the device form of
- *            gz_info (per node, for each k, alpha[R][7] u64 then
- *            gamma'[R][7] u32), zeroed for the empty graph; e.g. the array of
- *            a handle from gz_info, or memory the caller owns.
+ *   sketch : device, all V*K*84*R bytes of node sketches in the device form
+ *            of gz_info (per node, for each k, alpha[R][7] u64 then
+ *            gamma[R][7] u32), zeroed for the empty graph: memory the caller
+ *            owns, or the array of an all-HBM handle from gz_info.  An array
+ *            holding fewer nodes (gz_info reports NULL for a handle with
+ *            sketches beyond HBM) is not valid: the kernel would write past
+ *            its end.
  *   V, seed: vertex count (2 <= V <= GZ_NOALLOC_MAX_V) and the hash seed the
  *            sketches were built with.
  *   u, v   : device, n updates (n <= GZ_NOALLOC_MAX_UPDATES), same meaning and
@@ -358,16 +375,35 @@ const char *gz_server_last_error(gz_server *s);
  *            (the sketches are then incomplete), else 0.
  *   stream : cudaStream_t of all the work (NULL = default stream).
  * Returns GZ_EINVAL (nothing queued) for V or n beyond the limits or null
- * pointers, GZ_ECUDA when a CUDA call fails.  The first call on a device sets
- * up that device (it looks up the scratch array's device address); make that
- * first call before any stream capture begins.  All calls share the one
- * scratch array, so calls that overlap on the GPU race: issue them on one
- * stream, or order them. */
+ * pointers, GZ_ECUDA when a CUDA call fails: the set-up and the occupancy
+ * query run before anything is queued, so a failure there leaves everything
+ * untouched; a failure after the update kernel was queued leaves the sketches
+ * unknown.  The status word is written only when GZ_OK is returned.  An error
+ * left pending by earlier, unrelated work of the calling thread is cleared on
+ * entry and not reported.  The first call on a device sets up
+ * that device (it looks up the scratch array's device address and the update
+ * kernel's occupancy); make that first call before any stream capture
+ * begins.  All calls share the one scratch array, which keeps the last call's
+ * contents (each call clears what must start at zero), so calls that overlap
+ * on the GPU race: issue them on one stream, or order them. */
 #define GZ_NOALLOC_MAX_V (1u << 17)
 #define GZ_NOALLOC_MAX_UPDATES (1ull << 20)
 gz_status gz_sketch_update_noalloc(void *sketch, uint32_t V, uint64_t seed,
                                    const uint32_t *u, const uint32_t *v, size_t n,
                                    uint32_t *status, void *stream);
+
+/* Bound of the update kernel's waits, for testing the timeout path.  The
+ * batched kernel's warps hand tiles to each other through shared-memory
+ * barriers, and every wait on one is bounded: at most `polls` polls, each of
+ * which may suspend the thread for up to about suspend_ns nanoseconds
+ * (defaults 2^22 and 1000).  A wait that runs out makes the kernel stop and
+ * report: the next gz_sync, query or export returns GZ_ETIMEOUT (the
+ * allocation-free call sets status 2), and the sketches are incomplete until
+ * gz_reset or a restore.  With polls = 1 and suspend_ns = 0 the waits run out
+ * almost at once, so a test can drive that path without any GPU fault.
+ * polls = 0 restores the defaults.  h = NULL sets the bound of the
+ * allocation-free entry point on the current device.  Synchronous. */
+gz_status gz_set_wait_limit(gz_handle *h, uint32_t polls, uint32_t suspend_ns);
 
 /* Human-readable reason of the last non-OK status of h (never NULL); with
  * h == NULL, the reason the calling thread's last gz_create failed. */
@@ -377,16 +413,17 @@ const char *gz_last_error(gz_handle *h);
 /* Single-vector l0 sketches, for the micro-benchmark of Fig. l0speedup: the
  * standard l0 sampler of Fig. agm_code (Section 3.1) beside CubeSketch
  * (Fig. cube_code) on a plain vector of length n.  Both use 7 columns and
- * R = ceil(log2 n) rows, column keys a_j = SM(seed,3j)|1, b_j = SM(seed,3j+1),
- * c_j = SM(seed,3j+2) (SplitMix64), and put position x into rows 0..d,
+ * R = ceil(log2 n) rows, column keys a_j = SM(seed,5j)|1, b_j = SM(seed,5j+1),
+ * c0_j, c1_j, c2_j = SM(seed,5j+2..5j+4) (SplitMix64, the node sketches'
+ * schedule), and put position x into rows 0..d,
  * d = min(clz64(a_j*x + b_j), R-1) (nested rows, as in both figures).
  *   GZ_L0_CUBE     bucket (alpha u64, gamma u32): alpha ^= x,
- *                  gamma ^= fmix32(fold(x) ^ lo32(c_j)).
+ *                  gamma ^= ((c0_j*lo32(x) + c1_j*hi32(x) + c2_j) mod 2^64) >> 32.
  *                  Layout per sketch: alpha[7][R] then gamma[7][R], padded
  *                  to a multiple of 8 bytes (84R rounded up).
  *   GZ_L0_STANDARD bucket (a, b, c), u64 each: a += x*delta, b += delta
  *                  (two's complement), c = (c + delta * r_j^x) mod p with
- *                  p = 2^61 - 1 and r_j = 1 + c_j mod (p - 1).
+ *                  p = 2^61 - 1 and r_j = 1 + c0_j mod (p - 1).
  *                  Layout per sketch: a[7][R], b[7][R], c[7][R]. */
 #define GZ_L0_CUBE 0
 #define GZ_L0_STANDARD 1
@@ -407,12 +444,13 @@ gz_status gz_l0_geometry(uint64_t n, uint32_t *rows, uint32_t *bytes_cube, uint3
 gz_status gz_l0_update(int kind, uint64_t n, uint64_t seed, uint32_t sketches, uint32_t m,
                        const uint64_t *x, const int32_t *delta, void *buckets, void *stream);
 
-/* Measured integer throughput of the current device, the ceiling of the
+/* Measured integer throughput of the current device, the ceilings of the
  * batched update kernel (its work per (record, column) pair is integer only):
  * kind 0 = 32-bit multiply-add, 1 = three-input logic op, 2 = the two
- * interleaved.  *ops_per_s = thread-instructions per second over all SMs, the
- * best of nine timed launches of some tens of milliseconds each (after one untimed).  Synchronous;
- * uses its own stream and a 4-byte device allocation. */
+ * interleaved, 3 = leading-zero count, 4 = 32-bit shared-memory atomic XOR.
+ * *ops_per_s = thread-operations per second over all SMs, the best of nine
+ * timed launches of a few milliseconds each (after one untimed).
+ * Synchronous; uses its own stream and a 4-byte device allocation. */
 gz_status gz_int_peak(int kind, double *ops_per_s);
 
 const char *gz_version(void);

@@ -45,7 +45,8 @@ class Config(ctypes.Structure):
         ("smem_mode", ctypes.c_uint32),
         ("no_graph", ctypes.c_uint32),
         ("device_sketch_mb", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 3),
+        ("no_pipeline", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 2),
     ]
 
 
@@ -125,6 +126,7 @@ _SIGNATURES = {
     "gz_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                ctypes.c_void_p, ctypes.c_void_p]),
     "gz_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "gz_set_wait_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32]),
     "gz_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gz_gen_kron_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gz_gen_kron_num_chunks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -182,7 +184,7 @@ def geometry(V: int) -> tuple[int, int]:
 
 def _config(kernel: str = "batched", chunk_log2: int = 0, smem_rows: int = 0, tile_records: int = 0,
             ctas_per_sm: int = 0, small_segment: int = 0, smem_mode: int = 0, no_graph: int = 0,
-            device_sketch_mb: int = 0) -> Config:
+            device_sketch_mb: int = 0, no_pipeline: int = 0) -> Config:
     cfg = Config()
     cfg.chunk_log2 = chunk_log2
     cfg.kernel = KERNELS[kernel]
@@ -193,6 +195,7 @@ def _config(kernel: str = "batched", chunk_log2: int = 0, smem_rows: int = 0, ti
     cfg.smem_mode = smem_mode
     cfg.no_graph = no_graph
     cfg.device_sketch_mb = device_sketch_mb
+    cfg.no_pipeline = no_pipeline
     return cfg
 
 
@@ -206,10 +209,12 @@ def memory_bytes(V: int, **cfg) -> int:
 
 
 def int_peak(kind: str = "mixed") -> float:
-    """Measured integer thread-instructions/s of the current device
-    (gz_int_peak): "imad" (32-bit multiply-add), "lop3" (logic) or "mixed"."""
+    """Measured integer thread-operations/s of the current device
+    (gz_int_peak): "imad" (32-bit multiply-add), "lop3" (logic), "mixed" (the
+    two interleaved), "clz" (leading-zero count) or "atom_shared" (32-bit
+    shared-memory atomic XOR)."""
     out = ctypes.c_double()
-    k = {"imad": 0, "lop3": 1, "mixed": 2}[kind]
+    k = {"imad": 0, "lop3": 1, "mixed": 2, "clz": 3, "atom_shared": 4}[kind]
     st = lib().gz_int_peak(k, ctypes.byref(out))
     if st != GZ_OK:
         raise GzError(st, "gz_int_peak failed")
@@ -278,10 +283,10 @@ class Graph:
     def __init__(self, V: int, seed: int = 0, *, kernel: str = "batched", chunk_log2: int = 0,
                  smem_rows: int = 0, tile_records: int = 0, ctas_per_sm: int = 0,
                  small_segment: int = 0, smem_mode: int = 0, no_graph: int = 0, device_sketch_mb: int = 0,
-                 stream=None):
+                 no_pipeline: int = 0, stream=None):
         cfg = _config(kernel=kernel, chunk_log2=chunk_log2, smem_rows=smem_rows, tile_records=tile_records,
                       ctas_per_sm=ctas_per_sm, small_segment=small_segment, smem_mode=smem_mode,
-                      no_graph=no_graph, device_sketch_mb=device_sketch_mb)
+                      no_graph=no_graph, device_sketch_mb=device_sketch_mb, no_pipeline=no_pipeline)
         self._h = ctypes.c_void_p()
         s = _current_stream() if stream is None else stream
         st = lib().gz_create(V, seed & ((1 << 64) - 1), ctypes.byref(cfg), ctypes.c_void_p(s),
@@ -414,6 +419,10 @@ class Graph:
         g.K, g.R = info["K"], info["R"]
         g.seed = int(np.frombuffer(buf[24:32].tobytes(), np.uint64)[0])
         return g
+
+    def set_wait_limit(self, polls: int, suspend_ns: int = 0):
+        """Bound the update kernel's waits (polls = 0: the defaults)."""
+        self._check(lib().gz_set_wait_limit(self._h, polls, suspend_ns), "gz_set_wait_limit")
 
     def profile_enable(self, on: bool = True):
         self._check(lib().gz_profile_enable(self._h, 1 if on else 0), "gz_profile_enable")

@@ -1,8 +1,8 @@
 """Autotuner of the batched ingestion path.
 
 Picks, for one GPU model and one V, the knobs of gz_config that change speed
-but never results: the delta-update mode in shared memory (shared atomics or
-load-xor-store), the records per work tile, the exact-depth rows staged in
+but never results: the delta-update mode in shared memory (32-bit shared
+atomics or load-xor-store), the records per work tile, the exact-depth rows staged in
 shared memory, the resident CTAs per SM of the persistent kernel and the
 partition chunk (updates per partition pass).  The search is coordinate
 descent from the built-in defaults over a sample of the caller's device
@@ -20,11 +20,11 @@ import os
 SPACE = {
     "smem_mode": [1, 2],
     "tile_records": [256, 512, 1024, 2048],
-    "smem_rows": [10, 12, 16],
+    "smem_rows": [12, 14, 16],
     "ctas_per_sm": [0, 2, 3],
     "chunk_log2": [24, 25, 26, 27],
 }
-DEFAULT = {"smem_mode": 1, "tile_records": 512, "smem_rows": 12, "ctas_per_sm": 0, "chunk_log2": 26}
+DEFAULT = {"smem_mode": 1, "tile_records": 512, "smem_rows": 16, "ctas_per_sm": 0, "chunk_log2": 26}
 
 CACHE = os.environ.get("GZ_TUNE_CACHE",
                        os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_configs.json"))

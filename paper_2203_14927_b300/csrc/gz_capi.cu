@@ -68,7 +68,7 @@ void tier_geometry(uint32_t V, uint64_t node_bytes, uint32_t budget_mb, uint32_t
 }
 
 static size_t scratch_bytes(uint32_t V, uint64_t chunk) {
-    return (size_t)3 * (V + 1) * 4 + (size_t)2 * chunk * 4 + 64;
+    return (size_t)4 * (V + 1) * 4 + (size_t)2 * chunk * 4 + 64;
 }
 
 }  // namespace gz
@@ -106,7 +106,10 @@ gz_status gz_memory_bytes(uint32_t V, const gz_config* cfg, size_t* bytes) {
     size_t tier = 0;
     if (res_nodes < V)  // the shard slots and the per-round query gather array
         tier = gz_handle::kTierSlots * (size_t)shard_nodes * node_bytes + (size_t)V * 84ull * R;
-    *bytes = (size_t)res_nodes * node_bytes + tier + (size_t)K * 7 * 24 + scratch_bytes(V, chunk);
+    size_t pipe = 0;  // the second partition buffer set of a pipelined handle
+    if (res_nodes == V && (!cfg || (cfg->kernel == GZ_KERNEL_BATCHED && !cfg->no_pipeline)))
+        pipe = scratch_bytes(V, chunk) + (size_t)(2 * chunk / 256 + 2) * 4;
+    *bytes = (size_t)res_nodes * node_bytes + tier + pipe + (size_t)K * 7 * 4 * kKeyWords + scratch_bytes(V, chunk);
     return GZ_OK;
 }
 
@@ -139,18 +142,17 @@ gz_status gz_create(uint32_t V, uint64_t seed, const gz_config* cfg, void* strea
         delete h;
         return s;
     }
-    // keys: a (odd), b, c per column, from SplitMix64 outputs 3*col, 3*col+1, 3*col+2
+    // keys: word w of column col is lo32 of SplitMix64 output 256*col + w,
+    // stored word-major (word w of every column at hk[w * ncol + col])
     const size_t ncol = h->ncol;
-    uint64_t* hk = new (std::nothrow) uint64_t[3 * ncol];
+    uint32_t* hk = new (std::nothrow) uint32_t[(size_t)kKeyWords * ncol];
     if (!hk) {
         delete h;
         return GZ_ENOMEM;
     }
-    for (size_t col = 0; col < ncol; ++col) {
-        hk[col] = splitmix_nth(seed, 3 * col) | 1ull;
-        hk[ncol + col] = splitmix_nth(seed, 3 * col + 1);
-        hk[2 * ncol + col] = splitmix_nth(seed, 3 * col + 2);
-    }
+    for (size_t col = 0; col < ncol; ++col)
+        for (uint32_t w = 0; w < kKeyWords; ++w)
+            hk[w * ncol + col] = (uint32_t)splitmix_nth(seed, (uint64_t)kKeyWords * col + w);
     // Stream-ordered allocations: creating or destroying a handle never
     // synchronises the whole device (cudaFree would), so a server can admit
     // and release graphs while other graphs' work runs.
@@ -182,14 +184,15 @@ gz_status gz_create(uint32_t V, uint64_t seed, const gz_config* cfg, void* strea
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->tier_in, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->tier_out, cudaStreamNonBlocking);
     }
-    if (e == cudaSuccess) e = cudaMallocAsync(&h->d_keys, 3 * ncol * sizeof(uint64_t), as);
+    if (e == cudaSuccess) e = cudaMallocAsync(&h->d_keys, kKeyWords * ncol * sizeof(uint32_t), as);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->d_keys, hk, 3 * ncol * sizeof(uint64_t), cudaMemcpyHostToDevice, as);
+        e = cudaMemcpyAsync(h->d_keys, hk, kKeyWords * ncol * sizeof(uint32_t), cudaMemcpyHostToDevice, as);
     if (e == cudaSuccess) e = cudaStreamSynchronize(as);  // hk is freed below
     delete[] hk;
     if (e == cudaSuccess) e = cudaMallocAsync(&h->d_counts, (size_t)(V + 1) * 4, as);
     if (e == cudaSuccess) e = cudaMallocAsync(&h->d_offsets, (size_t)(V + 1) * 4, as);
     if (e == cudaSuccess) e = cudaMallocAsync(&h->d_cursor, (size_t)(V + 1) * 4, as);
+    if (e == cudaSuccess) e = cudaMallocAsync(&h->d_cursor_hi, (size_t)(V + 1) * 4, as);
     if (e == cudaSuccess && h->cfg.kernel == GZ_KERNEL_BATCHED)
         e = cudaMallocAsync(&h->d_records, (size_t)2 * h->chunk * 4, as);
     if (e == cudaSuccess) e = cudaMallocAsync(&h->d_flags, 32, as);  // [4], [5]: node window
@@ -213,16 +216,19 @@ gz_status gz_create(uint32_t V, uint64_t seed, const gz_config* cfg, void* strea
 
 gz_status gz_destroy(gz_handle* h) {
     if (!h) return GZ_EINVAL;
+    if (h->part_stream) cudaStreamSynchronize(h->part_stream);
     if (h->tier_in) cudaStreamSynchronize(h->tier_in);
     if (h->tier_out) cudaStreamSynchronize(h->tier_out);
     cudaStreamSynchronize(h->stream);
-    void* ptrs[] = {h->d_sketch, h->d_keys, h->d_counts, h->d_offsets, h->d_cursor, h->d_records,
+    void* ptrs[] = {h->d_sketch, h->d_keys, h->d_counts, h->d_offsets, h->d_cursor, h->d_cursor_hi, h->d_records,
                     h->d_stage, h->d_flags, h->q_label, h->q_parent, h->q_count, h->q_off,
                     h->q_cursor, h->q_members, h->q_roots, h->q_target, h->q_slot,
                     h->q_F, h->q_F2,
                     h->q_M, h->q_M2, h->q_flag, h->q_pos, h->q_forest, h->q_ctr, h->q_res,
                     h->q_acc, h->q_trace, h->d_stats, h->d_scan_tmp, h->d_tile_node, h->d_decode,
-                    h->d_slot[0], h->d_slot[1], h->d_slot[2], h->d_gather};
+                    h->d_slot[0], h->d_slot[1], h->d_slot[2], h->d_gather,
+                    h->pset1.counts, h->pset1.offsets, h->pset1.cursor, h->pset1.cursor_hi, h->pset1.records,
+                    h->pset1.tile_node, h->pset1.flags};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, h->stream);
     delete[] h->h_ctr;
@@ -239,13 +245,19 @@ gz_status gz_destroy(gz_handle* h) {
         if (h->ev_tdone[b]) cudaEventDestroy(h->ev_tdone[b]);
         if (h->ev_tout[b]) cudaEventDestroy(h->ev_tout[b]);
     }
+    for (int b = 0; b < 2; ++b) {
+        if (h->ev_part[b]) cudaEventDestroy(h->ev_part[b]);
+        if (h->ev_upd[b]) cudaEventDestroy(h->ev_upd[b]);
+    }
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->part_stream) cudaStreamDestroy(h->part_stream);
     if (h->tier_in) cudaStreamDestroy(h->tier_in);
     if (h->tier_out) cudaStreamDestroy(h->tier_out);
     cudaStreamSynchronize(h->stream);
     if (h->h_sketch) cudaFreeHost(h->h_sketch);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->graph) cudaGraphDestroy(h->graph);
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 4; ++i)
         if (h->cap_ev[i]) cudaEventDestroy(h->cap_ev[i]);
     delete h;
     return GZ_OK;
@@ -274,6 +286,8 @@ gz_status gz_edge_update(gz_handle* h, const uint32_t* u, const uint32_t* v, siz
     if (n == 0) return GZ_OK;
     if (!u || !v) return set_error(h, GZ_EINVAL, "null update arrays");
     if (on_device) {
+        // the inputs are ready once the handle stream's earlier work is done
+        input_stream(h, nullptr);
         for (size_t off = 0; off < n; off += h->chunk) {
             const uint64_t m = std::min<uint64_t>(h->chunk, n - off);
             gz_status s = ingest_batch(h, u + off, v + off, m);
@@ -282,7 +296,7 @@ gz_status gz_edge_update(gz_handle* h, const uint32_t* u, const uint32_t* v, siz
         return GZ_OK;
     }
     // Host input: two staging buffers; the copy of chunk i+1 (copy stream)
-    // overlaps the processing of chunk i (handle stream).
+    // overlaps the processing of chunk i.
     gz_status s = host_path_setup(h);
     if (s != GZ_OK) return s;
     cudaError_t e = cudaSuccess;
@@ -292,17 +306,17 @@ gz_status gz_edge_update(gz_handle* h, const uint32_t* u, const uint32_t* v, siz
         const int b = (int)(i & 1);
         uint32_t* su = h->d_stage + (size_t)b * 2 * h->chunk;
         uint32_t* sv = su + h->chunk;
-        // buffer b is free once the kernels of its previous chunk (this call
-        // or an earlier one) are done; an event never recorded is complete
+        // buffer b is free once the partition of its previous chunk (this call
+        // or an earlier one) has read it; an event never recorded is complete
         e = cudaStreamWaitEvent(h->copy_stream, h->ev_free[b], 0);
         if (e == cudaSuccess) e = cudaMemcpyAsync(su, u + off, m * 4, cudaMemcpyHostToDevice, h->copy_stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(sv, v + off, m * 4, cudaMemcpyHostToDevice, h->copy_stream);
         if (e == cudaSuccess) e = cudaEventRecord(h->ev_copied[b], h->copy_stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0);
         if (e != cudaSuccess) return cuda_check(h, e, "update copy");
+        cudaStream_t in = input_stream(h, h->ev_copied[b]);
         s = ingest_batch(h, su, sv, m);
         if (s != GZ_OK) return s;
-        e = cudaEventRecord(h->ev_free[b], h->stream);
+        e = cudaEventRecord(h->ev_free[b], in);
         if (e != cudaSuccess) return cuda_check(h, e, "update event");
     }
     // the caller may reuse its host buffers once every copy has landed
@@ -318,15 +332,19 @@ gz_status gz_edge_update_idx(gz_handle* h, const uint64_t* idx, size_t n, int on
     cudaError_t e = cudaSuccess;
     if (!h->d_decode) {
         e = cudaMallocAsync(&h->d_decode, (size_t)2 * h->chunk * 4, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // the partition stream uses it
         if (e != cudaSuccess) return cuda_check(h, e, "decode buffer");
     }
     uint32_t* du = h->d_decode;
     uint32_t* dv = du + h->chunk;
     gz_status s;
+    // the decode runs where the partition reads its output (the partition
+    // stream of a pipelined handle), so one decode buffer serves every chunk
     if (on_device) {
+        cudaStream_t in = input_stream(h, nullptr);
         for (size_t off = 0; off < n; off += h->chunk) {
             const uint64_t m = std::min<uint64_t>(h->chunk, n - off);
-            if ((s = decode_idx(h, idx + off, m, du, dv)) != GZ_OK) return s;
+            if ((s = decode_idx(h, idx + off, m, du, dv, in)) != GZ_OK) return s;
             if ((s = ingest_batch(h, du, dv, m)) != GZ_OK) return s;
         }
         return GZ_OK;
@@ -342,10 +360,10 @@ gz_status gz_edge_update_idx(gz_handle* h, const uint64_t* idx, size_t n, int on
         e = cudaStreamWaitEvent(h->copy_stream, h->ev_free[b], 0);
         if (e == cudaSuccess) e = cudaMemcpyAsync(sb, idx + off, m * 8, cudaMemcpyHostToDevice, h->copy_stream);
         if (e == cudaSuccess) e = cudaEventRecord(h->ev_copied[b], h->copy_stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0);
         if (e != cudaSuccess) return cuda_check(h, e, "update copy");
-        if ((s = decode_idx(h, sb, m, du, dv)) != GZ_OK) return s;
-        e = cudaEventRecord(h->ev_free[b], h->stream);
+        cudaStream_t in = input_stream(h, h->ev_copied[b]);
+        if ((s = decode_idx(h, sb, m, du, dv, in)) != GZ_OK) return s;
+        e = cudaEventRecord(h->ev_free[b], in);
         if (e != cudaSuccess) return cuda_check(h, e, "update event");
         if ((s = ingest_batch(h, du, dv, m)) != GZ_OK) return s;
     }
@@ -357,13 +375,19 @@ gz_status gz_edge_update_idx(gz_handle* h, const uint64_t* idx, size_t n, int on
 // flags[2]: sticky "a batch was discarded"; flags[3]: sticky "a bounded wait
 // of the update kernel ran out" (its tile may be partly applied)
 static gz_status check_rejected(gz_handle* h) {
-    uint32_t f[2] = {0, 0};
+    // every partition is followed by its update on the handle's stream, so
+    // once that stream is done both buffer sets' flags are final
+    uint32_t f[4] = {0, 0, 0, 0};
     cudaError_t e = cudaMemcpyAsync(f, h->d_flags + 2, 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && h->pset1.flags)
+        e = cudaMemcpyAsync(f + 2, h->pset1.flags + 2, 8, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_check(h, e, "sync");
     if (f[0] || f[1]) cudaMemsetAsync(h->d_flags + 2, 0, 8, h->stream);
-    if (f[1]) return set_error(h, GZ_ETIMEOUT, "a bounded wait in the update kernel ran out; the sketches are incomplete");
-    if (f[0])
+    if (f[2] || f[3]) cudaMemsetAsync(h->pset1.flags + 2, 0, 8, h->stream);
+    if (f[1] || f[3])
+        return set_error(h, GZ_ETIMEOUT, "a bounded wait in the update kernel ran out; the sketches are incomplete");
+    if (f[0] || f[2])
         return set_error(h, GZ_EINVAL, "an update batch held a self loop or a vertex id >= V and was discarded");
     return GZ_OK;
 }
@@ -462,10 +486,14 @@ gz_status gz_profile_read(gz_handle* h, gz_profile* out) {
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_check(h, e, "profile sync");
     double part = 0, upd = 0;
-    for (size_t i = 0; i + 2 < h->ev_used; i += 3) {
+    if (h->part_stream) {
+        e = cudaStreamSynchronize(h->part_stream);
+        if (e != cudaSuccess) return cuda_check(h, e, "profile sync");
+    }
+    for (size_t i = 0; i + 3 < h->ev_used; i += 4) {
         float a = 0, b = 0;
         e = cudaEventElapsedTime(&a, h->ev_pool[i], h->ev_pool[i + 1]);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, h->ev_pool[i + 1], h->ev_pool[i + 2]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, h->ev_pool[i + 2], h->ev_pool[i + 3]);
         if (e != cudaSuccess) return cuda_check(h, e, "cudaEventElapsedTime");
         part += a;
         upd += b;
@@ -492,6 +520,9 @@ struct CkptHeader {
 };
 static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
 const char kMagic[8] = {'G', 'Z', 'B', '3', 'C', 'K', 'P', '1'};
+// 3: sketches of the piece hashes (32-bit multiply-add-shift pieces on the
+// endpoint pair); version 2 held another hash family
+constexpr uint32_t kCkptVersion = 3;
 }  // namespace
 
 gz_status gz_checkpoint_bytes(gz_handle* h, size_t* bytes) {
@@ -509,7 +540,7 @@ gz_status gz_checkpoint(gz_handle* h, void* buf, size_t size) {
     CkptHeader hd;
     std::memset(&hd, 0, sizeof(hd));
     std::memcpy(hd.magic, kMagic, 8);
-    hd.version = 2;  // 2: gamma words hold gamma' (checksum sums before the final xorshift)
+    hd.version = kCkptVersion;
     hd.V = h->V;
     hd.K = h->K;
     hd.R = h->R;
@@ -533,7 +564,7 @@ gz_status gz_restore(const void* buf, size_t size, const gz_config* cfg, void* s
     CkptHeader hd;
     std::memcpy(&hd, buf, sizeof(hd));
     uint32_t K, R;
-    if (std::memcmp(hd.magic, kMagic, 8) != 0 || hd.version != 2 || !gz::geometry(hd.V, &K, &R) ||
+    if (std::memcmp(hd.magic, kMagic, 8) != 0 || hd.version != kCkptVersion || !gz::geometry(hd.V, &K, &R) ||
         K != hd.K || R != hd.R || hd.node_bytes != (uint64_t)K * 84u * R ||
         size < sizeof(hd) + (size_t)hd.V * hd.node_bytes)
         return GZ_EINVAL;
@@ -560,7 +591,8 @@ gz_status gz_info(gz_handle* h, uint32_t* V, uint32_t* K, uint32_t* R, size_t* n
     if (K) *K = h->K;
     if (R) *R = h->R;
     if (node_bytes) *node_bytes = h->node_bytes;
-    if (sketch_device) *sketch_device = h->d_sketch;
+    // a tiered handle's device array holds only the resident nodes
+    if (sketch_device) *sketch_device = h->tiered ? nullptr : h->d_sketch;
     return GZ_OK;
 }
 

@@ -211,8 +211,8 @@ gz_status gz_gen_kron_chunk(gz_gen* g, uint64_t c, uint32_t* u, uint32_t* v, uin
     cudaStream_t s = g->stream;
     const uint32_t nb = (uint32_t)g->nb;
     k_gen_count<<<nb, kThreads, 0, s>>>(a, g->d_cnt, g->d_cnt + nb);
-    gz::launch_scan(g->d_cnt, g->d_off, nullptr, nb, s, g->d_scan_tmp);
-    gz::launch_scan(g->d_cnt + nb, g->d_off + nb + 1, nullptr, nb, s, g->d_scan_tmp);
+    gz::launch_scan(g->d_cnt, g->d_off, nullptr, nullptr, nb, s, g->d_scan_tmp);
+    gz::launch_scan(g->d_cnt + nb, g->d_off + nb + 1, nullptr, nullptr, nb, s, g->d_scan_tmp);
     cudaError_t e = cudaMemcpyAsync(&g->h_tot[0], g->d_off + nb, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&g->h_tot[1], g->d_off + nb + 1 + nb, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -11,6 +11,15 @@
 #include "../../include/gz.h"
 #include "gz_internal.cuh"
 
+// The partition buffers of one chunk: counts, offsets, front and back
+// cursors (V+1 each), 2 * 2^chunk_log2 records, the tile table and 8 flag
+// words ([0] batch invalid, [1] tile counter, [2] sticky invalid, [3] sticky
+// timeout, [4..5] node window, [6..7] wait limit).
+struct gz_partset {
+    uint32_t *counts = nullptr, *offsets = nullptr, *cursor = nullptr, *cursor_hi = nullptr, *records = nullptr,
+             *tile_node = nullptr, *flags = nullptr;
+};
+
 struct gz_handle {
     // geometry
     uint32_t V = 0, K = 0, R = 0, ncol = 0;  // ncol = 7K columns
@@ -22,15 +31,17 @@ struct gz_handle {
     int sm_count = 0;
     cudaStream_t stream = nullptr;
 
-    // sketches (exact-depth form) and hash keys (3 arrays of 7K)
+    // sketches (exact-depth form) and hash keys (kKeyWords 32-bit words per
+    // column, word-major)
     uint8_t* d_sketch = nullptr;
-    uint64_t* d_keys = nullptr;
+    uint32_t* d_keys = nullptr;
 
     // ingestion scratch
     uint64_t chunk = 0;            // updates per partition pass
     uint32_t* d_counts = nullptr;  // V+1
     uint32_t* d_offsets = nullptr; // V+1
-    uint32_t* d_cursor = nullptr;  // V
+    uint32_t* d_cursor = nullptr;  // V: front cursors; after the scatter, the split of every segment
+    uint32_t* d_cursor_hi = nullptr;  // V: back cursors of the scatter
     uint32_t* d_records = nullptr; // 2*chunk
     uint32_t* d_tile_node = nullptr; // first node of every record tile (2*chunk/tile + 2)
     uint32_t* d_stage = nullptr;   // 2 buffers x (u, v) x chunk, host-input staging (lazy)
@@ -39,11 +50,23 @@ struct gz_handle {
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
     uint32_t* d_flags = nullptr;   // [0] batch invalid, [1] work counter, [2] sticky invalid, [4..5] node window
     uint32_t* d_scan_tmp = nullptr; // ceil((V+1)/1024) tile sums of the scans
+    gz::PieceGeo geo{};            // hash piece width and counts (gz_internal.cuh)
     uint32_t block = 0;            // columns padded to a warp multiple
     uint32_t smem_rows = 0, tile = 0, small_seg = 0, batched_grid = 0;
     uint32_t delta_mode = 1;       // batched kernel's delta update: 0 load-xor-store, 1 shared atomics
     uint64_t batches_done = 0;     // partition passes issued (graph capture after 8)
     size_t batched_smem = 0;
+
+    // pipelined ingest: chunk i+1 is partitioned on part_stream into the other
+    // buffer set while chunk i's update runs on the handle's stream.  Set 0 is
+    // the d_* buffers above, set 1 is pset1.  ev_part[b]: set b partitioned;
+    // ev_upd[b]: set b's update done (the set may be partitioned again);
+    // ev_in: the caller's inputs are ready (recorded at each ingest call).
+    bool pipelined = false;
+    int pipe_next = 0;
+    gz_partset pset1;
+    cudaStream_t part_stream = nullptr;
+    cudaEvent_t ev_part[2] = {nullptr, nullptr}, ev_upd[2] = {nullptr, nullptr}, ev_in = nullptr;
 
     // sketches beyond HBM: nodes [0, res_nodes) in d_sketch, the others in
     // pinned host memory h_sketch, streamed shard by shard through two slots
@@ -77,12 +100,12 @@ struct gz_handle {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     cudaGraphNode_t node_validate = nullptr, node_scatter = nullptr;
-    cudaGraphNode_t node_ev[3] = {nullptr, nullptr, nullptr};
-    cudaEvent_t cap_ev[3] = {nullptr, nullptr, nullptr};
+    cudaGraphNode_t node_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t cap_ev[4] = {nullptr, nullptr, nullptr, nullptr};
 
     // profiling window (gz_profile_enable / gz_profile_read)
     bool prof = false;
-    std::vector<cudaEvent_t> ev_pool;  // triples: before partition, before update, after update
+    std::vector<cudaEvent_t> ev_pool;  // quadruples: before/after partition, before/after update
     size_t ev_used = 0;
     uint64_t prof_batches = 0, prof_updates = 0, launches = 0;
     uint64_t* d_stats = nullptr;  // [0] rows flushed, [1] deep column updates
@@ -98,8 +121,15 @@ gz_status cuda_check(gz_handle* h, cudaError_t e, const char* what);
 // ingestion (gz_ingest.cu)
 gz_status ingest_setup(gz_handle* h);
 gz_status ingest_batch(gz_handle* h, const uint32_t* d_u, const uint32_t* d_v, uint64_t n);
-// packed indices min*V+max -> (u, v); non-canonical indices become (0, 0)
-gz_status decode_idx(gz_handle* h, const uint64_t* d_idx, uint64_t n, uint32_t* d_u, uint32_t* d_v);
+// the stream on which the work that reads a call's inputs runs (the partition
+// stream of a pipelined handle, else the handle's stream), made to wait for
+// `ready` (an event of the caller's inputs; null: the handle stream's work so far)
+cudaStream_t input_stream(gz_handle* h, cudaEvent_t ready);
+// partition buffer set b (0 or 1)
+gz_partset part_set(const gz_handle* h, int b);
+// packed indices min*V+max -> (u, v) on stream st; non-canonical indices become (0, 0)
+gz_status decode_idx(gz_handle* h, const uint64_t* d_idx, uint64_t n, uint32_t* d_u, uint32_t* d_v,
+                     cudaStream_t st);
 gz_status export_nested(gz_handle* h, uint32_t lo, uint32_t hi, uint64_t* d_alpha,
                         uint32_t* d_gamma);
 
@@ -122,12 +152,10 @@ gz_status query_setup(gz_handle* h);
 gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* forest_uv,
                   size_t* n_edges, uint32_t* n_cc, gz_query_stats* st);
 
-// profiling: record the next event of the current triple (no-op when disabled)
-gz_status prof_event(gz_handle* h);
 
 // exclusive scan: out[0..n] with out[n] = total; out2 (optional) = copy of out[0..n);
-// tile_scratch holds ceil(n / 1024) u32
-void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* out2, uint32_t n, cudaStream_t s,
+// out3 (optional) = out[1..n] (inclusive sums); tile_scratch holds ceil(n / 1024) u32
+void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* out2, uint32_t* out3, uint32_t n, cudaStream_t s,
                  uint32_t* tile_scratch);
 
 }  // namespace gz

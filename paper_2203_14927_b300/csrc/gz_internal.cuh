@@ -4,13 +4,10 @@
 // Sketch storage ("exact-depth" form).  The paper's CubeSketch keeps NESTED rows:
 // row i of column j holds every index e with h1(e) = 0 mod 2^i (Eq. 1-2), so one
 // update touches rows 0..depth.  On the device each update XORs only row
-// depth = min(#leading zero bits of (a*idx+b), R-1); nested row i is recovered as
-// the XOR of stored rows i..R-1 (a fixed linear map, so merges commute with it).
+// depth (edge_depth below); nested row i is recovered as the XOR of stored rows
+// i..R-1 (a fixed linear map, so merges commute with it).
 //
-// Gamma words hold gamma' (see fmix32_pre below): the paper's checksum sum of a
-// bucket is gamma' ^ (gamma' >> 16).
-//
-// Layout: node-major; per node, K blocks of (alpha[R][7] u64, gamma'[R][7] u32).
+// Layout: node-major; per node, K blocks of (alpha[R][7] u64, gamma[R][7] u32).
 // One CubeSketch (node, k) is therefore a contiguous 84*R-byte block, which is
 // what a Boruvka round reads per node.
 #pragma once
@@ -45,51 +42,62 @@ struct SketchView {
     }
 };
 
-// Per-column keys: depth hash a (odd), b; checksum key c.
+// Hash keys of the node sketches: kKeyWords 32-bit words per CubeSketch column,
+// stored word-major (word w of column col at w[w * ncol + col], so a thread per
+// column loads them coalesced).  Words [0, 128) hold the depth hash h1's
+// pieces, [128, 256) the checksum h2's, three words (k0, k1, k2) per piece.
+constexpr uint32_t kKeyWords = 256;
+constexpr uint32_t kH2Words = 128;
+
 struct Keys {
-    const uint64_t* a;
-    const uint64_t* b;
-    const uint64_t* c;
+    const uint32_t* w;  // kKeyWords * ncol
+    uint32_t ncol;
+    __device__ __forceinline__ uint32_t at(uint32_t word, uint32_t col) const { return w[word * ncol + col]; }
 };
 
-// MurmurHash3's 32-bit finalizer (Appleby 2011), without its last step
-// h ^= h >> 16.  That step is a linear, invertible map L over GF(2)^32, so it
-// commutes with XOR sums: the device keeps gamma' = XOR of fmix32_pre values
-// in every bucket, a bucket's paper checksum gamma is L(gamma'), and a
-// candidate alpha is good iff gamma' == fmix32_pre(fold(alpha) ^ lo32(c)).
-__device__ __forceinline__ uint32_t fmix32_pre(uint32_t h) {
-    h ^= h >> 16;
-    h *= 0x85EBCA6Bu;
-    h ^= h >> 13;
-    h *= 0xC2B2AE35u;
-    return h;
+// Piece geometry for V vertices: L = ceil(log2 V) (every id < 2^L), piece width
+// p = min(16, 33 - L), m1 = ceil((R-1)/p) pieces for h1 (R = 2L) and
+// m2 = ceil(32/p) for h2 (2 for every V <= 2^17).
+struct PieceGeo {
+    uint32_t p, m1, m2;
+};
+
+__host__ __device__ inline PieceGeo piece_geo(uint32_t V) {
+    uint32_t L = 0;
+    while ((1ull << L) < V) ++L;
+    PieceGeo g;
+    g.p = 33 - L < 16 ? 33 - L : 16;
+    g.m1 = (2 * L - 1 + g.p - 1) / g.p;
+    g.m2 = (32 + g.p - 1) / g.p;
+    return g;
 }
 
-// L: stored gamma' -> the checksum sum gamma of Fig. cube_code.
-__device__ __forceinline__ uint32_t gamma_final(uint32_t g) { return g ^ (g >> 16); }
-
-// 32-bit fold of an edge index: lo32 ^ lo32(hi32 * 0x9E3779B9) (the identity
-// below 2^32).
-__device__ __forceinline__ uint32_t fold32(uint64_t idx) {
-    return static_cast<uint32_t>(idx) ^ (static_cast<uint32_t>(idx >> 32) * 0x9E3779B9u);
+// One piece on the endpoint pair (u, v): (k0*u + k1*v + k2) mod 2^32, whose top
+// p bits are the hash bits (multiply-add-shift over a vector of two L-bit words,
+// Dietzfelbinger 1996 / Thorup 2015: strongly universal since 32 >= L + p - 1).
+// Concatenated pieces (the first most significant), left-aligned in 64 bits.
+__device__ __forceinline__ uint64_t pieces_cat(const Keys& k, uint32_t base, uint32_t col, uint32_t m,
+                                               uint32_t p, uint32_t u, uint32_t v) {
+    uint64_t acc = 0;
+    for (uint32_t i = 0; i < m; ++i) {
+        const uint32_t t = k.at(base + 3 * i, col) * u + k.at(base + 3 * i + 1, col) * v + k.at(base + 3 * i + 2, col);
+        acc |= (uint64_t)(t >> (32 - p)) << (64 - p * (i + 1));
+    }
+    return acc;
 }
 
-// Stored form of checksum h2 (Fig. cube_code) of one index:
-// h2(idx) = L(checksum_pre(c, idx)) = fmix32(fold(idx) ^ lo32(c)).
-__device__ __forceinline__ uint32_t checksum_pre(uint64_t c, uint64_t idx) {
-    return fmix32_pre(fold32(idx) ^ static_cast<uint32_t>(c));
-}
-
-// Depth hash: t = a*idx + b (mod 2^64), Dietzfelbinger's multiply-add-shift
-// family; an index lies in nested row i iff the top i bits of t are zero.
-__device__ __forceinline__ uint64_t depth_word(uint64_t a, uint64_t b, uint64_t idx) {
-    return a * idx + b;
-}
-
-// Exact depth = min(leading zeros of t, R-1).
-__device__ __forceinline__ uint32_t exact_depth(uint64_t t, uint32_t R) {
-    uint32_t d = static_cast<uint32_t>(__clzll(static_cast<long long>(t)));
+// Exact depth of edge (u, v) in column col: the leading zeros of h1's pieces,
+// capped at R-1 (an index lies in nested rows 0..depth, Fig. cube_code).
+__device__ __forceinline__ uint32_t edge_depth(const Keys& k, const PieceGeo& g, uint32_t R, uint32_t col,
+                                               uint32_t u, uint32_t v) {
+    const uint32_t d = (uint32_t)__clzll((long long)pieces_cat(k, 0, col, g.m1, g.p, u, v));
     return d < R - 1 ? d : R - 1;
+}
+
+// Checksum h2 of edge (u, v) in column col: the first 32 bits of its pieces.
+__device__ __forceinline__ uint32_t edge_checksum(const Keys& k, const PieceGeo& g, uint32_t col, uint32_t u,
+                                                  uint32_t v) {
+    return (uint32_t)(pieces_cat(k, kH2Words, col, g.m2, g.p, u, v) >> 32);
 }
 
 __device__ __forceinline__ uint64_t edge_index(uint32_t x, uint32_t y, uint32_t V) {

@@ -5,9 +5,10 @@
 // Both samplers put position x into rows 0..d of column j, with
 // d = min(clz64(a_j*x + b_j), R-1) and R = ceil(log2 n) (the membership rule
 // is the same by Section 3.2's own remark); they differ in the bucket update:
-//   CubeSketch  alpha ^= x, gamma ^= h2(x) (fmix32 over a 32-bit fold);
+//   CubeSketch  alpha ^= x, gamma ^= h2(x) (multiply-add-shift over the two
+//               32-bit words of x, keys c0, c1, c2; see pos_checksum);
 //   standard    a += x*delta, b += delta (two's complement 64-bit),
-//               c += delta * r_j^x mod p, p = 2^61 - 1, r_j = 1 + c_j mod (p-1):
+//               c += delta * r_j^x mod p, p = 2^61 - 1, r_j = 1 + c0_j mod (p-1):
 //               a modular exponentiation per column update (Section 3.1).
 // One thread owns one column of one sketch and applies the sketch's updates in
 // order; the buckets stay in the paper's nested form (rows 0..d per update),
@@ -17,7 +18,6 @@
 #include <stdint.h>
 
 #include "../../include/gz.h"
-#include "gz_internal.cuh"
 
 namespace {
 
@@ -39,6 +39,18 @@ __device__ __forceinline__ uint64_t mulmod61(uint64_t x, uint64_t y) {
     return s >= kP61 ? s - kP61 : s;
 }
 
+// Position hashes of the vector sketches (positions are not edges, so the node
+// sketches' pair hashes do not apply): depth = min(leading zeros of
+// (a*x + b) mod 2^64, R-1) and checksum ((c0*x0 + c1*x1 + c2) mod 2^64) >> 32
+// over the 32-bit words x0, x1 of x (multiply-add-shift, Dietzfelbinger 1996).
+__device__ __forceinline__ uint32_t pos_depth(uint64_t a, uint64_t b, uint64_t x, uint32_t R) {
+    const uint32_t d = (uint32_t)__clzll((long long)(a * x + b));
+    return d < R - 1 ? d : R - 1;
+}
+__device__ __forceinline__ uint32_t pos_checksum(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t x) {
+    return (uint32_t)((c0 * (uint32_t)x + c1 * (x >> 32) + c2) >> 32);
+}
+
 // r^e mod 2^61-1, square-and-multiply from the highest set bit of e
 __device__ __forceinline__ uint64_t powmod61(uint64_t r, uint64_t e) {
     uint64_t acc = 1;
@@ -57,7 +69,9 @@ __global__ void __launch_bounds__(224) k_l0_update(uint64_t n, uint32_t R, uint6
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (uint64_t)sketches * 7) return;
     const uint32_t s = (uint32_t)(t / 7), j = (uint32_t)(t % 7);
-    const uint64_t ka = sm64_at(seed, 3 * j) | 1u, kb = sm64_at(seed, 3 * j + 1), kc = sm64_at(seed, 3 * j + 2);
+    // column j's keys: SplitMix64 outputs 5j .. 5j+4 (the node sketches' schedule)
+    const uint64_t ka = sm64_at(seed, 5 * j) | 1u, kb = sm64_at(seed, 5 * j + 1);
+    const uint64_t kc0 = sm64_at(seed, 5 * j + 2), kc1 = sm64_at(seed, 5 * j + 3), kc2 = sm64_at(seed, 5 * j + 4);
     uint8_t* base = buckets + (uint64_t)s * bytes_per_sketch;
     const uint64_t* xs = x + (uint64_t)s * m;
     const int32_t* ds = delta ? delta + (uint64_t)s * m : nullptr;
@@ -66,8 +80,8 @@ __global__ void __launch_bounds__(224) k_l0_update(uint64_t n, uint32_t R, uint6
         uint32_t* G = reinterpret_cast<uint32_t*>(reinterpret_cast<uint64_t*>(base) + 7ull * R) + (uint64_t)j * R;
         for (uint32_t i = 0; i < m; ++i) {
             const uint64_t xi = xs[i];
-            const uint32_t d = gz::exact_depth(gz::depth_word(ka, kb, xi), R);
-            const uint32_t g = gz::gamma_final(gz::checksum_pre(kc, xi));
+            const uint32_t d = pos_depth(ka, kb, xi, R);
+            const uint32_t g = pos_checksum(kc0, kc1, kc2, xi);
             for (uint32_t row = 0; row <= d; ++row) {
                 A[row] ^= xi;
                 G[row] ^= g;
@@ -77,11 +91,11 @@ __global__ void __launch_bounds__(224) k_l0_update(uint64_t n, uint32_t R, uint6
         uint64_t* A = reinterpret_cast<uint64_t*>(base) + (uint64_t)j * R;
         uint64_t* B = A + 7ull * R;
         uint64_t* C = B + 7ull * R;
-        const uint64_t r = 1 + kc % (kP61 - 1);
+        const uint64_t r = 1 + kc0 % (kP61 - 1);
         for (uint32_t i = 0; i < m; ++i) {
             const uint64_t xi = xs[i];
             const int64_t dl = ds ? ds[i] : 1;
-            const uint32_t d = gz::exact_depth(gz::depth_word(ka, kb, xi), R);
+            const uint32_t d = pos_depth(ka, kb, xi, R);
             const uint64_t chk = powmod61(r, xi);
             const uint64_t add = dl > 0 ? chk : (chk ? kP61 - chk : 0);
             for (uint32_t row = 0; row <= d; ++row) {

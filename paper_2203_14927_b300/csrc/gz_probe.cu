@@ -1,10 +1,11 @@
 // gz_probe.cu -- measured ceilings of the integer pipes that the batched update
 // kernel runs on.  The update of one (record, column) pair is integer work
-// only (a 64-bit multiply-add for the depth hash, a 32-bit multiply-xorshift
-// checksum, a leading-zero count and two XORs), so its roofline is an integer
-// issue rate, not a floating-point or tensor peak.  Each probe runs eight
-// independent dependency chains per thread of one instruction kind on every
-// SM and reports thread-instructions per second.
+// only (a 64-bit multiply-add for the depth hash, a multiply-add checksum on
+// the index's 32-bit words, a leading-zero count and two or three XORs), so
+// its roofline is an integer issue rate, not a floating-point or tensor peak.
+// Each probe runs eight independent dependency chains per thread of one
+// instruction kind on every SM and reports thread-instructions per second; a
+// launch lasts a few milliseconds, so launch overhead is far below noise.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -12,11 +13,18 @@
 
 namespace {
 
+// kind 0: 32-bit multiply-add; 1: three-input logic; 2: the two interleaved;
+// 3: leading-zero count; 4: 32-bit shared-memory atomic XOR (each warp on its
+// own 32 words, one per lane: no bank conflicts).  64 operations per thread
+// and iteration.
 template <int kKind>
 __global__ void __launch_bounds__(256) k_int_probe(uint32_t* out, uint32_t iters, uint32_t k1, uint32_t k2) {
+    __shared__ uint32_t sh[256];
     uint32_t x[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) x[i] = threadIdx.x * 8u + (uint32_t)i + blockIdx.x;
+    sh[threadIdx.x] = 0;
+    __syncthreads();
     for (uint32_t it = 0; it < iters; ++it) {
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
@@ -24,11 +32,20 @@ __global__ void __launch_bounds__(256) k_int_probe(uint32_t* out, uint32_t iters
             for (int i = 0; i < 8; ++i) {
                 if (kKind == 0 || (kKind == 2 && (i & 1) == 0))
                     asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(x[i]) : "r"(k1), "r"(k2));
+                else if (kKind == 3)
+                    asm volatile("clz.b32 %0, %0;" : "+r"(x[i]));
+                else if (kKind == 4)
+                    asm volatile("red.shared.xor.b32 [%0], %1;" ::"r"(
+                                     static_cast<uint32_t>(__cvta_generic_to_shared(&sh[threadIdx.x]))),
+                                 "r"(x[i] + (uint32_t)r)
+                                 : "memory");
                 else
                     asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(x[i]) : "r"(k1), "r"(k2));
             }
         }
     }
+    __syncthreads();
+    if (kKind == 4) x[0] ^= sh[threadIdx.x];
     uint32_t acc = 0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc ^= x[i];
@@ -38,12 +55,14 @@ __global__ void __launch_bounds__(256) k_int_probe(uint32_t* out, uint32_t iters
 }  // namespace
 
 extern "C" gz_status gz_int_peak(int kind, double* ops_per_s) {
-    if (!ops_per_s || kind < 0 || kind > 2) return GZ_EINVAL;
+    if (!ops_per_s || kind < 0 || kind > 4) return GZ_EINVAL;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return GZ_ECUDA;
-    const uint32_t blocks = (uint32_t)sms * 8, threads = 256, iters = 64;
+    // the leading-zero count and the shared atomics run at 1/8 and 1/4 of the
+    // logic rate: fewer iterations keep every probe at a few milliseconds
+    const uint32_t blocks = (uint32_t)sms * 8, threads = 256, iters = kind >= 3 ? 1024 : 8192;
     uint32_t* out = nullptr;
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -56,7 +75,9 @@ extern "C" gz_status gz_int_peak(int kind, double* ops_per_s) {
         cudaEventRecord(e0, st);
         if (kind == 0) k_int_probe<0><<<blocks, threads, 0, st>>>(out, iters, 0x01000193u, 7u);
         else if (kind == 1) k_int_probe<1><<<blocks, threads, 0, st>>>(out, iters, 0x5bd1e995u, 0x2545F491u);
-        else k_int_probe<2><<<blocks, threads, 0, st>>>(out, iters, 0x01000193u, 7u);
+        else if (kind == 2) k_int_probe<2><<<blocks, threads, 0, st>>>(out, iters, 0x01000193u, 7u);
+        else if (kind == 3) k_int_probe<3><<<blocks, threads, 0, st>>>(out, iters, 0u, 0u);
+        else k_int_probe<4><<<blocks, threads, 0, st>>>(out, iters, 0u, 0u);
         cudaEventRecord(e1, st);
         e = cudaEventSynchronize(e1);
         float ms = 0.f;

@@ -41,7 +41,8 @@ enum {
 
 struct QArgs {
     SketchView s;
-    const uint64_t* kc;  // checksum keys, 7K
+    Keys keys;     // hash keys (the checksum's pieces)
+    PieceGeo geo;
     uint32_t V, K, R, M;  // the round index lives in ctr[C_ROUND]
     uint32_t *label, *parent, *count, *off, *cursor, *members, *roots, *target;
     uint32_t* slot;     // accumulator slot of a component with more than M members
@@ -295,12 +296,13 @@ __global__ void __launch_bounds__(256) k_q_sample(QArgs q) {
             const uint32_t carry_g = __shfl_sync(0xffffffffu, y1, 0);
             x0 ^= carry_a;
             y0 ^= carry_g;
-            const uint64_t kcj = q.kc[round * GZ_COLS + j];
+            const uint32_t colj = round * GZ_COLS + j;
+            // h2 is defined on edges: alpha must decode to u < v < V first
             auto good = [&](uint64_t a, uint32_t g, uint32_t row) -> bool {
-                if (row >= R || (a | g) == 0) return false;
-                if (g != checksum_pre(kcj, a) || a >= VV) return false;
+                if (row >= R || (a | g) == 0 || a >= VV) return false;
                 const uint32_t uu = (uint32_t)(a / q.V), vv = (uint32_t)(a % q.V);
                 if (uu >= vv) return false;
+                if (g != edge_checksum(q.keys, q.geo, colj, uu, vv)) return false;
                 return (q.label[uu] == c) != (q.label[vv] == c);
             };
             nz |= __any_sync(0xffffffffu, (r0 < R && (x0 | y0)) || (r1 < R && (x1 | y1))) != 0;
@@ -465,7 +467,9 @@ static QArgs query_args(gz_handle* h) {
         q.s.node_bytes = h->per_k_bytes;
         q.s.per_k_bytes = 0;
     }
-    q.kc = h->d_keys + 2 * (size_t)h->ncol;
+    q.keys.w = h->d_keys;
+    q.keys.ncol = h->ncol;
+    q.geo = h->geo;
     q.V = h->V;
     q.K = h->K;
     q.R = h->R;
@@ -503,7 +507,7 @@ static void enqueue_grouping(gz_handle* h, const QArgs& q, cudaStream_t stm) {
     cudaMemsetAsync(h->q_count, 0, (size_t)(V + 1) * sizeof(uint32_t), stm);
     cudaMemsetAsync(h->q_ctr, 0, 4 * sizeof(uint32_t), stm);  // roots, big, edges, fails
     k_q_count<<<gV, kTpb, 0, stm>>>(q);
-    launch_scan(h->q_count, h->q_off, h->q_cursor, V, stm, h->d_scan_tmp);
+    launch_scan(h->q_count, h->q_off, h->q_cursor, nullptr, V, stm, h->d_scan_tmp);
     k_q_group<<<gV, kTpb, 0, stm>>>(q);
     k_q_roots<<<gV, kTpb, 0, stm>>>(q);
     // one thread per word of a CubeSketch (one pass over its 21R/2 words)
@@ -661,7 +665,7 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
                     k_q_fj_mark<<<gR, kTpb, 0, stm>>>(q, F, Mx, h->q_flag);
                     // q_cursor is free again: reuse it for the accept flags
                     k_q_accept<<<gV, kTpb, 0, stm>>>(q, h->q_flag, h->q_cursor);
-                    launch_scan(h->q_cursor, h->q_pos, nullptr, V, stm, h->d_scan_tmp);
+                    launch_scan(h->q_cursor, h->q_pos, nullptr, nullptr, V, stm, h->d_scan_tmp);
                     k_q_forest_write<<<gV, kTpb, 0, stm>>>(q, h->q_cursor, h->q_pos, h->q_forest);
                     k_q_forest_advance<<<1, 1, 0, stm>>>(q, h->q_pos);
                     h->launches += J + 7;

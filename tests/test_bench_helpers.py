@@ -14,3 +14,21 @@ def test_wide_index_fraction_counts_indices_of_2p32_or_more():
         got = bench.wide_index_fraction(torch.from_numpy(u.astype(np.int32)), torch.from_numpy(v.astype(np.int32)),
                                         V, torch, block=777)
         assert got == want, V
+
+
+def test_wide_segment_fraction_counts_records_of_high_nodes():
+    # the batched kernel's 64-bit column code runs on every record of a node
+    # x >= floor((2^32 - V) / V) + 1; each update has two records
+    rng = np.random.default_rng(6)
+    for V in (1000, 65536, 70001, 1 << 17):
+        u = rng.integers(0, V, 4000)
+        v = (u + 1 + rng.integers(0, V - 1, 4000)) % V
+        xn = ((1 << 32) - V) // V + 1
+        want = 0.0
+        if V * V > 1 << 32:
+            # a node of a record can hold an index of 2^32 or more iff its
+            # largest possible index x*V + V-1 reaches 2^32
+            want = np.mean([x * V + V - 1 >= 1 << 32 for x in np.concatenate([u, v]).tolist()])
+        got = bench.wide_segment_fraction(torch.from_numpy(u.astype(np.int32)),
+                                          torch.from_numpy(v.astype(np.int32)), V, torch, block=555)
+        assert abs(got - want) < 1e-12, V

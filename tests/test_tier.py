@@ -58,6 +58,10 @@ def test_tiered_kronecker_checkpoint_and_reset():
     g.reset()
     a, gg = g.export_sketch()
     assert not a.any() and not gg.any()
+    # the device array of a tiered handle holds only some nodes: gz_info
+    # withholds its pointer, so nothing can mistake it for the whole sketch
+    assert g.info()["sketch_ptr"] is None
+    g.close()
 
 
 def test_tiered_wide_indices_match_all_hbm_and_oracle():

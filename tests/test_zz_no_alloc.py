@@ -1,9 +1,10 @@
 """The allocation-free ingestion entry point gives the same sketches as
 gz_edge_update.
 
-Callers that cannot allocate device memory (code running under CUDA graph
-capture, hosts whose device memory belongs to another allocator, latency-bound
-loops) use gz_sketch_update_noalloc, which works in a fixed static scratch
+Callers that cannot let a library allocate device memory (a host framework
+whose caching allocator owns the device memory and accounts for every byte, a
+latency-bound loop that may not call cudaMalloc, which can synchronise the
+device) use gz_sketch_update_noalloc, which works in a fixed static scratch
 array.  This test drives it through the C ABI on a handle's own sketch memory,
 two calls in a row, and compares the exported sketches bit for bit with a
 second handle fed the same batches through gz_edge_update (the tests of this
