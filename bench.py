@@ -973,7 +973,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--l0-cpu-seconds", type=float, default=0.5)
     ap.add_argument("--ref-seconds", type=float, default=40.0)
-    ap.add_argument("--e2e-log2", type=int, default=28)
+    ap.add_argument("--e2e-log2", type=int, default=30)
     ap.add_argument("--plain-log2", type=int, default=26)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")

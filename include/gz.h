@@ -143,10 +143,14 @@ gz_status gz_set_stream(gz_handle *h, void *stream);
  * sense of Section 2.1 (insert only absent edges, delete only present ones).
  *   u, v       : n vertex ids each; host memory if on_device == 0, else device
  *                memory.  Any order of endpoints is accepted.
- *   Validation : an update with u == v or an id >= V invalidates its batch;
- *                a batch is the whole call when n <= 2^chunk_log2, else each
- *                consecutive slice of 2^chunk_log2 updates.  An invalid batch
- *                is discarded whole before any sketch changes.  Validation
+ *   Validation : an update with u == v or an id >= V invalidates its batch.
+ *                With device input a batch is the whole call when
+ *                n <= 2^chunk_log2, else each consecutive slice of
+ *                2^chunk_log2 updates.  With host input the slices of a call
+ *                ramp up: 2^chunk_log2 / 16 updates, then 2^chunk_log2 / 4,
+ *                then 2^chunk_log2 each (at least 256), so the first copy to
+ *                the device, which nothing overlaps, is short.  An invalid
+ *                batch is discarded whole before any sketch changes.  Validation
  *                runs on the device, so the call itself returns GZ_OK and the
  *                error is reported as GZ_EINVAL by the next gz_sync, query or
  *                export call on this handle.
@@ -162,8 +166,8 @@ gz_status gz_edge_update(gz_handle *h, const uint32_t *u, const uint32_t *v,
  *                memory (8-byte aligned).
  *   Validation : an index that is not canonical (min >= max, so also a self
  *                loop, or idx >= V^2) invalidates its batch, with the same
- *                batches, discard rule and deferred GZ_EINVAL report as
- *                gz_edge_update.
+ *                batches (device or host input), discard rule and deferred
+ *                GZ_EINVAL report as gz_edge_update.
  *   Ownership  : as gz_edge_update.  The first call allocates a decode
  *                buffer of 8 * 2^chunk_log2 bytes on the device. */
 gz_status gz_edge_update_idx(gz_handle *h, const uint64_t *idx, size_t n, int on_device);

@@ -10,7 +10,10 @@
  * histograms, a prefix sum, a scatter of the edge index into the buffer of
  * each endpoint) and the node buffers are then applied in parallel, a node per
  * OpenMP iteration, with the update rule of Fig. cube_code (nested rows, the
- * form the paper's system stores).  The hash functions are the oracle's.
+ * form the paper's system stores).  The hashes follow the oracle's definition
+ * (the same keys and pieces), computed the way a tuned CPU system would:
+ * the edge is decoded once per record, and the depth reads only the pieces
+ * it needs.
  *
  * Only nodes in [node_lo, node_hi) are sketched (alpha/gamma hold exactly
  * those nodes' sketches, in the oracle's nested layout), so a bounded node
@@ -22,29 +25,48 @@
 
 #define GZB_COLS 7
 
-uint64_t gzo_h1(uint32_t V, const uint32_t *k1, uint64_t e);
-uint32_t gzo_h2(uint32_t V, const uint32_t *k2, uint64_t e);
 int gzo_geometry(uint32_t V, uint32_t *K, uint32_t *R);
 void gzo_keys(uint64_t seed, uint32_t K, uint32_t *keys);
+void gzo_pieces(uint32_t V, uint32_t *p, uint32_t *m1, uint32_t *m2);
 #define GZB_KEYS 256 /* key words per column: h1 pieces at [0, 128), h2 at [128, 256) */
 
-/* Fig. cube_code update_sketch for every CubeSketch of one node sketch */
-static void node_apply(uint32_t V, uint32_t K, uint32_t R, const uint32_t *keys, uint64_t *alpha,
-                       uint32_t *gamma, uint64_t idx)
+typedef struct {
+    uint32_t V, K, R, p, m1, m2;
+    const uint32_t *keys;
+} gzb_geo;
+
+/* the top p bits of piece i with keys k on (u, v) */
+static inline uint32_t piece(const uint32_t *k, uint32_t i, uint32_t p, uint32_t u, uint32_t v)
 {
-    for (uint32_t k = 0; k < K; k++) {
-        for (uint32_t j = 0; j < GZB_COLS; j++) {
-            size_t col = (size_t)k * GZB_COLS + j;
-            uint64_t h = gzo_h1(V, keys + col * GZB_KEYS, idx);
-            uint32_t g = gzo_h2(V, keys + col * GZB_KEYS + 128, idx);
-            uint64_t *A = alpha + col * R;
-            uint32_t *G = gamma + col * R;
-            uint32_t row = 0;
-            while (row < R && (row == 0 || ((h >> (row - 1)) & 1u) == 0)) {
-                A[row] ^= idx;
-                G[row] ^= g;
-                row++;
+    return (k[3 * i] * u + k[3 * i + 1] * v + k[3 * i + 2]) >> (32 - p);
+}
+
+/* Fig. cube_code update_sketch for every CubeSketch of one node sketch */
+static void node_apply(const gzb_geo *g, uint64_t *alpha, uint32_t *gamma, uint64_t idx)
+{
+    const uint32_t u = (uint32_t)(idx / g->V), v = (uint32_t)(idx % g->V), p = g->p, R = g->R;
+    for (uint32_t col = 0; col < g->K * GZB_COLS; col++) {
+        const uint32_t *k1 = g->keys + (size_t)col * GZB_KEYS, *k2 = k1 + 128;
+        /* depth: leading zeros of the h1 pieces, capped at R-1 */
+        uint32_t d = 0;
+        for (uint32_t i = 0; i < g->m1 && d < R - 1; i++) {
+            uint32_t t = piece(k1, i, p, u, v);
+            if (t) {
+                d += (uint32_t)__builtin_clz(t) - (32 - p);
+                break;
             }
+            d += p;
+        }
+        if (d > R - 1) d = R - 1;
+        /* checksum: the first 32 bits of the h2 pieces */
+        uint64_t acc = 0;
+        for (uint32_t i = 0; i < g->m2; i++) acc |= (uint64_t)piece(k2, i, p, u, v) << (64 - p * (i + 1));
+        const uint32_t gsum = (uint32_t)(acc >> 32);
+        uint64_t *A = alpha + (size_t)col * R;
+        uint32_t *G = gamma + (size_t)col * R;
+        for (uint32_t row = 0; row <= d; row++) {
+            A[row] ^= idx;
+            G[row] ^= gsum;
         }
     }
 }
@@ -62,6 +84,8 @@ int gzb_ingest_batched(uint32_t V, uint64_t seed, size_t n, const uint32_t *u, c
     if (threads <= 0) threads = omp_get_max_threads();
     const size_t ncol = (size_t)K * GZB_COLS, nb = ncol * R, span = node_hi - node_lo;
     uint32_t *keys = malloc(ncol * GZB_KEYS * 4);
+    gzb_geo geo = {V, K, R, 0, 0, 0, keys};
+    gzo_pieces(V, &geo.p, &geo.m1, &geo.m2);
     uint32_t *hist = calloc((size_t)threads * span, 4);
     uint32_t *off = malloc((span + 1) * 4);
     uint64_t *rec = malloc(2 * chunk * 8);
@@ -116,7 +140,7 @@ int gzb_ingest_batched(uint32_t V, uint64_t seed, size_t n, const uint32_t *u, c
         for (size_t x = 0; x < span; x++) {
             uint64_t *A = alpha + x * nb;
             uint32_t *G = gamma + x * nb;
-            for (uint32_t r = off[x]; r < off[x + 1]; r++) node_apply(V, K, R, keys, A, G, rec[r]);
+            for (uint32_t r = off[x]; r < off[x + 1]; r++) node_apply(&geo, A, G, rec[r]);
         }
     }
 out:

@@ -269,6 +269,14 @@ gz_status gz_set_stream(gz_handle* h, void* stream) {
     return GZ_OK;
 }
 
+// Updates in slice i of a call with host input: 2^chunk_log2 / 16, then
+// 2^chunk_log2 / 4, then 2^chunk_log2 (never below 256).
+static uint64_t host_slice(const gz_handle* h, size_t i) {
+    const uint64_t c = h->chunk;
+    const uint64_t s = i == 0 ? c / 16 : i == 1 ? c / 4 : c;
+    return std::max<uint64_t>(s, std::min<uint64_t>(c, 256));
+}
+
 static gz_status host_path_setup(gz_handle* h) {
     if (h->d_stage) return GZ_OK;
     cudaError_t e = cudaMallocAsync(&h->d_stage, (size_t)4 * h->chunk * 4, h->stream);
@@ -295,14 +303,16 @@ gz_status gz_edge_update(gz_handle* h, const uint32_t* u, const uint32_t* v, siz
         }
         return GZ_OK;
     }
-    // Host input: two staging buffers; the copy of chunk i+1 (copy stream)
-    // overlaps the processing of chunk i.
+    // Host input: two staging buffers; the copy of slice i+1 (copy stream)
+    // overlaps the processing of slice i.  The first slices are short (a
+    // sixteenth, then a quarter of a chunk), so the first copy, which nothing
+    // hides, is short too.
     gz_status s = host_path_setup(h);
     if (s != GZ_OK) return s;
     cudaError_t e = cudaSuccess;
     size_t i = 0;
-    for (size_t off = 0; off < n; off += h->chunk, ++i) {
-        const uint64_t m = std::min<uint64_t>(h->chunk, n - off);
+    for (size_t off = 0, m = 0; off < n; off += m, ++i) {
+        m = std::min<uint64_t>(host_slice(h, i), n - off);
         const int b = (int)(i & 1);
         uint32_t* su = h->d_stage + (size_t)b * 2 * h->chunk;
         uint32_t* sv = su + h->chunk;
@@ -349,12 +359,12 @@ gz_status gz_edge_update_idx(gz_handle* h, const uint64_t* idx, size_t n, int on
         }
         return GZ_OK;
     }
-    // Host input: the packed chunk (8 bytes per update) fills one staging
-    // buffer; it is free again once decoded.
+    // Host input: the packed slice (8 bytes per update) fills one staging
+    // buffer; it is free again once decoded.  Slices ramp up as above.
     if ((s = host_path_setup(h)) != GZ_OK) return s;
     size_t i = 0;
-    for (size_t off = 0; off < n; off += h->chunk, ++i) {
-        const uint64_t m = std::min<uint64_t>(h->chunk, n - off);
+    for (size_t off = 0, m = 0; off < n; off += m, ++i) {
+        m = std::min<uint64_t>(host_slice(h, i), n - off);
         const int b = (int)(i & 1);
         uint64_t* sb = reinterpret_cast<uint64_t*>(h->d_stage + (size_t)b * 2 * h->chunk);
         e = cudaStreamWaitEvent(h->copy_stream, h->ev_free[b], 0);

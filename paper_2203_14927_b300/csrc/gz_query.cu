@@ -44,6 +44,7 @@ struct QArgs {
     Keys keys;     // hash keys (the checksum's pieces)
     PieceGeo geo;
     uint32_t V, K, R, M;  // the round index lives in ctr[C_ROUND]
+    uint64_t vinv;        // floor((2^64 - 1) / V): a / V by one high multiply and a correction
     uint32_t *label, *parent, *count, *off, *cursor, *members, *roots, *target;
     uint32_t* slot;     // accumulator slot of a component with more than M members
     uint64_t* acc;      // slots x (21R/2) words, zero between rounds
@@ -300,7 +301,14 @@ __global__ void __launch_bounds__(256) k_q_sample(QArgs q) {
             // h2 is defined on edges: alpha must decode to u < v < V first
             auto good = [&](uint64_t a, uint32_t g, uint32_t row) -> bool {
                 if (row >= R || (a | g) == 0 || a >= VV) return false;
-                const uint32_t uu = (uint32_t)(a / q.V), vv = (uint32_t)(a % q.V);
+                // a < V^2: the high product underestimates a / V by at most one
+                uint64_t qu = __umul64hi(a, q.vinv);
+                uint64_t rem = a - qu * q.V;
+                if (rem >= q.V) {
+                    ++qu;
+                    rem -= q.V;
+                }
+                const uint32_t uu = (uint32_t)qu, vv = (uint32_t)rem;
                 if (uu >= vv) return false;
                 if (g != edge_checksum(q.keys, q.geo, colj, uu, vv)) return false;
                 return (q.label[uu] == c) != (q.label[vv] == c);
@@ -471,6 +479,7 @@ static QArgs query_args(gz_handle* h) {
     q.keys.ncol = h->ncol;
     q.geo = h->geo;
     q.V = h->V;
+    q.vinv = ~0ull / h->V;
     q.K = h->K;
     q.R = h->R;
     q.M = kMergeChunk;

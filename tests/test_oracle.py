@@ -577,3 +577,12 @@ def test_paper_design_cpu_baseline_equals_oracle():
     assert np.array_equal(a, A[37:190]) and np.array_equal(g, G[37:190])
     with pytest.raises(ValueError):
         oracle.ingest_batched(V, 9, np.array([3], np.uint32), np.array([3], np.uint32))
+    # 16-bit pieces at V = 2^17 (three depth pieces) and 14-bit pieces at
+    # V = 2^19 (three checksum pieces): sampled nodes against the oracle
+    for V in (1 << 17, 1 << 19):
+        u, v = S.hub_stream(V, 4000, 5, [0, 1, V - 1])
+        eu, ev = S.net_graph(V, u, v)
+        a, g = oracle.ingest_batched(V, 4, u, v, node_lo=0, node_hi=2, threads=2, chunk=1000)
+        for x in (0, 1):
+            A1, G1 = oracle.sketch_node(V, 4, x, S.neighbors_from_edges(V, eu, ev, x))
+            assert np.array_equal(a[x], A1) and np.array_equal(g[x], G1), (V, x)

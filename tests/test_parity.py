@@ -179,6 +179,26 @@ def test_invalid_batch_is_discarded_whole():
     assert np.array_equal(before[0], after[0])
 
 
+@pytest.mark.parametrize("pipelined", [True, False])
+def test_host_input_slices_ramp_up_and_validate_each_slice(pipelined):
+    # host input is cut into slices of 2^c/16, 2^c/4, then 2^c updates; a bad
+    # update discards exactly its slice (here the second: updates 256..1279
+    # at 2^c = 4096) and every other slice is applied
+    V, seed = 500, 8
+    u, v = S.random_stream(V, 12000, seed=9, n_distinct=6000)
+    u[700] = v[700]  # a self loop in the second slice
+    g = gz.Graph(V, seed, chunk_log2=12, no_pipeline=0 if pipelined else 1)
+    g.edge_update(u, v)
+    with pytest.raises(gz.GzError) as ei:
+        g.sync()
+    assert ei.value.status == gz.GZ_EINVAL
+    keep = np.ones(len(u), bool)
+    keep[256:256 + 1024] = False
+    A, G = oracle.ingest(V, seed, u[keep], v[keep])
+    _assert_same_sketches(g, A, G)
+    g.close()
+
+
 def test_empty_graph_single_edge_and_reset():
     V = 50
     g = gz.Graph(V, 1)
