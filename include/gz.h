@@ -274,12 +274,21 @@ gz_status gz_profile_read(gz_handle *h, gz_profile *out);
  *     served, and only while the running total stays within hbm_budget;
  *     otherwise it waits; a closed graph gives its memory back when its last
  *     request is done;
+ *   - eviction: when a graph has waited 20 ms for memory, the least recently
+ *     used resident graph with no pending request is checkpointed into
+ *     pinned host memory (gz_checkpoint) and its device memory freed; its
+ *     next request restores it (gz_restore), bit for bit;
  *   - continuous batching: `slots` workers, each a host thread with its own
- *     CUDA stream, repeatedly take the resident (or admissible) graph whose
- *     oldest pending request is oldest and serve its pending requests in
- *     order; requests that arrive while others run join the queue and are
- *     picked up as soon as a slot and memory free up, and the work of
- *     different graphs overlaps on the device;
+ *     CUDA stream, repeatedly take a resident graph with pending requests
+ *     (oldest request first; finishing resident graphs is what frees memory),
+ *     else the admissible graph with the oldest request, and serve up to
+ *     max_batch of its pending requests in order; an admissible graph whose
+ *     request is 20 ms older than every resident one goes first.  Requests
+ *     that arrive while others run join the queue and are picked up as soon
+ *     as a slot and memory free up, and the work of different graphs overlaps
+ *     on the device;
+ *   - server graphs run with no_pipeline set (the server overlaps graphs,
+ *     not the partition and update of one graph);
  *   - a graph is served by one worker at a time, so each graph sees its
  *     requests in submission order and gets exactly the result it would get
  *     alone.
@@ -307,6 +316,11 @@ typedef struct {
     uint64_t resident_bytes, peak_resident_bytes, budget_bytes;
     uint32_t graphs, resident_graphs, waiting_graphs, pending_requests;
     uint64_t completed_requests;
+    uint64_t evictions;      /* graphs checkpointed to host memory to make room */
+    uint32_t evicted_graphs; /* graphs held in host memory now */
+    uint32_t reserved;
+    double evict_ms;         /* host time spent checkpointing evicted graphs out */
+    double restore_ms;       /* host time spent restoring them */
 } gz_server_stats;
 
 /* Start a server on the current device (cfg may be NULL).  The server raises
@@ -348,6 +362,14 @@ gz_status gz_server_poll(gz_server *s, gz_completion *out, size_t max, size_t *n
 gz_status gz_server_drain(gz_server *s);
 
 gz_status gz_server_stats_read(gz_server *s, gz_server_stats *out);
+
+/* Change the HBM budget while the server runs.  A smaller budget than the
+ * bytes now resident makes admissions wait (and idle graphs be evicted) until
+ * the total fits; graphs registered with more bytes than the new budget wait
+ * until it grows again.  Pinned checkpoint buffers of released graphs are
+ * kept for later evictions until the server is destroyed.  GZ_EINVAL for a
+ * zero budget. */
+gz_status gz_server_set_budget(gz_server *s, uint64_t hbm_budget);
 
 /* Reason of the most recent failed request ("" if none); valid until the next
  * call of this function by the same thread. */

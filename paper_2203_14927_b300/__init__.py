@@ -147,6 +147,7 @@ _SIGNATURES = {
                                       ctypes.c_int]),
     "gz_server_drain": (ctypes.c_int, [ctypes.c_void_p]),
     "gz_server_stats_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gz_server_set_budget": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     "gz_server_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "gz_checkpoint_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gz_checkpoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
@@ -511,7 +512,9 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("resident_bytes", ctypes.c_uint64), ("peak_resident_bytes", ctypes.c_uint64),
                 ("budget_bytes", ctypes.c_uint64), ("graphs", ctypes.c_uint32),
                 ("resident_graphs", ctypes.c_uint32), ("waiting_graphs", ctypes.c_uint32),
-                ("pending_requests", ctypes.c_uint32), ("completed_requests", ctypes.c_uint64)]
+                ("pending_requests", ctypes.c_uint32), ("completed_requests", ctypes.c_uint64),
+                ("evictions", ctypes.c_uint64), ("evicted_graphs", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("evict_ms", ctypes.c_double), ("restore_ms", ctypes.c_double)]
 
 
 class Server:
@@ -594,6 +597,11 @@ class Server:
 
     def last_error(self) -> str:
         return lib().gz_server_last_error(self._s).decode()
+
+    def set_budget(self, hbm_budget: int):
+        st = lib().gz_server_set_budget(self._s, int(hbm_budget))
+        if st != GZ_OK:
+            raise GzError(st, "gz_server_set_budget failed")
 
     def stats(self) -> dict:
         st = ServerStats()

@@ -89,6 +89,7 @@ struct gz_handle {
     int64_t* q_res = nullptr;
     uint64_t* q_acc = nullptr;     // per big component: XOR of its members' CubeSketch
     uint32_t q_slots_cap = 0;
+    uint32_t q_merge_occ = 1;               // resident merge blocks per SM
     cudaGraph_t q_graph = nullptr;          // the CC query as one graph (built at the first query)
     cudaGraphExec_t q_graph_exec = nullptr;
     int64_t* q_trace = nullptr;

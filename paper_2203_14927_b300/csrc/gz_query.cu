@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -119,224 +120,402 @@ __global__ void k_fill64(int64_t* p, uint64_t n, int64_t val) {
         p[i] = val;
 }
 
-// Grouping by label.  After round 0 most vertices share a few labels, so the
-// per-label counters are bumped once per warp and label (match_any), not once
-// per vertex.  The loops below step whole blocks, so every warp is convergent.
-__global__ void k_q_count(QArgs q) {
-    const uint32_t lane = threadIdx.x & 31;
-    for (uint32_t b = blockIdx.x * blockDim.x; b < q.V; b += gridDim.x * blockDim.x) {
-        const uint32_t v = b + threadIdx.x;
-        const bool act = v < q.V;
-        const uint32_t l = act ? q.label[v] : 0xffffffffu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, l);
-        if (act && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&q.count[l], __popc(peers));
+// Grouping by label (a counting sort).  After a few rounds most vertices
+// share a few labels, and a counter bumped per warp would meet thousands of
+// atomics on one address.  So a block takes kGroupSpan consecutive vertices
+// and first counts their labels in a shared-memory hash table (open
+// addressing; a warp adds equal labels once, via match_any), then touches
+// each global counter once per distinct label it holds.
+constexpr uint32_t kGroupThreads = 256, kGroupPer = 4, kGroupSpan = kGroupThreads * kGroupPer;
+constexpr uint32_t kGroupTable = 2 * kGroupSpan;  // load factor <= 1/2
+constexpr uint32_t kEmpty = 0xffffffffu;            // labels are < V <= 2^32 - 1
+constexpr uint32_t kGroupTableLog2 = 11;
+static_assert(kGroupTable == 1u << kGroupTableLog2, "table size");
+
+// slot of `label` in the table, inserting it if absent
+__device__ __forceinline__ uint32_t table_slot(uint32_t* keys, uint32_t label) {
+    uint32_t h = (label * 0x9E3779B1u) >> (32 - kGroupTableLog2);  // multiplicative hashing
+    for (;;) {
+        const uint32_t k = *static_cast<volatile uint32_t*>(&keys[h]);
+        if (k == label) return h;
+        if (k == kEmpty) {
+            const uint32_t old = atomicCAS(&keys[h], kEmpty, label);
+            if (old == kEmpty || old == label) return h;
+        }
+        h = (h + 1) & (kGroupTable - 1);
     }
 }
 
-__global__ void k_q_group(QArgs q) {
+// the block's labels into the table: keys and counts; returns, per thread,
+// the slot of each of its vertices (kEmpty past V)
+__device__ __forceinline__ void table_build(const QArgs& q, uint64_t base, uint32_t* keys, uint32_t* cnt,
+                                            uint32_t (&slot)[kGroupPer]) {
+    for (uint32_t i = threadIdx.x; i < kGroupTable; i += blockDim.x) {
+        keys[i] = kEmpty;
+        cnt[i] = 0;
+    }
+    __syncthreads();
     const uint32_t lane = threadIdx.x & 31;
-    for (uint32_t b = blockIdx.x * blockDim.x; b < q.V; b += gridDim.x * blockDim.x) {
-        const uint32_t v = b + threadIdx.x;
-        const bool act = v < q.V;
-        const uint32_t l = act ? q.label[v] : 0xffffffffu;
+#pragma unroll
+    for (uint32_t k = 0; k < kGroupPer; ++k) {
+        const uint64_t v = base + k * kGroupThreads + threadIdx.x;
+        const uint32_t l = v < q.V ? q.label[v] : kEmpty;
         const uint32_t peers = __match_any_sync(0xffffffffu, l);
         const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
-        uint32_t pos = 0;
-        if (act && lane == leader) pos = atomicAdd(&q.cursor[l], __popc(peers));
-        pos = __shfl_sync(0xffffffffu, pos, leader);
-        if (act) q.members[pos + __popc(peers & ((1u << lane) - 1u))] = v;
+        uint32_t sl = kEmpty;
+        if (l != kEmpty && lane == leader) {
+            sl = table_slot(keys, l);
+            atomicAdd(&cnt[sl], __popc(peers));
+        }
+        slot[k] = __shfl_sync(0xffffffffu, sl, leader);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kGroupThreads) k_q_count(QArgs q) {
+    __shared__ uint32_t keys[kGroupTable], cnt[kGroupTable];
+    for (uint64_t base = (uint64_t)blockIdx.x * kGroupSpan; base < q.V; base += (uint64_t)gridDim.x * kGroupSpan) {
+        uint32_t slot[kGroupPer];
+        table_build(q, base, keys, cnt, slot);
+        for (uint32_t i = threadIdx.x; i < kGroupTable; i += blockDim.x)
+            if (keys[i] != kEmpty) atomicAdd(&q.count[keys[i]], cnt[i]);
+        __syncthreads();  // the table is rebuilt for the next span
     }
 }
 
-// Root list (one append per warp) and an accumulator slot for every
-// component with more than M members.
-__global__ void k_q_roots(QArgs q) {
-    const uint32_t lane = threadIdx.x & 31, round = q.ctr[C_ROUND];
-    for (uint32_t b = blockIdx.x * blockDim.x; b < q.V; b += gridDim.x * blockDim.x) {
-        const uint32_t c = b + threadIdx.x;
-        const uint32_t cnt = c < q.V ? q.count[c] : 0u;
+// After the scan: each block reserves one range of member positions per
+// distinct label it holds, then places its vertices in them.
+__global__ void __launch_bounds__(kGroupThreads) k_q_group(QArgs q) {
+    __shared__ uint32_t keys[kGroupTable], cnt[kGroupTable];
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint64_t base = (uint64_t)blockIdx.x * kGroupSpan; base < q.V; base += (uint64_t)gridDim.x * kGroupSpan) {
+        uint32_t slot[kGroupPer];
+        table_build(q, base, keys, cnt, slot);
+        for (uint32_t i = threadIdx.x; i < kGroupTable; i += blockDim.x)
+            if (keys[i] != kEmpty) cnt[i] = atomicAdd(&q.cursor[keys[i]], cnt[i]);  // now the next position
+        __syncthreads();
+#pragma unroll
+        for (uint32_t k = 0; k < kGroupPer; ++k) {
+            const uint32_t v = (uint32_t)(base + k * kGroupThreads + threadIdx.x);  // used only where v < V
+            const uint32_t sl = slot[k];
+            const uint32_t peers = __match_any_sync(0xffffffffu, sl);
+            const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
+            uint32_t pos = 0;
+            if (sl != kEmpty && lane == leader) pos = atomicAdd(&cnt[sl], __popc(peers));
+            pos = __shfl_sync(0xffffffffu, pos, leader);
+            if (sl != kEmpty) q.members[pos + __popc(peers & ((1u << lane) - 1u))] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// Root list (one append per block of kTpb vertices) and an accumulator slot
+// for every component with more than M members.
+constexpr uint32_t kTpb = 256;
+
+__global__ void __launch_bounds__(kTpb) k_q_roots(QArgs q) {
+    __shared__ uint32_t s_warp[kTpb / 32];
+    __shared__ uint32_t s_base;
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, round = q.ctr[C_ROUND];
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x; b < q.V; b += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t c64 = b + threadIdx.x;
+        const uint32_t c = (uint32_t)c64;  // used only where c64 < V
+        const uint32_t cnt = c64 < q.V ? q.count[c] : 0u;
         const uint32_t bal = __ballot_sync(0xffffffffu, cnt > 0);
-        uint32_t base = 0;
-        if (lane == 0 && bal) base = atomicAdd(&q.ctr[C_ROOTS], __popc(bal));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (cnt > 0) q.roots[base + __popc(bal & ((1u << lane) - 1u))] = c;
+        if (lane == 0) s_warp[wid] = __popc(bal);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+            for (uint32_t w = 0; w < kTpb / 32; ++w) {
+                const uint32_t n = s_warp[w];
+                s_warp[w] = tot;
+                tot += n;
+            }
+            s_base = tot ? atomicAdd(&q.ctr[C_ROOTS], tot) : 0u;
+        }
+        __syncthreads();
+        if (cnt > 0) q.roots[s_base + s_warp[wid] + __popc(bal & ((1u << lane) - 1u))] = c;
         if (cnt > q.M) q.slot[c] = atomicAdd(&q.ctr[C_BIG], 1u);
-        if (c < q.V && cnt == 0 && q.trace) q.trace[(uint64_t)round * q.V + c] = -3;
+        if (c64 < q.V && cnt == 0 && q.trace) q.trace[(uint64_t)round * q.V + c] = -3;
+        __syncthreads();  // s_warp and s_base are reused
     }
 }
 
 // XOR of CubeSketch `round` over the members of every component with more
-// than M members, into that component's accumulator slot.  The members array
-// is grouped by component, so a chunk of M consecutive members meets at most
-// two such components: one that covers its start, one that covers its end.
-__global__ void __launch_bounds__(1024) k_q_merge(QArgs q) {
-    __shared__ uint32_t s_node[kMergeChunk];
+// than M members, into that component's accumulator slot.  Block b takes the
+// members [b * per_block, (b + 1) * per_block) of the grouped members array
+// and thread w word w of a CubeSketch (one coalesced pass over each member's
+// 84R bytes).  The block first resolves node and slot of up to blockDim of
+// its members at once (one round of dependent loads per blockDim members),
+// then streams their blocks kMergeDepth members at a time.  Members are
+// grouped by component, so a block meets each large component as one run:
+// it XORs the run in a register and adds it to the slot with one atomic per
+// word, at the run's end.
+constexpr uint32_t kMergeMaxThreads = 704;  // 21R/2 words rounded up to a warp, R <= 64
+constexpr uint32_t kMergeDepth = 16;
+
+__global__ void __launch_bounds__(kMergeMaxThreads) k_q_merge(QArgs q, uint32_t per_block) {
+    __shared__ uint32_t s_node[kMergeMaxThreads], s_slot[kMergeMaxThreads];
     const uint32_t nw = 21u * q.R / 2u;  // u64 words of one CubeSketch (84R bytes)
-    const uint32_t M = q.M, nchunks = (q.V + M - 1) / M, round = q.ctr[C_ROUND];
-    for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        const uint32_t lo = ch * M, hi = min(q.V, lo + M);
-        const uint32_t cA = q.label[q.members[lo]], cB = q.label[q.members[hi - 1]];
-        const uint32_t nA = q.count[cA], nB = q.count[cB];
-        const bool bigA = nA > M, bigB = cB != cA && nB > M;
-        if (!bigA && !bigB) continue;  // block-uniform
-        __syncthreads();               // s_node of the previous chunk is consumed
-        if (threadIdx.x < hi - lo) s_node[threadIdx.x] = q.members[lo + threadIdx.x];
+    const uint32_t w = threadIdx.x, round = q.ctr[C_ROUND];
+    const uint64_t lo64 = (uint64_t)blockIdx.x * per_block;
+    if (lo64 >= q.V) return;  // block-uniform
+    const uint32_t lo = (uint32_t)lo64, hi = (uint32_t)(lo64 + per_block < q.V ? lo64 + per_block : q.V);
+    uint32_t cur = 0xffffffffu;  // slot of the run being XORed
+    uint64_t x = 0;
+    for (uint32_t b = lo; b < hi; b += blockDim.x) {
+        const uint32_t n = min(blockDim.x, hi - b);
+        __syncthreads();  // the previous segment's s_node / s_slot are consumed
+        if (w < n) {
+            const uint32_t node = q.members[b + w];
+            const uint32_t c = q.label[node];
+            const uint32_t cnt = q.count[c], sl = q.slot[c];
+            s_node[w] = node;
+            s_slot[w] = cnt > q.M ? sl : 0xffffffffu;
+        }
         __syncthreads();
-        const uint32_t eA = bigA ? min(hi, q.off[cA] + nA) - lo : 0u;
-        const uint32_t sB = bigB ? max(lo, q.off[cB]) - lo : hi - lo;
-        uint64_t* accA = bigA ? q.acc + (uint64_t)q.slot[cA] * nw : nullptr;
-        uint64_t* accB = bigB ? q.acc + (uint64_t)q.slot[cB] * nw : nullptr;
-        for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) {
-            if (bigA) {
-                uint64_t x = 0;
-#pragma unroll 8
-                for (uint32_t m = 0; m < eA; ++m)
-                    x ^= __ldg(reinterpret_cast<const uint64_t*>(q.s.cube(s_node[m], round)) + w);
-                atomicXor(reinterpret_cast<unsigned long long*>(accA + w), (unsigned long long)x);
+        for (uint32_t i0 = 0; i0 < n; i0 += kMergeDepth) {
+            uint64_t t[kMergeDepth];
+#pragma unroll
+            for (uint32_t k = 0; k < kMergeDepth; ++k) {
+                const uint32_t i = i0 + k;
+                t[k] = (i < n && s_slot[i] != 0xffffffffu && w < nw)
+                           ? __ldg(reinterpret_cast<const uint64_t*>(q.s.cube(s_node[i], round)) + w)
+                           : 0ull;
             }
-            if (bigB) {
-                uint64_t x = 0;
-#pragma unroll 8
-                for (uint32_t m = sB; m < hi - lo; ++m)
-                    x ^= __ldg(reinterpret_cast<const uint64_t*>(q.s.cube(s_node[m], round)) + w);
-                atomicXor(reinterpret_cast<unsigned long long*>(accB + w), (unsigned long long)x);
+#pragma unroll
+            for (uint32_t k = 0; k < kMergeDepth; ++k) {
+                const uint32_t i = i0 + k;
+                const uint32_t sl = i < n ? s_slot[i] : 0xffffffffu;
+                if (sl == 0xffffffffu) continue;
+                if (sl != cur) {
+                    if (cur != 0xffffffffu && w < nw && x)
+                        atomicXor(reinterpret_cast<unsigned long long*>(q.acc + (uint64_t)cur * nw + w),
+                                  (unsigned long long)x);
+                    cur = sl;
+                    x = 0;
+                }
+                x ^= t[k];
             }
         }
     }
+    if (cur != 0xffffffffu && w < nw && x)
+        atomicXor(reinterpret_cast<unsigned long long*>(q.acc + (uint64_t)cur * nw + w), (unsigned long long)x);
 }
 
-// Sample, one warp per component.  Lane l holds rows l and l+32 of all 7
-// columns of the component's CubeSketch `round`: the XOR of its members'
-// blocks (at most M of them), or its accumulator slot, which is cleared again
-// for the next round.  The nested rows (row i = XOR of exact rows >= i) come
-// from a warp-shuffle suffix XOR per column, and the first good bucket in
-// Fig. cube_code's order (columns, then rows ascending) is found with a ballot
-// per column.
-__device__ __forceinline__ uint64_t shfl_down64(uint64_t x, int off) {
-    const uint32_t lo = __shfl_down_sync(0xffffffffu, (uint32_t)x, off);
-    const uint32_t hi = __shfl_down_sync(0xffffffffu, (uint32_t)(x >> 32), off);
-    return ((uint64_t)hi << 32) | lo;
+// Sample, one warp per component.  A warp takes up to kSampleBatch
+// components at a time and resolves their sizes, offsets, slots and first
+// members with one load per lane.  It builds each component's CubeSketch
+// `round` in one of two shared-memory buffers of its own: a component whose
+// sketch has one source (a single member, or the accumulator slot of a large
+// component, cleared again for the next round) is fetched with asynchronous
+// copies while the warp still works on the previous component; a component
+// of 2..M members is the XOR of its members' blocks, loaded into registers.
+// Lane l moves u64 words l, l + 32, ... of each 84R-byte block, so every
+// access covers 256 contiguous bytes.  Then lane l takes row l of a column
+// from the buffer, the nested rows (row i = XOR of exact rows >= i) come
+// from a warp-shuffle suffix XOR (rows 32 and up, which only V > 2^16 has,
+// by a short loop over the buffer), and the first good bucket in Fig.
+// cube_code's order (columns, then rows ascending) is found with ballots.
+// The checksum keys of the round's 7 columns sit in shared memory.
+constexpr uint32_t kSampleThreads = 256;
+constexpr uint32_t kSampleBatch = 8;
+constexpr uint32_t kMaxKeyWords = 3 * 32;  // 3 words per piece, at most 32 checksum pieces (p >= 1)
+
+// h2 of edge (u, v) in column j of the round, keys from shared memory
+// (word t of column j at sk[t * 7 + j]); the same pieces as edge_checksum
+__device__ __forceinline__ uint32_t round_checksum(const uint32_t* sk, const PieceGeo& g, uint32_t j, uint32_t u,
+                                                   uint32_t v) {
+    uint64_t acc = 0;
+    for (uint32_t i = 0; i < g.m2; ++i) {
+        const uint32_t t = sk[(3 * i) * GZ_COLS + j] * u + sk[(3 * i + 1) * GZ_COLS + j] * v +
+                           sk[(3 * i + 2) * GZ_COLS + j];
+        acc |= (uint64_t)(t >> (32 - g.p)) << (64 - g.p * (i + 1));
+    }
+    return (uint32_t)(acc >> 32);
 }
 
-__global__ void __launch_bounds__(256) k_q_sample(QArgs q) {
+__device__ __forceinline__ void cp_async8(uint64_t* dst, const uint64_t* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(static_cast<uint64_t>(__cvta_generic_to_global(src)))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int kN>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(kN) : "memory");
+}
+
+// kW: u64 words per lane, at least ceil(21R/2 / 32)
+template <int kW>
+__global__ void __launch_bounds__(kSampleThreads, 4) k_q_sample(QArgs q) {
+    extern __shared__ uint64_t q_cube[];  // (kSampleThreads / 32) x 2 x 21R/2 words
+    __shared__ uint32_t s_keys[kMaxKeyWords * GZ_COLS];
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t R = q.R, n_roots = q.ctr[C_ROOTS], nw = 21u * R / 2u, round = q.ctr[C_ROUND];
+    for (uint32_t i = threadIdx.x; i < 3 * q.geo.m2 * GZ_COLS; i += blockDim.x)
+        s_keys[i] = q.keys.at(kH2Words + i / GZ_COLS, round * GZ_COLS + i % GZ_COLS);
+    __syncthreads();
+    uint64_t* bufs = q_cube + (threadIdx.x >> 5) * 2 * nw;
     const uint64_t VV = (uint64_t)q.V * q.V;
     const uint32_t r0 = lane, r1 = lane + 32;
-    for (uint32_t ri = warp; ri < n_roots; ri += nwarps) {
-        const uint32_t c = q.roots[ri];
-        const uint32_t cnt = q.count[c];
-        const bool big = cnt > q.M;
-        uint64_t a0[GZ_COLS], a1[GZ_COLS];
-        uint32_t g0[GZ_COLS], g1[GZ_COLS];
+    // source block of component k of the batch when it has one source
+    auto single_src = [&](uint32_t cnt, uint32_t src) -> const uint64_t* {
+        if (cnt > q.M) return q.acc + (uint64_t)src * nw;
+        return reinterpret_cast<const uint64_t*>(q.s.cube(src, round));
+    };
+    auto fetch = [&](uint64_t* dst, const uint64_t* src) {
 #pragma unroll
-        for (int j = 0; j < GZ_COLS; ++j) {
-            a0[j] = a1[j] = 0;
-            g0[j] = g1[j] = 0;
+        for (int i = 0; i < kW; ++i) {
+            const uint32_t w = lane + 32u * i;
+            if (w < nw) cp_async8(dst + w, src + w);
         }
-        const uint32_t nsrc = big ? 1u : cnt;
-        const uint32_t my_node = (!big && lane < cnt) ? q.members[q.off[c] + lane] : 0u;
-        uint64_t* slot_base = big ? q.acc + (uint64_t)q.slot[c] * nw : nullptr;
-        for (uint32_t sidx = 0; sidx < nsrc; ++sidx) {
-            const uint64_t* A;
-            if (big) A = slot_base;
-            else A = reinterpret_cast<const uint64_t*>(q.s.cube(__shfl_sync(0xffffffffu, my_node, sidx), round));
-            const uint32_t* G = reinterpret_cast<const uint32_t*>(A + GZ_COLS * R);
+    };
+    // components per warp batch: up to kSampleBatch, fewer when the warps
+    // outnumber the batches (late rounds have few components)
+    const uint32_t bsz = max(1u, min(kSampleBatch, n_roots / nwarps));
+    for (uint32_t base = warp * bsz; base < n_roots; base += nwarps * bsz) {
+        const uint32_t nb = min(bsz, n_roots - base);
+        // lane k < nb: component base + k, its size, member offset and source
+        // (accumulator slot of a large component, else its first member)
+        uint32_t m_c = 0, m_cnt = 0, m_off = 0, m_src = 0;
+        if (lane < nb) {
+            m_c = q.roots[base + lane];
+            m_cnt = q.count[m_c];
+            m_off = q.off[m_c];
+            const uint32_t sl = q.slot[m_c];
+            m_src = m_cnt > q.M ? sl : q.members[m_off];
+        }
+        {
+            const uint32_t cnt = __shfl_sync(0xffffffffu, m_cnt, 0), src = __shfl_sync(0xffffffffu, m_src, 0);
+            if (cnt == 1 || cnt > q.M) fetch(bufs, single_src(cnt, src));
+            cp_async_commit();
+        }
+        for (uint32_t k = 0; k < nb; ++k) {
+            const uint32_t c = __shfl_sync(0xffffffffu, m_c, k);
+            const uint32_t cnt = __shfl_sync(0xffffffffu, m_cnt, k);
+            const uint32_t src = __shfl_sync(0xffffffffu, m_src, k);
+            // prefetch the next component of the batch into the other buffer
+            // (its previous contents were consumed before the last __syncwarp)
+            const uint32_t kn = k + 1 < nb ? k + 1 : k;
+            const uint32_t cnt_n = __shfl_sync(0xffffffffu, m_cnt, kn);
+            const uint32_t src_n = __shfl_sync(0xffffffffu, m_src, kn);
+            if (k + 1 < nb && (cnt_n == 1 || cnt_n > q.M)) fetch(bufs + ((k + 1) & 1) * nw, single_src(cnt_n, src_n));
+            cp_async_commit();
+            uint64_t* cube = bufs + (k & 1) * nw;
+            const uint32_t* cube_g = reinterpret_cast<const uint32_t*>(cube + GZ_COLS * R);
+            cp_async_wait<1>();  // component k's copies are done (this lane's)
+            if (cnt > q.M) {
+                uint64_t* slot = q.acc + (uint64_t)src * nw;
 #pragma unroll
+                for (int i = 0; i < kW; ++i) {
+                    const uint32_t w = lane + 32u * i;
+                    if (w < nw) slot[w] = 0;
+                }
+            } else if (cnt > 1) {
+                uint64_t acc[kW];
+                const uint64_t* A = reinterpret_cast<const uint64_t*>(q.s.cube(src, round));
+#pragma unroll
+                for (int i = 0; i < kW; ++i) {
+                    const uint32_t w = lane + 32u * i;
+                    acc[i] = w < nw ? __ldg(A + w) : 0ull;
+                }
+                const uint32_t off = __shfl_sync(0xffffffffu, m_off, k);
+                const uint32_t my_node = lane < cnt ? q.members[off + lane] : 0u;
+                for (uint32_t sidx = 1; sidx < cnt; ++sidx) {
+                    const uint64_t* B =
+                        reinterpret_cast<const uint64_t*>(q.s.cube(__shfl_sync(0xffffffffu, my_node, sidx), round));
+#pragma unroll
+                    for (int i = 0; i < kW; ++i) {
+                        const uint32_t w = lane + 32u * i;
+                        if (w < nw) acc[i] ^= __ldg(B + w);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < kW; ++i) {
+                    const uint32_t w = lane + 32u * i;
+                    if (w < nw) cube[w] = acc[i];
+                }
+            }
+            __syncwarp();
+            bool nz = false;
+            int64_t result = -1;  // warp-uniform
+            // columns in order; a column's rows come from the buffer only when
+            // it is scanned (most components stop at the first column)
             for (int j = 0; j < GZ_COLS; ++j) {
-                if (r0 < R) {
-                    a0[j] ^= A[r0 * GZ_COLS + j];
-                    g0[j] ^= G[r0 * GZ_COLS + j];
+                if (result >= 0) break;
+                // rows 32.. by a loop: lane l < R - 32 takes nested row 32 + l
+                uint64_t x1 = 0;
+                uint32_t y1 = 0;
+                for (uint32_t r = r1; r < R; ++r) {
+                    x1 ^= cube[r * GZ_COLS + j];
+                    y1 ^= cube_g[r * GZ_COLS + j];
                 }
-                if (r1 < R) {
-                    a1[j] ^= A[r1 * GZ_COLS + j];
-                    g1[j] ^= G[r1 * GZ_COLS + j];
-                }
-            }
-        }
-        if (big) {  // clear the slot for the next round (each word is read by its own lane only)
-            uint32_t* G = reinterpret_cast<uint32_t*>(slot_base + GZ_COLS * R);
+                uint64_t x0 = r0 < R ? cube[r0 * GZ_COLS + j] : 0ull;
+                uint32_t y0 = r0 < R ? cube_g[r0 * GZ_COLS + j] : 0u;
+                // suffix XOR over rows 0..31
 #pragma unroll
-            for (int j = 0; j < GZ_COLS; ++j) {
-                if (r0 < R) {
-                    slot_base[r0 * GZ_COLS + j] = 0;
-                    G[r0 * GZ_COLS + j] = 0;
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint32_t lo = __shfl_down_sync(0xffffffffu, (uint32_t)x0, off);
+                    const uint32_t hi = __shfl_down_sync(0xffffffffu, (uint32_t)(x0 >> 32), off);
+                    const uint32_t u0 = __shfl_down_sync(0xffffffffu, y0, off);
+                    if (lane + off < 32) {
+                        x0 ^= ((uint64_t)hi << 32) | lo;
+                        y0 ^= u0;
+                    }
                 }
-                if (r1 < R) {
-                    slot_base[r1 * GZ_COLS + j] = 0;
-                    G[r1 * GZ_COLS + j] = 0;
+                // rows 0..31 also take every row from 32 on (lane 0's x1)
+                const uint64_t carry_a = ((uint64_t)__shfl_sync(0xffffffffu, (uint32_t)(x1 >> 32), 0) << 32) |
+                                         __shfl_sync(0xffffffffu, (uint32_t)x1, 0);
+                const uint32_t carry_g = __shfl_sync(0xffffffffu, y1, 0);
+                x0 ^= carry_a;
+                y0 ^= carry_g;
+                // h2 is defined on edges: alpha must decode to u < v < V first
+                auto good = [&](uint64_t a, uint32_t g, uint32_t row) -> bool {
+                    if (row >= R || (a | g) == 0 || a >= VV) return false;
+                    // a < V^2: the high product underestimates a / V by at most one
+                    uint64_t qu = __umul64hi(a, q.vinv);
+                    uint64_t rem = a - qu * q.V;
+                    if (rem >= q.V) {
+                        ++qu;
+                        rem -= q.V;
+                    }
+                    const uint32_t uu = (uint32_t)qu, vv = (uint32_t)rem;
+                    if (uu >= vv) return false;
+                    if (g != round_checksum(s_keys, q.geo, (uint32_t)j, uu, vv)) return false;
+                    return (q.label[uu] == c) != (q.label[vv] == c);
+                };
+                // rows 32.. are almost always empty: their check runs only when not
+                const bool deep = __any_sync(0xffffffffu, r1 < R && (x1 | y1)) != 0;
+                nz |= deep || __any_sync(0xffffffffu, r0 < R && (x0 | y0)) != 0;
+                const uint32_t b0 = __ballot_sync(0xffffffffu, good(x0, y0, r0));
+                const uint32_t b1 = deep ? __ballot_sync(0xffffffffu, good(x1, y1, r1)) : 0u;
+                if (b0 | b1) {
+                    const uint32_t srcl = b0 ? (uint32_t)(__ffs(b0) - 1) : (uint32_t)(__ffs(b1) - 1);
+                    const uint64_t pick = b0 ? x0 : x1;
+                    result = (int64_t)(((uint64_t)__shfl_sync(0xffffffffu, (uint32_t)(pick >> 32), srcl) << 32) |
+                                       __shfl_sync(0xffffffffu, (uint32_t)pick, srcl));
                 }
+            }
+            __syncwarp();  // this buffer may be refilled by the next prefetch
+            if (lane == 0) {
+                int64_t r;
+                if (result >= 0) {
+                    r = result;
+                    atomicAdd(&q.ctr[C_EDGES], 1u);
+                } else if (nz) {
+                    r = -2;
+                    atomicAdd(&q.ctr[C_FAILS], 1u);
+                } else {
+                    r = -1;
+                }
+                q.res[c] = r;
+                if (q.trace) q.trace[(uint64_t)round * q.V + c] = r;
             }
         }
-        bool nz = false;
-        int64_t result = -1;  // warp-uniform
-#pragma unroll
-        for (int j = 0; j < GZ_COLS; ++j) {
-            if (result >= 0) continue;
-            uint64_t x0 = a0[j], x1 = a1[j];
-            uint32_t y0 = g0[j], y1 = g1[j];
-            // suffix XOR over rows, within each half of the warp's rows
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint64_t t1 = shfl_down64(x1, off);
-                const uint32_t u1 = __shfl_down_sync(0xffffffffu, y1, off);
-                const uint64_t t0 = shfl_down64(x0, off);
-                const uint32_t u0 = __shfl_down_sync(0xffffffffu, y0, off);
-                if (lane + off < 32) {
-                    x1 ^= t1;
-                    y1 ^= u1;
-                    x0 ^= t0;
-                    y0 ^= u0;
-                }
-            }
-            // rows 0..31 also take every row from 32 on
-            const uint64_t carry_a = ((uint64_t)__shfl_sync(0xffffffffu, (uint32_t)(x1 >> 32), 0) << 32) |
-                                     __shfl_sync(0xffffffffu, (uint32_t)x1, 0);
-            const uint32_t carry_g = __shfl_sync(0xffffffffu, y1, 0);
-            x0 ^= carry_a;
-            y0 ^= carry_g;
-            const uint32_t colj = round * GZ_COLS + j;
-            // h2 is defined on edges: alpha must decode to u < v < V first
-            auto good = [&](uint64_t a, uint32_t g, uint32_t row) -> bool {
-                if (row >= R || (a | g) == 0 || a >= VV) return false;
-                // a < V^2: the high product underestimates a / V by at most one
-                uint64_t qu = __umul64hi(a, q.vinv);
-                uint64_t rem = a - qu * q.V;
-                if (rem >= q.V) {
-                    ++qu;
-                    rem -= q.V;
-                }
-                const uint32_t uu = (uint32_t)qu, vv = (uint32_t)rem;
-                if (uu >= vv) return false;
-                if (g != edge_checksum(q.keys, q.geo, colj, uu, vv)) return false;
-                return (q.label[uu] == c) != (q.label[vv] == c);
-            };
-            nz |= __any_sync(0xffffffffu, (r0 < R && (x0 | y0)) || (r1 < R && (x1 | y1))) != 0;
-            const uint32_t b0 = __ballot_sync(0xffffffffu, good(x0, y0, r0));
-            const uint32_t b1 = __ballot_sync(0xffffffffu, good(x1, y1, r1));
-            if (b0 | b1) {
-                const uint32_t src = b0 ? (uint32_t)(__ffs(b0) - 1) : (uint32_t)(__ffs(b1) - 1);
-                const uint64_t pick = b0 ? x0 : x1;
-                result = (int64_t)(((uint64_t)__shfl_sync(0xffffffffu, (uint32_t)(pick >> 32), src) << 32) |
-                                   __shfl_sync(0xffffffffu, (uint32_t)pick, src));
-            }
-        }
-        if (lane == 0) {
-            int64_t r;
-            if (result >= 0) {
-                r = result;
-                atomicAdd(&q.ctr[C_EDGES], 1u);
-            } else if (nz) {
-                r = -2;
-                atomicAdd(&q.ctr[C_FAILS], 1u);
-            } else {
-                r = -1;
-            }
-            q.res[c] = r;
-            if (q.trace) q.trace[(uint64_t)round * q.V + c] = r;
-        }
+        cp_async_wait<0>();
     }
 }
 
@@ -430,6 +609,10 @@ __global__ void k_q_ncc(QArgs q) {
 
 // ------------------------------------------------------------------ host side
 
+// dynamic shared memory of the sampler: two CubeSketch buffers per warp
+static size_t sample_smem(uint32_t R) { return (size_t)(kSampleThreads / 32) * 2 * (21u * R / 2u) * sizeof(uint64_t); }
+static uint32_t merge_threads(uint32_t R) { return (21u * R / 2u + 31) / 32 * 32; }  // <= kMergeMaxThreads
+
 gz_status query_setup(gz_handle* h) {
     if (h->query_ready) return GZ_OK;
     const size_t V = h->V;
@@ -456,6 +639,29 @@ gz_status query_setup(gz_handle* h) {
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_check(h, e, "query scratch allocation");
+    // The sampler's two buffers per warp exceed the default 48 KB of dynamic
+    // shared memory for R > 36.  The limit is a property of the kernel, shared
+    // by every handle of the process (and set while other threads may launch
+    // it), so it is raised once, to what the largest R (64) needs.
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        const int smem = (int)sample_smem(64);
+        attr_err = cudaFuncSetAttribute(k_q_sample<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(k_q_sample<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(k_q_sample<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(k_q_sample<21>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    });
+    e = attr_err;
+    // the merge runs one wave of resident blocks
+    int occ = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_q_merge, (int)merge_threads(h->R), 0);
+    if (e != cudaSuccess) return cuda_check(h, e, "query kernel attributes");
+    h->q_merge_occ = (uint32_t)std::max(occ, 1);
     h->query_ready = true;
     return GZ_OK;
 }
@@ -499,8 +705,6 @@ static QArgs query_args(gz_handle* h) {
     return q;
 }
 
-constexpr uint32_t kTpb = 256;
-
 // query start: singletons, counters, clear accumulator slots (the sampler
 // clears every slot it reads; this only guards against a query that stopped
 // on an error between a merge and its sampler)
@@ -515,17 +719,36 @@ static void enqueue_grouping(gz_handle* h, const QArgs& q, cudaStream_t stm) {
     const uint32_t V = h->V, gV = grid_for(h, V, kTpb);
     cudaMemsetAsync(h->q_count, 0, (size_t)(V + 1) * sizeof(uint32_t), stm);
     cudaMemsetAsync(h->q_ctr, 0, 4 * sizeof(uint32_t), stm);  // roots, big, edges, fails
-    k_q_count<<<gV, kTpb, 0, stm>>>(q);
+    // one block per span of kGroupSpan vertices
+    const uint32_t gS = (uint32_t)std::min<uint64_t>(((uint64_t)V + kGroupSpan - 1) / kGroupSpan,
+                                                     (uint64_t)h->sm_count * 8);
+    k_q_count<<<gS, kGroupThreads, 0, stm>>>(q);
     launch_scan(h->q_count, h->q_off, h->q_cursor, nullptr, V, stm, h->d_scan_tmp);
-    k_q_group<<<gV, kTpb, 0, stm>>>(q);
+    k_q_group<<<gS, kGroupThreads, 0, stm>>>(q);
     k_q_roots<<<gV, kTpb, 0, stm>>>(q);
-    // one thread per word of a CubeSketch (one pass over its 21R/2 words)
-    const uint32_t mt = std::min<uint32_t>(1024, (21u * h->R / 2u + 31) / 32 * 32);
-    k_q_merge<<<std::min<uint32_t>((V + kMergeChunk - 1) / kMergeChunk, h->sm_count * (2048 / mt)), mt, 0, stm>>>(q);
+    // one thread per u64 word of a CubeSketch, contiguous member ranges, one
+    // wave of blocks
+    const uint32_t mt = merge_threads(h->R);
+    const uint32_t nblk = std::max<uint32_t>(1, std::min<uint32_t>((V + 31) / 32, h->sm_count * h->q_merge_occ));
+    const uint32_t per_block = (V + nblk - 1) / nblk;
+    k_q_merge<<<nblk, mt, 0, stm>>>(q, per_block);
+}
+
+// u64 words per lane of the sampler's staging loads
+static int sample_words(uint32_t R) {
+    const uint32_t w = (21u * R / 2u + 31) / 32;
+    return w <= 6 ? 6 : w <= 12 ? 12 : w <= 16 ? 16 : 21;
 }
 
 static void enqueue_sample(gz_handle* h, const QArgs& q, cudaStream_t stm) {
-    k_q_sample<<<h->sm_count * 16, 256, 0, stm>>>(q);
+    const size_t smem = sample_smem(h->R);
+    const uint32_t grid = h->sm_count * 16;
+    switch (sample_words(h->R)) {
+    case 6: k_q_sample<6><<<grid, kSampleThreads, smem, stm>>>(q); break;
+    case 12: k_q_sample<12><<<grid, kSampleThreads, smem, stm>>>(q); break;
+    case 16: k_q_sample<16><<<grid, kSampleThreads, smem, stm>>>(q); break;
+    default: k_q_sample<21><<<grid, kSampleThreads, smem, stm>>>(q); break;
+    }
 }
 
 static void enqueue_link(gz_handle* h, const QArgs& q, cudaStream_t stm) {

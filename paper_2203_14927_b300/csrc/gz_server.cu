@@ -1,14 +1,20 @@
 // gz_server.cu -- serving many independent graphs on one GPU (host code only;
 // the device work is the library's ingestion and query kernels).
 //
-// State: every graph has a FIFO of requests and is WAITING (no device memory),
-// RESIDENT (a gz_handle holds its sketches) or RELEASED.  `slots` worker
-// threads, each with its own CUDA stream, loop: pick the graph whose oldest
-// pending request is oldest among the graphs that are resident and idle or
-// that fit in the remaining memory budget, mark it busy, take up to
-// max_batch of its requests, serve them in order on the worker's stream
-// (creating the handle first if the graph is not resident), report the
-// completions, and release the graph's memory if it was closed and drained.
+// State: every graph has a FIFO of requests and is WAITING (no device memory
+// yet), RESIDENT (a gz_handle holds its sketches), EVICTED (its sketches wait
+// in pinned host memory as a checkpoint) or RELEASED.  `slots` worker
+// threads, each with its own CUDA stream, loop:
+//   - serve a resident idle graph with pending requests (oldest request
+//     first): finishing resident graphs is what frees memory;
+//   - else admit the waiting or evicted graph with the oldest request that
+//     fits in the remaining budget (create, or restore its checkpoint);
+//   - else, when such a graph has waited kEvictAfterMs, evict the least
+//     recently used idle resident graph (checkpoint to pinned host memory,
+//     free its device memory) to make room;
+// taking up to max_batch requests of a graph, serving them in order on the
+// worker's stream, reporting the completions, and releasing the graph's
+// memory once it is closed and drained.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,7 +46,10 @@ struct Request {
     double submit_ms = 0;
 };
 
-enum GraphState { WAITING = 0, RESIDENT = 1, RELEASED = 2 };
+enum GraphState { WAITING = 0, RESIDENT = 1, RELEASED = 2, EVICTED = 3 };
+
+// a graph that cannot be admitted for this long evicts an idle resident one
+constexpr double kEvictAfterMs = 20.0;
 
 struct Graph {
     uint32_t V = 0;
@@ -52,6 +61,10 @@ struct Graph {
     bool busy = false, closed = false;
     gz_handle* h = nullptr;
     std::deque<Request> queue;
+    double last_used_ms = 0;         // end of its last service
+    void* ckpt = nullptr;            // pinned host checkpoint of an evicted graph
+    size_t ckpt_bytes = 0;
+    uint64_t evictions = 0;
 };
 
 }  // namespace
@@ -67,7 +80,12 @@ struct gz_server {
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;
     uint64_t next_req = 1;
-    uint64_t resident_bytes = 0, peak_bytes = 0, completed = 0;
+    uint64_t resident_bytes = 0, peak_bytes = 0, completed = 0, evictions = 0;
+    uint64_t evicting_bytes = 0;  // resident bytes of graphs being checkpointed out
+    double evict_ms = 0, restore_ms = 0;
+    // pinned checkpoint buffers of released graphs, kept for later evictions
+    // (pinning host memory costs far more than the copy into it)
+    std::vector<std::pair<void*, size_t>> spare_ckpt;
     uint64_t outstanding = 0;  // submitted, not completed
     uint32_t busy_workers = 0;
     bool stop = false;
@@ -91,23 +109,89 @@ uint64_t graph_bytes(uint32_t V, const gz_config* cfg) {
     return b + (uint64_t)V * 96 + (uint64_t)gz::query_slots(V) * 84ull * R + (4ull << cl) * 4;
 }
 
-// pick under the lock: a resident idle graph or an admissible waiting one,
-// whichever has the oldest pending request
-Graph* pick(gz_server* s, uint32_t* gid) {
-    Graph* best = nullptr;
-    double best_t = 0;
+enum Task { NONE = 0, SERVE = 1, EVICT = 2 };
+
+// Pick work under the lock (see the top of the file for the order).
+Task pick(gz_server* s, uint32_t* gid) {
+    const double now = s->now_ms();
+    int best = -1, adm = -1, starving = -1, lru = -1;
     for (size_t i = 0; i < s->graphs.size(); ++i) {
         Graph* g = s->graphs[i].get();
-        if (g->busy || g->queue.empty() || g->state == RELEASED) continue;
-        if (g->state == WAITING && s->resident_bytes + g->bytes > s->cfg.hbm_budget) continue;
+        if (g->busy || g->state == RELEASED) continue;
+        if (g->queue.empty()) {
+            if (g->state == RESIDENT && !g->closed &&
+                (lru < 0 || g->last_used_ms < s->graphs[lru]->last_used_ms))
+                lru = (int)i;
+            continue;
+        }
         const double t = g->queue.front().submit_ms;
-        if (!best || t < best_t) {
-            best = g;
-            best_t = t;
-            *gid = (uint32_t)i;
+        if (g->state == RESIDENT) {
+            if (best < 0 || t < s->graphs[best]->queue.front().submit_ms) best = (int)i;
+        } else if (s->resident_bytes + g->bytes <= s->cfg.hbm_budget) {
+            if (adm < 0 || t < s->graphs[adm]->queue.front().submit_ms) adm = (int)i;
+        } else if (now - t >= kEvictAfterMs) {
+            if (starving < 0 || t < s->graphs[starving]->queue.front().submit_ms) starving = (int)i;
         }
     }
-    return best;
+    // resident graphs first, unless an admissible graph has waited
+    // kEvictAfterMs longer than the oldest resident request (no starvation)
+    if (adm >= 0 && (best < 0 || s->graphs[adm]->queue.front().submit_ms + kEvictAfterMs <
+                                     s->graphs[best]->queue.front().submit_ms)) {
+        *gid = (uint32_t)adm;
+        return SERVE;
+    }
+    if (best >= 0) {
+        *gid = (uint32_t)best;
+        return SERVE;
+    }
+    // evict only what the oldest starving graph still lacks once the
+    // evictions under way have finished
+    if (starving >= 0 && lru >= 0 &&
+        s->resident_bytes - s->evicting_bytes + s->graphs[starving]->bytes > s->cfg.hbm_budget) {
+        *gid = (uint32_t)lru;
+        return EVICT;
+    }
+    return NONE;
+}
+
+// Checkpoint an idle resident graph to pinned host memory and free its
+// device memory (outside the lock; the graph is marked busy).
+gz_status evict(gz_server* s, Graph* g) {
+    size_t need = 0;
+    gz_status st = gz_checkpoint_bytes(g->h, &need);
+    if (st == GZ_OK && g->ckpt_bytes < need) {
+        void* old = g->ckpt;
+        const size_t old_bytes = g->ckpt_bytes;
+        g->ckpt = nullptr;
+        g->ckpt_bytes = 0;
+        {  // the smallest spare buffer that fits, else a new one
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (old) s->spare_ckpt.emplace_back(old, old_bytes);
+            int best = -1;
+            for (size_t i = 0; i < s->spare_ckpt.size(); ++i)
+                if (s->spare_ckpt[i].second >= need &&
+                    (best < 0 || s->spare_ckpt[i].second < s->spare_ckpt[best].second))
+                    best = (int)i;
+            if (best >= 0) {
+                g->ckpt = s->spare_ckpt[best].first;
+                g->ckpt_bytes = s->spare_ckpt[best].second;
+                s->spare_ckpt.erase(s->spare_ckpt.begin() + best);
+            }
+        }
+        if (!g->ckpt) {
+            if (cudaMallocHost(&g->ckpt, need) != cudaSuccess) {
+                g->ckpt = nullptr;
+                return GZ_ENOMEM;
+            }
+            g->ckpt_bytes = need;
+        }
+    }
+    if (st == GZ_OK) st = gz_checkpoint(g->h, g->ckpt, g->ckpt_bytes);
+    if (st == GZ_OK) {
+        gz_destroy(g->h);
+        g->h = nullptr;
+    }
+    return st;
 }
 
 void worker_main(gz_server* s, int slot) {
@@ -117,19 +201,54 @@ void worker_main(gz_server* s, int slot) {
         uint32_t gid = 0;
         Graph* g = nullptr;
         std::vector<Request> batch;
-        bool admit = false;
+        bool admit = false, restore = false;
         {
             std::unique_lock<std::mutex> lk(s->mu);
+            Task task = NONE;
             for (;;) {
-                g = pick(s, &gid);
-                if (g || s->stop) break;
-                s->work_cv.wait(lk);
+                task = pick(s, &gid);
+                if (task != NONE || s->stop) break;
+                // an admission that waits for memory is re-examined after
+                // kEvictAfterMs even when nothing else happens
+                s->work_cv.wait_for(lk, std::chrono::milliseconds((int)kEvictAfterMs));
             }
-            if (!g) return;  // stopping and nothing left to do
+            if (task == NONE) return;  // stopping and nothing left to do
+            g = s->graphs[gid].get();
             g->busy = true;
             ++s->busy_workers;
-            if (g->state == WAITING) {
-                admit = true;
+            if (task == EVICT) {
+                s->evicting_bytes += g->bytes;
+                lk.unlock();
+                gz_set_stream(g->h, stream);
+                const double te = s->now_ms();
+                const gz_status est = evict(s, g);
+                lk.lock();
+                s->evict_ms += s->now_ms() - te;
+                g->busy = false;
+                --s->busy_workers;
+                s->evicting_bytes -= g->bytes;
+                if (est == GZ_OK) {
+                    g->state = EVICTED;
+                    s->resident_bytes -= g->bytes;
+                    ++g->evictions;
+                    ++s->evictions;
+                    if (g->closed && g->queue.empty()) {  // closed while it was copied out
+                        g->state = RELEASED;
+                        s->spare_ckpt.emplace_back(g->ckpt, g->ckpt_bytes);
+                        g->ckpt = nullptr;
+                        g->ckpt_bytes = 0;
+                    }
+                } else {
+                    s->last_err = "eviction of graph " + std::to_string(gid) + " failed";
+                }
+                lk.unlock();
+                s->work_cv.notify_all();
+                s->done_cv.notify_all();
+                continue;
+            }
+            if (g->state == WAITING || g->state == EVICTED) {
+                admit = g->state == WAITING;
+                restore = g->state == EVICTED;
                 g->state = RESIDENT;  // memory is reserved now, taken below
                 s->resident_bytes += g->bytes;
                 s->peak_bytes = std::max(s->peak_bytes, s->resident_bytes);
@@ -144,6 +263,12 @@ void worker_main(gz_server* s, int slot) {
         if (admit) {
             create_st = gz_create(g->V, g->seed, g->has_cfg ? &g->cfg : nullptr, stream, &g->h);
             if (create_st != GZ_OK) g->h = nullptr;
+        } else if (restore) {
+            const double tr = s->now_ms();
+            create_st = gz_restore(g->ckpt, g->ckpt_bytes, g->has_cfg ? &g->cfg : nullptr, stream, &g->h);
+            if (create_st != GZ_OK) g->h = nullptr;
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->restore_ms += s->now_ms() - tr;
         } else if (g->h) {
             gz_set_stream(g->h, stream);  // the previous worker synchronised before releasing it
         }
@@ -203,6 +328,7 @@ void worker_main(gz_server* s, int slot) {
             s->completed += done.size();
             s->outstanding -= done.size();
             g->busy = false;
+            g->last_used_ms = s->now_ms();
             --s->busy_workers;
             if (create_st != GZ_OK) {
                 // the graph cannot be admitted: its queued requests fail too
@@ -225,6 +351,9 @@ void worker_main(gz_server* s, int slot) {
                 g->state = RELEASED;
                 to_free = g->h;
                 g->h = nullptr;
+                if (g->ckpt) s->spare_ckpt.emplace_back(g->ckpt, g->ckpt_bytes);
+                g->ckpt = nullptr;
+                g->ckpt_bytes = 0;
             }
         }
         if (to_free) gz_destroy(to_free);
@@ -293,8 +422,11 @@ gz_status gz_server_destroy(gz_server* s) {
     }
     s->work_cv.notify_all();
     for (std::thread& t : s->workers) t.join();
-    for (auto& g : s->graphs)
+    for (auto& g : s->graphs) {
         if (g->h) gz_destroy(g->h);
+        if (g->ckpt) cudaFreeHost(g->ckpt);
+    }
+    for (auto& b : s->spare_ckpt) cudaFreeHost(b.first);
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
     delete s;
     return GZ_OK;
@@ -312,6 +444,9 @@ gz_status gz_server_add_graph(gz_server* s, uint32_t V, uint64_t seed, const gz_
     // serving requests are small batches: partition buffers for 2^20 updates
     // unless the caller chose otherwise (larger batches are split by the call)
     if (g->cfg.chunk_log2 == 0) g->cfg.chunk_log2 = 20;
+    // the server overlaps graphs on its worker streams; a graph's own
+    // partition/update pipeline would only add a stream and buffers per graph
+    g->cfg.no_pipeline = 1;
     g->has_cfg = true;
     g->bytes = graph_bytes(V, &g->cfg);
     std::lock_guard<std::mutex> lk(s->mu);
@@ -380,6 +515,9 @@ gz_status gz_server_close_graph(gz_server* s, uint32_t graph) {
             g->state = RELEASED;
             to_free = g->h;
             g->h = nullptr;
+            if (g->ckpt) s->spare_ckpt.emplace_back(g->ckpt, g->ckpt_bytes);
+            g->ckpt = nullptr;
+            g->ckpt_bytes = 0;
         }
     }
     if (to_free) gz_destroy(to_free);
@@ -416,6 +554,21 @@ const char* gz_server_last_error(gz_server* s) {
     return copy.c_str();
 }
 
+gz_status gz_server_set_budget(gz_server* s, uint64_t hbm_budget) {
+    if (!s || !hbm_budget) return GZ_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->cfg.hbm_budget = hbm_budget;
+    }
+    cudaMemPool_t pool;
+    uint64_t cur = 0;
+    if (cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) == cudaSuccess && cur < hbm_budget)
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &hbm_budget);
+    s->work_cv.notify_all();
+    return GZ_OK;
+}
+
 gz_status gz_server_stats_read(gz_server* s, gz_server_stats* out) {
     if (!s || !out) return GZ_EINVAL;
     std::lock_guard<std::mutex> lk(s->mu);
@@ -427,9 +580,13 @@ gz_status gz_server_stats_read(gz_server* s, gz_server_stats* out) {
     for (auto& g : s->graphs) {
         out->resident_graphs += g->state == RESIDENT;
         out->waiting_graphs += g->state == WAITING && !g->queue.empty();
+        out->evicted_graphs += g->state == EVICTED;
         out->pending_requests += (uint32_t)g->queue.size();
     }
     out->completed_requests = s->completed;
+    out->evictions = s->evictions;
+    out->evict_ms = s->evict_ms;
+    out->restore_ms = s->restore_ms;
     return GZ_OK;
 }
 

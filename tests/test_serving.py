@@ -118,3 +118,59 @@ def test_server_rejects_graph_beyond_budget_and_bad_ids():
     srv.close_graph(gid)
     assert gz.lib().gz_server_submit_query(srv._s, gid, None, None) == gz.GZ_EINVAL
     srv.close()
+
+
+def _server_graph_bytes(V):
+    """Device bytes the server reserves for a graph of V nodes (sketches,
+    ingest scratch for 2^20-update batches, query scratch, host staging)."""
+    import ctypes
+    c = gz.Config()
+    c.chunk_log2 = 20
+    c.no_pipeline = 1
+    b = ctypes.c_size_t()
+    gz.lib().gz_memory_bytes(V, ctypes.byref(c), ctypes.byref(b))
+    K, R = gz.geometry(V)
+    return b.value + V * 96 + (V // 33 + 1) * 84 * R + (16 << 20)
+
+
+def test_idle_graphs_are_evicted_and_restored_bit_for_bit():
+    """A budget for one graph: a graph that waits for memory evicts the idle
+    resident one (checkpoint to host), whose next request restores it; each
+    graph's results still equal its results alone."""
+    rng = np.random.default_rng(5)
+    graphs = [_graph_requests(i, rng) for i in range(2)]
+    want = [_alone(V, seed, reqs) for V, seed, reqs in graphs]
+    budget = int(1.5 * max(_server_graph_bytes(V) for V, _, _ in graphs))
+    srv = gz.Server(hbm_budget=budget, slots=2, max_batch=4)
+    gids = [srv.add_graph(V, seed) for V, seed, _ in graphs]
+    got = {0: [], 1: []}
+
+    def run(i, reqs):
+        for r in reqs:
+            if r[0] == "u":
+                srv.submit_update(gids[i], r[1], r[2])
+            else:
+                srv.submit_query(gids[i])
+        srv.drain()
+        for c in srv.poll(1000):
+            assert c["status"] in (gz.GZ_OK, gz.GZ_ESKETCH_FAIL), srv.last_error()
+            if c["kind"] == 1:
+                got[c["graph"]].append((c["labels"], c["status"]))
+
+    halves = [(r[: len(r) // 2], r[len(r) // 2:]) for _, _, r in graphs]
+    run(0, halves[0][0])  # graph 0 resident, then idle
+    run(1, halves[1][0])  # graph 1 waits, evicts graph 0
+    run(0, halves[0][1])  # graph 0 restored from its checkpoint, graph 1 evicted
+    run(1, halves[1][1])  # and back
+    for i in range(2):
+        srv.close_graph(gids[i])
+    srv.drain()
+    st = srv.stats()
+    assert st["evictions"] >= 3, st
+    assert st["peak_resident_bytes"] <= budget
+    assert st["resident_bytes"] == 0 and st["evicted_graphs"] == 0
+    srv.close()
+    for i in range(2):
+        assert len(got[i]) == len(want[i])
+        for (lab, status), (wl, ws) in zip(got[i], want[i]):
+            assert status == ws and np.array_equal(lab, wl), i
