@@ -41,13 +41,14 @@ WORKLOADS = {
 }
 CHUNK_LOG2 = 24
 
-# DRAM bytes per launch of k_batched from one ncu capture (one-pass
-# dram__bytes_read.sum + dram__bytes_write.sum) of this bench's own step; valid
-# only for the kernel source it was taken with (kernel_sha) and its configuration.
+# DRAM bytes per update of k_batched from one ncu capture (one-pass
+# dram__bytes_read.sum + dram__bytes_write.sum, two full 2^26-update launches
+# of this bench's own step); valid only for the kernel source it was taken with
+# (kernel_sha) and its configuration.
 TRAFFIC = {
-    "kron17": {"sha": "1c4a7036d029efcc",
-               "cfg": {"smem_mode": 1, "tile_records": 512, "smem_rows": 12, "ctas_per_sm": 0, "chunk_log2": 26},
-               "bytes_per_launch": 9.667e9, "updates_per_launch": 66592033,
+    "kron17": {"sha": "88d5cd4044072f1f",
+               "cfg": {"smem_mode": 1, "tile_records": 512, "smem_rows": 16, "ctas_per_sm": 0, "chunk_log2": 26},
+               "bytes_per_update": 140.92,
                "source": "profiles/k_batched_kron17_dram.md"},
 }
 
@@ -77,7 +78,23 @@ def measured_traffic(workload: str, cfg: dict, kernel: str):
         return None, "kernel sources changed since the ncu capture"
     if any(cfg.get(k) != v for k, v in t["cfg"].items()):
         return None, f"ncu capture taken at config {t['cfg']}"
-    return t["bytes_per_launch"], t["source"]
+    return t["bytes_per_update"], t["source"]
+
+
+def nvtx_push(name: str):
+    try:
+        import torch
+        torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
+def nvtx_pop():
+    try:
+        import torch
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
 
 
 def log(*a):
@@ -390,8 +407,10 @@ def run_ours(args, rank: int, world: int):
         if dist:
             dist.barrier()
         ev0.record(stream)
+        nvtx_push("timed")  # lets a profiler take the timed steps' kernels alone (--nvtx-include timed/)
         for _ in range(args.steps):
             ncc, st = step()
+        nvtx_pop()
         ev1.record(stream)
         torch.cuda.synchronize()
         if dist:
@@ -420,7 +439,8 @@ def run_ours(args, rank: int, world: int):
     # buckets as rows_flushed).  The full-sketch bound, one read and write of
     # every node sketch per chunk, overstates it whenever nodes touch few rows.
     rows_per_launch = prof["rows_flushed"] / launches
-    traffic, traffic_note = measured_traffic(args.workload, cfg, args.kernel)
+    traffic_per_update, traffic_note = measured_traffic(args.workload, cfg, args.kernel)
+    traffic = traffic_per_update * upd_per_launch if traffic_per_update else None
     hbm_bytes = 8.0 * upd_per_launch + 24.0 * rows_per_launch
     hbm = {"bound": "hbm", "achieved": hbm_bytes / sec / 1e9, "peak": peak, "unit": "GB/s",
            "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
@@ -484,14 +504,19 @@ def run_ours(args, rank: int, world: int):
 
     # --- query latency -----------------------------------------------------------
     qs = [st["ms"]] if args.queries == 0 else []
+    if args.trace_queries:
+        g.enable_trace(True)  # host-driven rounds: a profiler lists every round's kernels
+    qc = []  # the library's own clock around the call (graph launch to labels on the host)
     for _ in range(args.queries):
         t1 = time.perf_counter()
         labels, ncc, st = g.connected_components()
         qs.append((time.perf_counter() - t1) * 1000.0)
+        qc.append(st["ms"])
     qs.sort()
     query = {"p50_ms": float(np.percentile(qs, 50)), "p99_ms": float(np.percentile(qs, 99)),
              "n": len(qs), "rounds": st["rounds"], "components": ncc, "fails_last": st["fails_last"],
-             "in_step_ms": qtimes}
+             "in_step_ms": qtimes, "host_driven_trace": bool(args.trace_queries),
+             "library_p50_ms": float(np.percentile(qc, 50)) if qc else None}
 
     # --- end to end through host buffers -------------------------------------
     e2e = None
@@ -1040,6 +1065,8 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--kernel", choices=["batched", "plain"], default="batched")
     ap.add_argument("--queries", type=int, default=20)
+    ap.add_argument("--trace-queries", action="store_true",
+                    help="run the --queries extra CC queries host-driven with the per-round trace (for profiling)")
     ap.add_argument("--paper-design-log2", type=int, default=22,
                     help="stream prefix (log2 updates) for the OpenMP paper-design CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

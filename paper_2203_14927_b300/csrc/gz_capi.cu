@@ -232,6 +232,7 @@ gz_status gz_destroy(gz_handle* h) {
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, h->stream);
     delete[] h->h_ctr;
+    if (h->h_labels) cudaFreeHost(h->h_labels);
     if (h->q_graph_exec) cudaGraphExecDestroy(h->q_graph_exec);
     if (h->q_graph) cudaGraphDestroy(h->q_graph);
     for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);

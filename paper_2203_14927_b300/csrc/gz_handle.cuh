@@ -86,6 +86,7 @@ struct gz_handle {
              *q_slot = nullptr, *q_F = nullptr, *q_F2 = nullptr,
              *q_M = nullptr, *q_M2 = nullptr, *q_flag = nullptr, *q_pos = nullptr,
              *q_forest = nullptr, *q_ctr = nullptr, *h_ctr = nullptr;
+    uint32_t* h_labels = nullptr;  // pinned, V words: labels on their way to the caller
     int64_t* q_res = nullptr;
     uint64_t* q_acc = nullptr;     // per big component: XOR of its members' CubeSketch
     uint32_t q_slots_cap = 0;

@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstring>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -102,7 +103,9 @@ __global__ void k_q_init(QArgs q) {
 // whether another round runs (a sampled edge and a fresh CubeSketch left), and
 // advance the round index.  With use_cond the decision also sets the
 // condition of the graph's WHILE node.
-__global__ void k_q_next(QArgs q, cudaGraphConditionalHandle cond, int use_cond) {
+// The per-round counters (roots, large components, edges, FAIL results) are
+// cleared here for the next round.
+__device__ __forceinline__ void round_end(const QArgs& q, cudaGraphConditionalHandle cond, int use_cond) {
     const uint32_t r = q.ctr[C_ROUND], e = q.ctr[C_EDGES], f = q.ctr[C_FAILS];
     q.ctr[C_ROUNDS] = r + 1;
     q.ctr[C_FLAST] = f;
@@ -111,8 +114,11 @@ __global__ void k_q_next(QArgs q, cudaGraphConditionalHandle cond, int use_cond)
     const uint32_t go = e > 0 && r + 1 < q.K;
     q.ctr[C_GO] = go;
     q.ctr[C_ROUND] = r + 1;
+    q.ctr[C_ROOTS] = q.ctr[C_BIG] = q.ctr[C_EDGES] = q.ctr[C_FAILS] = 0;
     if (use_cond) cudaGraphSetConditional(cond, go);
 }
+
+__global__ void k_q_next(QArgs q, cudaGraphConditionalHandle cond, int use_cond) { round_end(q, cond, use_cond); }
 
 __global__ void k_fill64(int64_t* p, uint64_t n, int64_t val) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -584,7 +590,7 @@ __global__ void k_q_forest_advance(QArgs q, const uint32_t* pos) {
     q.ctr[C_FOREST] += pos[q.V];
 }
 
-// new component of every old root (its set's minimum vertex id) ...
+// New component of every old root (its set's minimum vertex id) ...
 __global__ void k_q_newroot(QArgs q, uint32_t* newroot) {
     const uint32_t n_roots = q.ctr[C_ROOTS];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_roots; i += gridDim.x * blockDim.x) {
@@ -593,10 +599,18 @@ __global__ void k_q_newroot(QArgs q, uint32_t* newroot) {
     }
 }
 
-// ... then every vertex follows its old root
-__global__ void k_q_relabel(QArgs q, const uint32_t* newroot) {
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < q.V; v += gridDim.x * blockDim.x)
+// ... then every vertex follows its old root and clears its counter for the
+// next round's grouping.  (A find per vertex instead would walk the same
+// few root chains from every member of a large component at once.)  With
+// end_round (the query graph) the first thread also ends the round
+// (round_end): it only touches counters that the sampler and k_q_newroot
+// have finished with.
+__global__ void k_q_relabel(QArgs q, const uint32_t* newroot, cudaGraphConditionalHandle cond, int end_round) {
+    if (end_round && blockIdx.x == 0 && threadIdx.x == 0) round_end(q, cond, 1);
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < q.V; v += (uint64_t)gridDim.x * blockDim.x) {
         q.label[v] = newroot[q.label[v]];
+        q.count[v] = 0;
+    }
 }
 
 __global__ void k_q_ncc(QArgs q) {
@@ -612,6 +626,8 @@ __global__ void k_q_ncc(QArgs q) {
 // dynamic shared memory of the sampler: two CubeSketch buffers per warp
 static size_t sample_smem(uint32_t R) { return (size_t)(kSampleThreads / 32) * 2 * (21u * R / 2u) * sizeof(uint64_t); }
 static uint32_t merge_threads(uint32_t R) { return (21u * R / 2u + 31) / 32 * 32; }  // <= kMergeMaxThreads
+
+constexpr uint32_t kPinnedLabels = 1u << 17;  // graphs this large stage their labels in pinned memory
 
 gz_status query_setup(gz_handle* h) {
     if (h->query_ready) return GZ_OK;
@@ -636,6 +652,14 @@ gz_status query_setup(gz_handle* h) {
         // short-lived handles (a server creates and releases many)
         h->h_ctr = new (std::nothrow) uint32_t[C_N];
         if (!h->h_ctr) return set_error(h, GZ_ENOMEM, "query counters");
+        // Large graphs' labels come back through a pinned buffer: a copy of
+        // 2^17 or more labels into pageable memory goes through the driver's
+        // staging buffers and takes as long as the last Boruvka rounds.
+        // Small graphs (a server makes and frees many) copy directly.
+        if (V >= kPinnedLabels) {
+            e = cudaMallocHost(&h->h_labels, V * sizeof(uint32_t));
+            if (e != cudaSuccess) h->h_labels = nullptr;
+        }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_check(h, e, "query scratch allocation");
@@ -717,8 +741,8 @@ static void enqueue_start(gz_handle* h, const QArgs& q, cudaStream_t stm) {
 // round 0 starts from singletons)
 static void enqueue_grouping(gz_handle* h, const QArgs& q, cudaStream_t stm) {
     const uint32_t V = h->V, gV = grid_for(h, V, kTpb);
-    cudaMemsetAsync(h->q_count, 0, (size_t)(V + 1) * sizeof(uint32_t), stm);
-    cudaMemsetAsync(h->q_ctr, 0, 4 * sizeof(uint32_t), stm);  // roots, big, edges, fails
+    // the counters start at zero: the previous round's relabel cleared them
+    // (count[0..V)), and so did its round end (roots, big, edges, fails)
     // one block per span of kGroupSpan vertices
     const uint32_t gS = (uint32_t)std::min<uint64_t>(((uint64_t)V + kGroupSpan - 1) / kGroupSpan,
                                                      (uint64_t)h->sm_count * 8);
@@ -755,21 +779,23 @@ static void enqueue_link(gz_handle* h, const QArgs& q, cudaStream_t stm) {
     k_q_link<<<grid_for(h, h->V, kTpb), kTpb, 0, stm>>>(q);
 }
 
-// new component of every old root, then every vertex follows its old root
-// (no-ops after a round without a sampled edge: no union happened)
-static void enqueue_relabel(gz_handle* h, const QArgs& q, cudaStream_t stm) {
+// new component of every old root, then every vertex follows its old root (a
+// no-op after a round without a sampled edge: no union happened); in the
+// query graph the relabel also ends the round
+static void enqueue_relabel(gz_handle* h, const QArgs& q, cudaStream_t stm, cudaGraphConditionalHandle cond,
+                            int end_round) {
     const uint32_t gV = grid_for(h, h->V, kTpb);
     k_q_newroot<<<gV, kTpb, 0, stm>>>(q, h->q_cursor);
-    k_q_relabel<<<gV, kTpb, 0, stm>>>(q, h->q_cursor);
+    k_q_relabel<<<gV, kTpb, 0, stm>>>(q, h->q_cursor, cond, end_round);
 }
 
 // kernels of a query run as one CUDA graph: start, round 0, WHILE(another
 // round) { round }, component count
-constexpr uint64_t kLaunchesStartEnd = 2, kLaunchesRound0 = 5, kLaunchesRound = 11;
+constexpr uint64_t kLaunchesStartEnd = 2, kLaunchesRound0 = 4, kLaunchesRound = 10;
 
 // The CC query as one CUDA graph, captured once per handle: round 0, then a
-// conditional WHILE node whose body is one more round; k_q_next at the end of
-// every round sets the node's condition on the device, so the host waits once
+// conditional WHILE node whose body is one more round; the relabel kernel at
+// the end of every round sets the node's condition on the device, so the host waits once
 // per query instead of once per round.
 static gz_status build_query_graph(gz_handle* h) {
     const QArgs q = query_args(h);
@@ -783,11 +809,10 @@ static gz_status build_query_graph(gz_handle* h) {
         enqueue_start(h, q, cs);
         enqueue_sample(h, q, cs);
         enqueue_link(h, q, cs);
-        enqueue_relabel(h, q, cs);
         cudaStreamCaptureStatus cst;
         e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, nullptr, nullptr, nullptr);
         if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, cg, 0, cudaGraphCondAssignDefault);
-        if (e == cudaSuccess) k_q_next<<<1, 1, 0, cs>>>(q, cond, 1);
+        if (e == cudaSuccess) enqueue_relabel(h, q, cs, cond, 1);
         const cudaGraphNode_t* deps = nullptr;
         size_t nd = 0;
         if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &nd);
@@ -807,8 +832,7 @@ static gz_status build_query_graph(gz_handle* h) {
                 enqueue_grouping(h, q, bs);
                 enqueue_sample(h, q, bs);
                 enqueue_link(h, q, bs);
-                enqueue_relabel(h, q, bs);
-                k_q_next<<<1, 1, 0, bs>>>(q, cond, 1);
+                enqueue_relabel(h, q, bs, cond, 1);
                 e = cudaStreamEndCapture(bs, &body);
             }
         }
@@ -902,8 +926,8 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
                     k_q_forest_advance<<<1, 1, 0, stm>>>(q, h->q_pos);
                     h->launches += J + 7;
                 }
-                enqueue_relabel(h, q, stm);
-                h->launches += 3;
+                enqueue_relabel(h, q, stm, 0, 0);
+                h->launches += 3;  // link, newroot, relabel
             }
             k_q_next<<<1, 1, 0, stm>>>(q, 0, 0);
             h->launches += 2;  // sample, next
@@ -916,9 +940,11 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
         }
     }
     if (e == cudaSuccess && labels)
-        e = cudaMemcpyAsync(labels, h->q_label, (size_t)V * sizeof(uint32_t), cudaMemcpyDeviceToHost, stm);
+        e = cudaMemcpyAsync(h->h_labels ? h->h_labels : labels, h->q_label, (size_t)V * sizeof(uint32_t),
+                            cudaMemcpyDeviceToHost, stm);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stm);
     if (e != cudaSuccess) return cuda_check(h, e, "query");
+    if (labels && h->h_labels) std::memcpy(labels, h->h_labels, (size_t)V * sizeof(uint32_t));
     const uint32_t ncc = h->h_ctr[C_NCC];
     const uint32_t nf = h->h_ctr[C_FOREST];
     const uint32_t rounds = h->h_ctr[C_ROUNDS], fails_last = h->h_ctr[C_FLAST];
