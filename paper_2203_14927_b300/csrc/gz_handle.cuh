@@ -91,6 +91,7 @@ struct gz_handle {
     uint64_t* q_acc = nullptr;     // per big component: XOR of its members' CubeSketch
     uint32_t q_slots_cap = 0;
     uint32_t q_merge_occ = 1;               // resident merge blocks per SM
+    bool q_acc_dirty = true;                // accumulator slots need clearing before the next query
     cudaGraph_t q_graph = nullptr;          // the CC query as one graph (built at the first query)
     cudaGraphExec_t q_graph_exec = nullptr;
     int64_t* q_trace = nullptr;
@@ -145,11 +146,11 @@ gz_status tier_settle(gz_handle* h);
 gz_status tier_gather_nodes(gz_handle* h, uint32_t lo, uint32_t hi, uint8_t* dst);
 
 // query (gz_query.cu)
-// Components with more than kMergeChunk members are merged by chunks of
-// kMergeChunk members into an accumulator slot of their own; at most
-// V / (kMergeChunk + 1) components are that large.
-constexpr uint32_t kMergeChunk = 32;
-inline uint32_t query_slots(uint32_t V) { return V / (kMergeChunk + 1) + 1; }
+// Every component of more than kSlotAbove members gets an accumulator slot
+// (one CubeSketch) that the merge kernel fills; at most V / (kSlotAbove + 1)
+// components are that large.
+constexpr uint32_t kSlotAbove = 1;
+inline uint32_t query_slots(uint32_t V) { return V / (kSlotAbove + 1) + 1; }
 gz_status query_setup(gz_handle* h);
 gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* forest_uv,
                   size_t* n_edges, uint32_t* n_cc, gz_query_stats* st);

@@ -4,10 +4,10 @@
 //
 // Round r:
 //   group    nodes by current component (counting sort by label);
-//   merge    component sketch = XOR of the members' CubeSketch r (a
-//            component of more than M members is merged by chunks of M
-//            members, each XORed into the component's accumulator with
-//            atomics);
+//   merge    component sketch = XOR of the members' CubeSketch r, in an
+//            accumulator slot per component of two or more members (a
+//            block stores a component it holds whole and XORs its part of
+//            one that spans blocks in with atomics);
 //   sample   nested rows by suffix XOR, then the first bucket in the scan
 //            order of Fig. cube_code (columns, then rows ascending) that passes
 //            the checksum, decodes to an edge u < v < V and leaves the component;
@@ -50,6 +50,7 @@ struct QArgs {
     uint32_t *label, *parent, *count, *off, *cursor, *members, *roots, *target;
     uint32_t* slot;     // accumulator slot of a component with more than M members
     uint64_t* acc;      // slots x (21R/2) words, zero between rounds
+    uint32_t merge_per_block;  // members per merge block (a component within one block is stored whole)
     int64_t* res;
     int64_t* trace;     // K x V or null
     uint32_t* ctr;
@@ -254,30 +255,38 @@ __global__ void __launch_bounds__(kTpb) k_q_roots(QArgs q) {
 // 84R bytes).  The block first resolves node and slot of up to blockDim of
 // its members at once (one round of dependent loads per blockDim members),
 // then streams their blocks kMergeDepth members at a time.  Members are
-// grouped by component, so a block meets each large component as one run:
-// it XORs the run in a register and adds it to the slot with one atomic per
-// word, at the run's end.
+// grouped by component, so a block meets each component as one run: it XORs
+// the run in a register and, at the run's end, stores it (a component that
+// lies wholly in the block's range) or XORs it into the slot with one atomic
+// per word (a component that spans blocks; slots are zero between rounds).
 constexpr uint32_t kMergeMaxThreads = 704;  // 21R/2 words rounded up to a warp, R <= 64
-constexpr uint32_t kMergeDepth = 16;
+constexpr uint32_t kMergeDepth = 12;
+constexpr uint32_t kWhole = 0x80000000u;    // slot flag: the component lies in this block
 
-__global__ void __launch_bounds__(kMergeMaxThreads) k_q_merge(QArgs q, uint32_t per_block) {
+__global__ void __launch_bounds__(kMergeMaxThreads) k_q_merge(QArgs q) {
     __shared__ uint32_t s_node[kMergeMaxThreads], s_slot[kMergeMaxThreads];
     const uint32_t nw = 21u * q.R / 2u;  // u64 words of one CubeSketch (84R bytes)
-    const uint32_t w = threadIdx.x, round = q.ctr[C_ROUND];
+    const uint32_t w = threadIdx.x, round = q.ctr[C_ROUND], per_block = q.merge_per_block;
     const uint64_t lo64 = (uint64_t)blockIdx.x * per_block;
     if (lo64 >= q.V) return;  // block-uniform
     const uint32_t lo = (uint32_t)lo64, hi = (uint32_t)(lo64 + per_block < q.V ? lo64 + per_block : q.V);
-    uint32_t cur = 0xffffffffu;  // slot of the run being XORed
+    uint32_t cur = 0xffffffffu;  // slot (with kWhole) of the run being XORed
     uint64_t x = 0;
+    auto flush = [&]() {
+        if (cur == 0xffffffffu || w >= nw) return;
+        uint64_t* dst = q.acc + (uint64_t)(cur & ~kWhole) * nw + w;
+        if (cur & kWhole) *dst = x;
+        else if (x) atomicXor(reinterpret_cast<unsigned long long*>(dst), (unsigned long long)x);
+    };
     for (uint32_t b = lo; b < hi; b += blockDim.x) {
         const uint32_t n = min(blockDim.x, hi - b);
         __syncthreads();  // the previous segment's s_node / s_slot are consumed
         if (w < n) {
             const uint32_t node = q.members[b + w];
             const uint32_t c = q.label[node];
-            const uint32_t cnt = q.count[c], sl = q.slot[c];
+            const uint32_t cnt = q.count[c], off = q.off[c], sl = q.slot[c];
             s_node[w] = node;
-            s_slot[w] = cnt > q.M ? sl : 0xffffffffu;
+            s_slot[w] = cnt > q.M ? (sl | (off >= lo && off + cnt <= hi ? kWhole : 0u)) : 0xffffffffu;
         }
         __syncthreads();
         for (uint32_t i0 = 0; i0 < n; i0 += kMergeDepth) {
@@ -295,9 +304,7 @@ __global__ void __launch_bounds__(kMergeMaxThreads) k_q_merge(QArgs q, uint32_t 
                 const uint32_t sl = i < n ? s_slot[i] : 0xffffffffu;
                 if (sl == 0xffffffffu) continue;
                 if (sl != cur) {
-                    if (cur != 0xffffffffu && w < nw && x)
-                        atomicXor(reinterpret_cast<unsigned long long*>(q.acc + (uint64_t)cur * nw + w),
-                                  (unsigned long long)x);
+                    flush();
                     cur = sl;
                     x = 0;
                 }
@@ -305,20 +312,17 @@ __global__ void __launch_bounds__(kMergeMaxThreads) k_q_merge(QArgs q, uint32_t 
             }
         }
     }
-    if (cur != 0xffffffffu && w < nw && x)
-        atomicXor(reinterpret_cast<unsigned long long*>(q.acc + (uint64_t)cur * nw + w), (unsigned long long)x);
+    flush();
 }
 
 // Sample, one warp per component.  A warp takes up to kSampleBatch
-// components at a time and resolves their sizes, offsets, slots and first
-// members with one load per lane.  It builds each component's CubeSketch
-// `round` in one of two shared-memory buffers of its own: a component whose
-// sketch has one source (a single member, or the accumulator slot of a large
-// component, cleared again for the next round) is fetched with asynchronous
-// copies while the warp still works on the previous component; a component
-// of 2..M members is the XOR of its members' blocks, loaded into registers.
-// Lane l moves u64 words l, l + 32, ... of each 84R-byte block, so every
-// access covers 256 contiguous bytes.  Then lane l takes row l of a column
+// components at a time and resolves their sizes, slots and first members
+// with one load per lane.  Each component's CubeSketch `round` has one
+// source: the block of its single member, or its accumulator slot (cleared
+// again for the next round).  The warp fetches it into one of two
+// shared-memory buffers of its own with asynchronous copies while it still
+// works on the previous component; lane l moves u64 words l, l + 32, ... of
+// the 84R-byte block, so every access covers 256 contiguous bytes.  Then lane l takes row l of a column
 // from the buffer, the nested rows (row i = XOR of exact rows >= i) come
 // from a warp-shuffle suffix XOR (rows 32 and up, which only V > 2^16 has,
 // by a short loop over the buffer), and the first good bucket in Fig.
@@ -386,17 +390,16 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_q_sample(QArgs q) {
         const uint32_t nb = min(bsz, n_roots - base);
         // lane k < nb: component base + k, its size, member offset and source
         // (accumulator slot of a large component, else its first member)
-        uint32_t m_c = 0, m_cnt = 0, m_off = 0, m_src = 0;
+        uint32_t m_c = 0, m_cnt = 0, m_src = 0;
         if (lane < nb) {
             m_c = q.roots[base + lane];
             m_cnt = q.count[m_c];
-            m_off = q.off[m_c];
-            const uint32_t sl = q.slot[m_c];
-            m_src = m_cnt > q.M ? sl : q.members[m_off];
+            const uint32_t off = q.off[m_c], sl = q.slot[m_c];
+            m_src = m_cnt > q.M ? sl : q.members[off];
         }
         {
             const uint32_t cnt = __shfl_sync(0xffffffffu, m_cnt, 0), src = __shfl_sync(0xffffffffu, m_src, 0);
-            if (cnt == 1 || cnt > q.M) fetch(bufs, single_src(cnt, src));
+            fetch(bufs, single_src(cnt, src));
             cp_async_commit();
         }
         for (uint32_t k = 0; k < nb; ++k) {
@@ -408,7 +411,7 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_q_sample(QArgs q) {
             const uint32_t kn = k + 1 < nb ? k + 1 : k;
             const uint32_t cnt_n = __shfl_sync(0xffffffffu, m_cnt, kn);
             const uint32_t src_n = __shfl_sync(0xffffffffu, m_src, kn);
-            if (k + 1 < nb && (cnt_n == 1 || cnt_n > q.M)) fetch(bufs + ((k + 1) & 1) * nw, single_src(cnt_n, src_n));
+            if (k + 1 < nb) fetch(bufs + ((k + 1) & 1) * nw, single_src(cnt_n, src_n));
             cp_async_commit();
             uint64_t* cube = bufs + (k & 1) * nw;
             const uint32_t* cube_g = reinterpret_cast<const uint32_t*>(cube + GZ_COLS * R);
@@ -419,30 +422,6 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_q_sample(QArgs q) {
                 for (int i = 0; i < kW; ++i) {
                     const uint32_t w = lane + 32u * i;
                     if (w < nw) slot[w] = 0;
-                }
-            } else if (cnt > 1) {
-                uint64_t acc[kW];
-                const uint64_t* A = reinterpret_cast<const uint64_t*>(q.s.cube(src, round));
-#pragma unroll
-                for (int i = 0; i < kW; ++i) {
-                    const uint32_t w = lane + 32u * i;
-                    acc[i] = w < nw ? __ldg(A + w) : 0ull;
-                }
-                const uint32_t off = __shfl_sync(0xffffffffu, m_off, k);
-                const uint32_t my_node = lane < cnt ? q.members[off + lane] : 0u;
-                for (uint32_t sidx = 1; sidx < cnt; ++sidx) {
-                    const uint64_t* B =
-                        reinterpret_cast<const uint64_t*>(q.s.cube(__shfl_sync(0xffffffffu, my_node, sidx), round));
-#pragma unroll
-                    for (int i = 0; i < kW; ++i) {
-                        const uint32_t w = lane + 32u * i;
-                        if (w < nw) acc[i] ^= __ldg(B + w);
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < kW; ++i) {
-                    const uint32_t w = lane + 32u * i;
-                    if (w < nw) cube[w] = acc[i];
                 }
             }
             __syncwarp();
@@ -712,7 +691,8 @@ static QArgs query_args(gz_handle* h) {
     q.vinv = ~0ull / h->V;
     q.K = h->K;
     q.R = h->R;
-    q.M = kMergeChunk;
+    q.M = kSlotAbove;
+    q.merge_per_block = 1;  // set where the merge is enqueued
     q.label = h->q_label;
     q.parent = h->q_parent;
     q.count = h->q_count;
@@ -729,12 +709,9 @@ static QArgs query_args(gz_handle* h) {
     return q;
 }
 
-// query start: singletons, counters, clear accumulator slots (the sampler
-// clears every slot it reads; this only guards against a query that stopped
-// on an error between a merge and its sampler)
+// query start: singletons and counters
 static void enqueue_start(gz_handle* h, const QArgs& q, cudaStream_t stm) {
     k_q_init<<<grid_for(h, h->V, kTpb), kTpb, 0, stm>>>(q);
-    cudaMemsetAsync(h->q_acc, 0, (size_t)h->q_slots_cap * h->per_k_bytes, stm);
 }
 
 // group vertices by component and merge the large components (rounds > 0;
@@ -754,8 +731,9 @@ static void enqueue_grouping(gz_handle* h, const QArgs& q, cudaStream_t stm) {
     // wave of blocks
     const uint32_t mt = merge_threads(h->R);
     const uint32_t nblk = std::max<uint32_t>(1, std::min<uint32_t>((V + 31) / 32, h->sm_count * h->q_merge_occ));
-    const uint32_t per_block = (V + nblk - 1) / nblk;
-    k_q_merge<<<nblk, mt, 0, stm>>>(q, per_block);
+    QArgs qm = q;
+    qm.merge_per_block = (V + nblk - 1) / nblk;
+    k_q_merge<<<nblk, mt, 0, stm>>>(qm);
 }
 
 // u64 words per lane of the sampler's staging loads
@@ -869,6 +847,14 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
     const QArgs q = query_args(h);
     const uint32_t V = h->V;
     cudaError_t e = cudaSuccess;
+    // The sampler clears every accumulator slot it reads, so slots are zero
+    // after a query that ran to its end; after an allocation or a failed
+    // query they are cleared here.
+    if (h->q_acc_dirty) {
+        e = cudaMemsetAsync(h->q_acc, 0, (size_t)h->q_slots_cap * h->per_k_bytes, stm);
+        if (e != cudaSuccess) return cuda_check(h, e, "query slots");
+        h->q_acc_dirty = false;
+    }
 
     if (!want_forest && !h->trace && !h->tiered && !h->cfg.no_graph) {
         if (!h->q_graph_exec && (s = build_query_graph(h)) != GZ_OK) return s;
@@ -943,7 +929,10 @@ gz_status boruvka(gz_handle* h, bool want_forest, uint32_t* labels, uint32_t* fo
         e = cudaMemcpyAsync(h->h_labels ? h->h_labels : labels, h->q_label, (size_t)V * sizeof(uint32_t),
                             cudaMemcpyDeviceToHost, stm);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stm);
-    if (e != cudaSuccess) return cuda_check(h, e, "query");
+    if (e != cudaSuccess) {
+        h->q_acc_dirty = true;
+        return cuda_check(h, e, "query");
+    }
     if (labels && h->h_labels) std::memcpy(labels, h->h_labels, (size_t)V * sizeof(uint32_t));
     const uint32_t ncc = h->h_ctr[C_NCC];
     const uint32_t nf = h->h_ctr[C_FOREST];

@@ -130,7 +130,7 @@ def _server_graph_bytes(V):
     b = ctypes.c_size_t()
     gz.lib().gz_memory_bytes(V, ctypes.byref(c), ctypes.byref(b))
     K, R = gz.geometry(V)
-    return b.value + V * 96 + (V // 33 + 1) * 84 * R + (16 << 20)
+    return b.value + V * 96 + (V // 2 + 1) * 84 * R + (16 << 20)
 
 
 def test_idle_graphs_are_evicted_and_restored_bit_for_bit():
