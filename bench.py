@@ -329,8 +329,10 @@ def whole_job_rate(updates_per_rank_step: int, steps: int, world: int, ms_max: f
 
 def generate_on_device(spec, torch, gz):
     gen = gz.DeviceKronStream(spec)
+    # the expected stream length with a margin; the generator refuses a chunk
+    # that would not fit (GZ_EINVAL), it never writes past the capacity
     est = spec.target_edges * (1 + 2 * spec.churn)
-    cap = int(est * 1.08) + 4 * spec.slice_len + (1 << 20)
+    cap = int(est * 1.08) + (1 << 26)
     U = torch.empty(cap, dtype=torch.int32, device="cuda")
     Vv = torch.empty(cap, dtype=torch.int32, device="cuda")
     off = 0

@@ -248,8 +248,10 @@ __device__ __forceinline__ uint32_t side_checksum(const SideKey<kM2>& s, uint32_
     const uint32_t g1 = s.cs[1] * y + s.coff[1];
     if (kM2 == 2) return __byte_perm(g1, g0, 0x7632);  // (g0 & 0xffff0000) | (g1 >> 16)
     const uint32_t g2 = s.cs[kM2 - 1] * y + s.coff[kM2 - 1];
-    const uint32_t t1 = g1 >> (32 - p), t2 = g2 >> (32 - p);  // 3p >= 33 bits in all
-    return (g0 & (0xffffffffu << (32 - p))) | (t1 << (32 - 2 * p)) | (t2 >> (3 * p - 32));
+    // bits [32-p, 32): piece 0; [32-2p, 32-p): piece 1, i.e. g1's top p bits
+    // moved down by p; [0, 32-2p): the top 32-2p bits of piece 2 (3p >= 33)
+    const uint32_t m0 = 0xffffffffu << (32 - p), m1 = (0xffffffffu >> (32 - p)) << (32 - 2 * p);
+    return (g0 & m0) | ((g1 >> p) & m1) | (g2 >> (2 * p));
 }
 
 // mbarrier handover between the producer warp and the column warps.  Every

@@ -56,6 +56,19 @@ struct QArgs {
     uint32_t* ctr;
 };
 
+// a = u*V + v with a < V^2 -> (u, v): the high product with floor((2^64-1)/V)
+// underestimates a / V by at most one
+__device__ __forceinline__ void decode_edge(const QArgs& q, uint64_t a, uint32_t& u, uint32_t& v) {
+    uint64_t qu = __umul64hi(a, q.vinv);
+    uint64_t rem = a - qu * q.V;
+    if (rem >= q.V) {
+        ++qu;
+        rem -= q.V;
+    }
+    u = (uint32_t)qu;
+    v = (uint32_t)rem;
+}
+
 __device__ __forceinline__ uint32_t dsu_find(uint32_t* parent, uint32_t x) {
     volatile uint32_t* P = parent;
     uint32_t p = P[x];
@@ -460,16 +473,12 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_q_sample(QArgs q) {
                 // h2 is defined on edges: alpha must decode to u < v < V first
                 auto good = [&](uint64_t a, uint32_t g, uint32_t row) -> bool {
                     if (row >= R || (a | g) == 0 || a >= VV) return false;
-                    // a < V^2: the high product underestimates a / V by at most one
-                    uint64_t qu = __umul64hi(a, q.vinv);
-                    uint64_t rem = a - qu * q.V;
-                    if (rem >= q.V) {
-                        ++qu;
-                        rem -= q.V;
-                    }
-                    const uint32_t uu = (uint32_t)qu, vv = (uint32_t)rem;
+                    uint32_t uu, vv;
+                    decode_edge(q, a, uu, vv);
                     if (uu >= vv) return false;
                     if (g != round_checksum(s_keys, q.geo, (uint32_t)j, uu, vv)) return false;
+                    // round 0: every vertex is its own component (label = id)
+                    if (round == 0) return (uu == c) != (vv == c);
                     return (q.label[uu] == c) != (q.label[vv] == c);
                 };
                 // rows 32.. are almost always empty: their check runs only when not
@@ -510,7 +519,8 @@ __global__ void k_q_link(QArgs q) {
         const uint32_t c = q.roots[i];
         const int64_t r = q.res[c];
         if (r <= 0) continue;
-        const uint32_t uu = (uint32_t)((uint64_t)r / q.V), vv = (uint32_t)((uint64_t)r % q.V);
+        uint32_t uu, vv;
+        decode_edge(q, (uint64_t)r, uu, vv);
         const uint32_t a = q.label[uu], b = q.label[vv];
         const uint32_t t = a == c ? b : a;
         q.target[c] = t;
@@ -560,8 +570,7 @@ __global__ void k_q_forest_write(QArgs q, const uint32_t* acc, const uint32_t* p
         if (!acc[v]) continue;
         const uint64_t e = (uint64_t)q.res[v];
         const uint32_t p = base + pos[v];
-        forest[2 * p] = (uint32_t)(e / q.V);
-        forest[2 * p + 1] = (uint32_t)(e % q.V);
+        decode_edge(q, e, forest[2 * p], forest[2 * p + 1]);
     }
 }
 

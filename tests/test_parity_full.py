@@ -35,7 +35,7 @@ def _device_stream(spec):
     import torch
 
     gen = gz.DeviceKronStream(spec)
-    cap = int(spec.target_edges * (1 + 2 * spec.churn) * 1.08) + 4 * spec.slice_len + (1 << 20)
+    cap = int(spec.target_edges * (1 + 2 * spec.churn) * 1.08) + (1 << 26)
     U = torch.empty(cap, dtype=torch.int32, device="cuda")
     W = torch.empty(cap, dtype=torch.int32, device="cuda")
     n = 0
