@@ -46,7 +46,7 @@ CHUNK_LOG2 = 24
 # of this bench's own step); valid only for the kernel source it was taken with
 # (kernel_sha) and its configuration.
 TRAFFIC = {
-    "kron17": {"sha": "88d5cd4044072f1f",
+    "kron17": {"sha": "ed532baf39b96e24",
                "cfg": {"smem_mode": 1, "tile_records": 512, "smem_rows": 16, "ctas_per_sm": 0, "chunk_log2": 26},
                "bytes_per_update": 140.92,
                "source": "profiles/k_batched_kron17_dram.md"},
