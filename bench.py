@@ -49,6 +49,8 @@ TRAFFIC = {
     "kron17": {"sha": "ed532baf39b96e24",
                "cfg": {"smem_mode": 1, "tile_records": 512, "smem_rows": 16, "ctas_per_sm": 0, "chunk_log2": 26},
                "bytes_per_update": 140.92,
+               # smsp__thread_inst_executed.sum per column update, same capture rules
+               "thread_instr_per_column_update": 17.20,
                "source": "profiles/k_batched_kron17_dram.md"},
 }
 
@@ -78,7 +80,7 @@ def measured_traffic(workload: str, cfg: dict, kernel: str):
         return None, "kernel sources changed since the ncu capture"
     if any(cfg.get(k) != v for k, v in t["cfg"].items()):
         return None, f"ncu capture taken at config {t['cfg']}"
-    return t["bytes_per_update"], t["source"]
+    return t, t["source"]
 
 
 def nvtx_push(name: str):
@@ -441,8 +443,8 @@ def run_ours(args, rank: int, world: int):
     # buckets as rows_flushed).  The full-sketch bound, one read and write of
     # every node sketch per chunk, overstates it whenever nodes touch few rows.
     rows_per_launch = prof["rows_flushed"] / launches
-    traffic_per_update, traffic_note = measured_traffic(args.workload, cfg, args.kernel)
-    traffic = traffic_per_update * upd_per_launch if traffic_per_update else None
+    captured, traffic_note = measured_traffic(args.workload, cfg, args.kernel)
+    traffic = captured["bytes_per_update"] * upd_per_launch if captured else None
     hbm_bytes = 8.0 * upd_per_launch + 24.0 * rows_per_launch
     hbm = {"bound": "hbm", "achieved": hbm_bytes / sec / 1e9, "peak": peak, "unit": "GB/s",
            "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
@@ -492,6 +494,15 @@ def run_ours(args, rank: int, world: int):
             "atomics_per_column_update": 2.0 + f_wide}
     atom["frac"] = atom["achieved"] / atom_peak
     binding = max((hbm, alu, imad, clz, atom), key=lambda r: r["frac"])
+    # context, not the roofline: the instructions the kernel executes (ncu)
+    # against the same issue ceiling
+    executed = None
+    if captured:
+        tpi = captured["thread_instr_per_column_update"]
+        executed = {"bound": "alu", "pipe": "issue, executed instructions", "unit": "T thread-instr/s",
+                    "achieved": col_updates * tpi / sec / 1e12, "peak": issue_peak,
+                    "thread_instr_per_column_update": tpi, "source": captured["source"]}
+        executed["frac"] = executed["achieved"] / issue_peak
     roofline = dict(binding)
     roofline.update({
         "kernel": "k_batched" if args.kernel == "batched" else "k_plain",
@@ -502,6 +513,7 @@ def run_ours(args, rank: int, world: int):
         "share_of_step": prof["update_ms"] / ms if ms > 0 else None,
         "partition_ms_per_launch": prof["partition_ms"] / launches,
         "all": {"hbm": hbm, "alu_issue": alu, "imad_pipe": imad, "clz_pipe": clz, "shared_atomics": atom},
+        "executed_issue": executed,
     })
 
     # --- query latency -----------------------------------------------------------

@@ -358,8 +358,21 @@ __device__ __forceinline__ uint32_t round_checksum(const uint32_t* sk, const Pie
     return (uint32_t)(acc >> 32);
 }
 
+// two pieces of 16 bits (every V <= 2^17): the top halves joined by one byte
+// permute, as in the update kernel
+__device__ __forceinline__ uint32_t round_checksum2(const uint32_t* sk, uint32_t j, uint32_t u, uint32_t v) {
+    const uint32_t t0 = sk[0 * GZ_COLS + j] * u + sk[1 * GZ_COLS + j] * v + sk[2 * GZ_COLS + j];
+    const uint32_t t1 = sk[3 * GZ_COLS + j] * u + sk[4 * GZ_COLS + j] * v + sk[5 * GZ_COLS + j];
+    return __byte_perm(t1, t0, 0x7632);  // (t0 & 0xffff0000) | (t1 >> 16)
+}
+
 __device__ __forceinline__ void cp_async8(uint64_t* dst, const uint64_t* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(static_cast<uint64_t>(__cvta_generic_to_global(src)))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint64_t* dst, const uint64_t* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
                  "l"(static_cast<uint64_t>(__cvta_generic_to_global(src)))
                  : "memory");
 }
@@ -369,10 +382,16 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(kN) : "memory");
 }
 
-// kW: u64 words per lane, at least ceil(21R/2 / 32)
-template <int kW>
+// words of one staging buffer: 21R/2 plus one, so that a block that starts
+// 8 bytes past a 16-byte boundary can be staged at the same offset, rounded
+// up to keep every buffer 16-byte aligned
+__host__ __device__ inline uint32_t sample_stride(uint32_t R) { return (21u * R / 2u + 2u) & ~1u; }
+
+// kW: u64 words per lane, at least ceil(21R/2 / 32); kTwo: the checksum has
+// two 16-bit pieces (V <= 2^17)
+template <int kW, bool kTwo>
 __global__ void __launch_bounds__(kSampleThreads, 4) k_q_sample(QArgs q) {
-    extern __shared__ uint64_t q_cube[];  // (kSampleThreads / 32) x 2 x 21R/2 words
+    extern __shared__ __align__(16) uint64_t q_cube[];  // (kSampleThreads / 32) x 2 x sample_stride(R) words
     __shared__ uint32_t s_keys[kMaxKeyWords * GZ_COLS];
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -381,7 +400,8 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_q_sample(QArgs q) {
     for (uint32_t i = threadIdx.x; i < 3 * q.geo.m2 * GZ_COLS; i += blockDim.x)
         s_keys[i] = q.keys.at(kH2Words + i / GZ_COLS, round * GZ_COLS + i % GZ_COLS);
     __syncthreads();
-    uint64_t* bufs = q_cube + (threadIdx.x >> 5) * 2 * nw;
+    const uint32_t stride = sample_stride(R);
+    uint64_t* bufs = q_cube + (threadIdx.x >> 5) * 2 * stride;
     const uint64_t VV = (uint64_t)q.V * q.V;
     const uint32_t r0 = lane, r1 = lane + 32;
     // source block of component k of the batch when it has one source
@@ -389,12 +409,26 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_q_sample(QArgs q) {
         if (cnt > q.M) return q.acc + (uint64_t)src * nw;
         return reinterpret_cast<const uint64_t*>(q.s.cube(src, round));
     };
-    auto fetch = [&](uint64_t* dst, const uint64_t* src) {
+    // word offset in the buffer at which a source block is staged: 1 when it
+    // starts 8 bytes past a 16-byte boundary, so that both sides of the
+    // 16-byte copies are aligned
+    auto lead = [&](const uint64_t* src) -> uint32_t {
+        return (uint32_t)(reinterpret_cast<uintptr_t>(src) >> 3) & 1u;
+    };
+    // the block into buf + lead(src): 16-byte copies of word pairs, an
+    // 8-byte copy of a leading or trailing single word
+    auto fetch = [&](uint64_t* buf, const uint64_t* src) {
+        const uint32_t a = lead(src);
+        uint64_t* dst = buf + a;  // dst[w] is src[w]
+        const uint32_t npairs = (nw - a) >> 1;
 #pragma unroll
-        for (int i = 0; i < kW; ++i) {
-            const uint32_t w = lane + 32u * i;
-            if (w < nw) cp_async8(dst + w, src + w);
+        for (int i = 0; i < (kW + 1) / 2; ++i) {
+            const uint32_t c = lane + 32u * i;
+            if (c < npairs) cp_async16(dst + a + 2 * c, src + a + 2 * c);
         }
+        const uint32_t tail = a + 2 * npairs;
+        if (a && lane == 0) cp_async8(dst, src);
+        if (tail < nw && lane == 1) cp_async8(dst + tail, src + tail);
     };
     // components per warp batch: up to kSampleBatch, fewer when the warps
     // outnumber the batches (late rounds have few components)
@@ -424,11 +458,12 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_q_sample(QArgs q) {
             const uint32_t kn = k + 1 < nb ? k + 1 : k;
             const uint32_t cnt_n = __shfl_sync(0xffffffffu, m_cnt, kn);
             const uint32_t src_n = __shfl_sync(0xffffffffu, m_src, kn);
-            if (k + 1 < nb) fetch(bufs + ((k + 1) & 1) * nw, single_src(cnt_n, src_n));
+            if (k + 1 < nb) fetch(bufs + ((k + 1) & 1) * stride, single_src(cnt_n, src_n));
             cp_async_commit();
-            uint64_t* cube = bufs + (k & 1) * nw;
+            uint64_t* cube = bufs + (k & 1) * stride + lead(single_src(cnt, src));
             const uint32_t* cube_g = reinterpret_cast<const uint32_t*>(cube + GZ_COLS * R);
-            cp_async_wait<1>();  // component k's copies are done (this lane's)
+            cp_async_wait<1>();  // component k's copies are done (this lane's) ...
+            __syncwarp();        // ... and every lane's
             if (cnt > q.M) {
                 uint64_t* slot = q.acc + (uint64_t)src * nw;
 #pragma unroll
@@ -476,7 +511,9 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_q_sample(QArgs q) {
                     uint32_t uu, vv;
                     decode_edge(q, a, uu, vv);
                     if (uu >= vv) return false;
-                    if (g != round_checksum(s_keys, q.geo, (uint32_t)j, uu, vv)) return false;
+                    const uint32_t h2 = kTwo ? round_checksum2(s_keys, (uint32_t)j, uu, vv)
+                                             : round_checksum(s_keys, q.geo, (uint32_t)j, uu, vv);
+                    if (g != h2) return false;
                     // round 0: every vertex is its own component (label = id)
                     if (round == 0) return (uu == c) != (vv == c);
                     return (q.label[uu] == c) != (q.label[vv] == c);
@@ -612,7 +649,7 @@ __global__ void k_q_ncc(QArgs q) {
 // ------------------------------------------------------------------ host side
 
 // dynamic shared memory of the sampler: two CubeSketch buffers per warp
-static size_t sample_smem(uint32_t R) { return (size_t)(kSampleThreads / 32) * 2 * (21u * R / 2u) * sizeof(uint64_t); }
+static size_t sample_smem(uint32_t R) { return (size_t)(kSampleThreads / 32) * 2 * sample_stride(R) * sizeof(uint64_t); }
 static uint32_t merge_threads(uint32_t R) { return (21u * R / 2u + 31) / 32 * 32; }  // <= kMergeMaxThreads
 
 constexpr uint32_t kPinnedLabels = 1u << 17;  // graphs this large stage their labels in pinned memory
@@ -659,13 +696,13 @@ gz_status query_setup(gz_handle* h) {
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once, [] {
         const int smem = (int)sample_smem(64);
-        attr_err = cudaFuncSetAttribute(k_q_sample<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (attr_err == cudaSuccess)
-            attr_err = cudaFuncSetAttribute(k_q_sample<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (attr_err == cudaSuccess)
-            attr_err = cudaFuncSetAttribute(k_q_sample<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (attr_err == cudaSuccess)
-            attr_err = cudaFuncSetAttribute(k_q_sample<21>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        const void* fns[] = {(const void*)k_q_sample<6, true>,  (const void*)k_q_sample<12, true>,
+                             (const void*)k_q_sample<16, true>, (const void*)k_q_sample<21, true>,
+                             (const void*)k_q_sample<6, false>, (const void*)k_q_sample<12, false>,
+                             (const void*)k_q_sample<16, false>, (const void*)k_q_sample<21, false>};
+        for (const void* f : fns)
+            if (attr_err == cudaSuccess)
+                attr_err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     });
     e = attr_err;
     // the merge runs one wave of resident blocks
@@ -754,11 +791,17 @@ static int sample_words(uint32_t R) {
 static void enqueue_sample(gz_handle* h, const QArgs& q, cudaStream_t stm) {
     const size_t smem = sample_smem(h->R);
     const uint32_t grid = h->sm_count * 16;
-    switch (sample_words(h->R)) {
-    case 6: k_q_sample<6><<<grid, kSampleThreads, smem, stm>>>(q); break;
-    case 12: k_q_sample<12><<<grid, kSampleThreads, smem, stm>>>(q); break;
-    case 16: k_q_sample<16><<<grid, kSampleThreads, smem, stm>>>(q); break;
-    default: k_q_sample<21><<<grid, kSampleThreads, smem, stm>>>(q); break;
+    // two checksum pieces means 16-bit pieces (p = 16 whenever m2 = 2)
+    const bool two = h->geo.m2 == 2;
+    switch (sample_words(h->R) * 2 + (two ? 1 : 0)) {
+    case 13: k_q_sample<6, true><<<grid, kSampleThreads, smem, stm>>>(q); break;
+    case 25: k_q_sample<12, true><<<grid, kSampleThreads, smem, stm>>>(q); break;
+    case 33: k_q_sample<16, true><<<grid, kSampleThreads, smem, stm>>>(q); break;
+    case 43: k_q_sample<21, true><<<grid, kSampleThreads, smem, stm>>>(q); break;
+    case 12: k_q_sample<6, false><<<grid, kSampleThreads, smem, stm>>>(q); break;
+    case 24: k_q_sample<12, false><<<grid, kSampleThreads, smem, stm>>>(q); break;
+    case 32: k_q_sample<16, false><<<grid, kSampleThreads, smem, stm>>>(q); break;
+    default: k_q_sample<21, false><<<grid, kSampleThreads, smem, stm>>>(q); break;
     }
 }
 
