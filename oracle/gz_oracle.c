@@ -366,7 +366,14 @@ static int dsu_union(uint32_t *parent, uint32_t a, uint32_t b)
  *   stats       : out[4] = rounds run, FAIL count of the last round run,
  *                 1 if round K-1 still sampled an edge, number of components
  * Returns 0, 1 when the result may be wrong (a FAIL in the last round run or
- * rounds exhausted), negative on bad arguments. */
+ * rounds exhausted), negative on bad arguments.
+ *
+ * A component whose sketch is entirely zero in a round (EMPTY) has a zero
+ * characteristic vector as far as the sketches can tell (a sketch is linear
+ * in the vector, and the members' shared edges cancel), so no merge can reach
+ * it (Section 2.2: Boruvka continues "until no new merges are possible"): it
+ * is final, and in later rounds it reports EMPTY without a sample.  A
+ * component that a sampled edge touches is no longer final. */
 int gzo_boruvka(uint32_t V, uint64_t seed, const uint64_t *alpha,
                 const uint32_t *gamma, uint32_t *labels, uint32_t *forest,
                 uint64_t *n_forest, int64_t *samples, uint64_t *stats)
@@ -379,7 +386,8 @@ int gzo_boruvka(uint32_t V, uint64_t seed, const uint64_t *alpha,
     uint64_t *SA = malloc((size_t)V * per_k * 8);
     uint32_t *SG = malloc((size_t)V * per_k * 4);
     int64_t *res = malloc((size_t)V * 8);
-    if (!parent || !SA || !SG || !res) return -2;
+    uint8_t *final = calloc(V, 1);  /* final[c]: component c sampled EMPTY, untouched since */
+    if (!parent || !SA || !SG || !res || !final) return -2;
     for (uint32_t i = 0; i < V; i++) { parent[i] = i; labels[i] = i; }
     if (samples)
         for (size_t i = 0; i < (size_t)x.K * V; i++) samples[i] = -4;
@@ -404,10 +412,12 @@ int gzo_boruvka(uint32_t V, uint64_t seed, const uint64_t *alpha,
         uint64_t n_edges = 0, n_fail = 0;
         for (uint32_t c = 0; c < V; c++) {
             if (labels[c] != c) { res[c] = -3; continue; }
+            if (final[c]) { res[c] = GZO_EMPTY; continue; }
             res[c] = cubesketch_query(&x, r, SA + (size_t)c * per_k,
                                       SG + (size_t)c * per_k, labels, c);
             if (res[c] > 0) n_edges++;
             else if (res[c] == GZO_FAIL) n_fail++;
+            else final[c] = 1;
         }
         if (samples)
             for (uint32_t c = 0; c < V; c++) samples[(size_t)r * V + c] = res[c];
@@ -420,6 +430,7 @@ int gzo_boruvka(uint32_t V, uint64_t seed, const uint64_t *alpha,
             if (res[c] <= 0) continue;
             uint32_t uu = (uint32_t)((uint64_t)res[c] / V);
             uint32_t vv = (uint32_t)((uint64_t)res[c] % V);
+            final[labels[uu]] = final[labels[vv]] = 0;  /* both components take part in a merge */
             if (dsu_union(parent, uu, vv)) {
                 if (forest) {
                     forest[2 * nf] = uu;
@@ -439,7 +450,7 @@ int gzo_boruvka(uint32_t V, uint64_t seed, const uint64_t *alpha,
         stats[2] = exhausted;
         stats[3] = ncomp;
     }
-    free(parent); free(SA); free(SG); free(res);
+    free(parent); free(SA); free(SG); free(res); free(final);
     ctx_close(&x);
     return (fails_last || exhausted) ? 1 : 0;
 }

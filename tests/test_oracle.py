@@ -586,3 +586,27 @@ def test_paper_design_cpu_baseline_equals_oracle():
         for x in (0, 1):
             A1, G1 = oracle.sketch_node(V, 4, x, S.neighbors_from_edges(V, eu, ev, x))
             assert np.array_equal(a[x], A1) and np.array_equal(g[x], G1), (V, x)
+
+
+def test_boruvka_empty_component_is_final():
+    """A component whose sketch is entirely zero in a round takes no part in
+    later rounds (it reports EMPTY), unless a sampled edge touches it.  With
+    the round-0 CubeSketches of 5 and 9 cleared by hand, the pair (5, 9) is
+    EMPTY in round 0; round 1 runs (20-21 merges) and, although 5's and 9's
+    round-1 CubeSketches hold their edge, both report EMPTY again, so they
+    stay apart.  Sampling them anew would join them."""
+    V = 64
+    u = np.array([5, 20], np.uint32)
+    v = np.array([9, 21], np.uint32)
+    A, G = oracle.ingest(V, 3, u, v)
+    A[[5, 9], 0] = 0
+    G[[5, 9], 0] = 0
+    res = oracle.boruvka(V, 3, A, G)
+    assert res["rounds"] == 2
+    assert res["samples"][0][5] == -1 and res["samples"][0][9] == -1
+    assert res["samples"][1][5] == -1 and res["samples"][1][9] == -1
+    assert res["labels"][9] == 9 and res["labels"][21] == 20
+    # untouched sketches: every component found, 5-9 joined in round 0
+    A, G = oracle.ingest(V, 3, u, v)
+    res = oracle.boruvka(V, 3, A, G)
+    assert res["labels"][9] == 5 and res["labels"][21] == 20
