@@ -222,7 +222,7 @@ gz_status gz_destroy(gz_handle* h) {
     cudaStreamSynchronize(h->stream);
     void* ptrs[] = {h->d_sketch, h->d_keys, h->d_counts, h->d_offsets, h->d_cursor, h->d_cursor_hi, h->d_records,
                     h->d_stage, h->d_flags, h->q_label, h->q_parent, h->q_count, h->q_off,
-                    h->q_cursor, h->q_members, h->q_roots, h->q_target, h->q_slot,
+                    h->q_cursor, h->q_members, h->q_roots, h->q_target, h->q_slot, h->q_final,
                     h->q_F, h->q_F2,
                     h->q_M, h->q_M2, h->q_flag, h->q_pos, h->q_forest, h->q_ctr, h->q_res,
                     h->q_acc, h->q_trace, h->d_stats, h->d_scan_tmp, h->d_tile_node, h->d_decode,

@@ -85,7 +85,8 @@ struct gz_handle {
              *q_cursor = nullptr, *q_members = nullptr, *q_roots = nullptr, *q_target = nullptr,
              *q_slot = nullptr, *q_F = nullptr, *q_F2 = nullptr,
              *q_M = nullptr, *q_M2 = nullptr, *q_flag = nullptr, *q_pos = nullptr,
-             *q_forest = nullptr, *q_ctr = nullptr, *h_ctr = nullptr;
+             *q_forest = nullptr, *q_ctr = nullptr, *h_ctr = nullptr,
+             *q_final = nullptr;  // per component root: 1 once it sampled EMPTY and nothing touched it
     uint32_t* h_labels = nullptr;  // pinned, V words: labels on their way to the caller
     int64_t* q_res = nullptr;
     uint64_t* q_acc = nullptr;     // per big component: XOR of its members' CubeSketch

@@ -35,11 +35,17 @@ namespace gz {
 
 // device counters of a query: per round (roots, large components, sampled
 // edges, FAIL results), per query (forest edges, components), the round index
-// and the loop decision, and the statistics of the rounds run so far
+// and the loop decision, the statistics of the rounds run so far, and (two
+// words from C_GIANT, one u64) the round's largest live component of more
+// than V/8 members as (members << 32) | ~id, or 0
 enum {
     C_ROOTS = 0, C_BIG = 1, C_EDGES = 2, C_FAILS = 3, C_FOREST = 4, C_NCC = 5, C_ROUND = 6, C_GO = 7,
-    C_ROUNDS = 8, C_FLAST = 9, C_FTOT = 10, C_EXH = 11, C_N = 12
+    C_ROUNDS = 8, C_FLAST = 9, C_FTOT = 10, C_EXH = 11, C_GIANT = 12, C_N = 14
 };
+
+__device__ __forceinline__ unsigned long long* giant_word(const uint32_t* ctr) {
+    return reinterpret_cast<unsigned long long*>(const_cast<uint32_t*>(ctr) + 12);  // C_GIANT, 8-byte aligned
+}
 
 struct QArgs {
     SketchView s;
@@ -49,8 +55,8 @@ struct QArgs {
     uint64_t vinv;        // floor((2^64 - 1) / V): a / V by one high multiply and a correction
     uint32_t *label, *parent, *count, *off, *cursor, *members, *roots, *target;
     uint32_t* slot;     // accumulator slot of a component with more than M members
+    uint32_t* final;    // 1 for a component root that sampled EMPTY and that no sampled edge touched since
     uint64_t* acc;      // slots x (21R/2) words, zero between rounds
-    uint32_t merge_per_block;  // members per merge block (a component within one block is stored whole)
     int64_t* res;
     int64_t* trace;     // K x V or null
     uint32_t* ctr;
@@ -101,6 +107,7 @@ __device__ void dsu_unite(uint32_t* parent, uint32_t a, uint32_t b) {
 __global__ void k_q_init(QArgs q) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < q.V; v += gridDim.x * blockDim.x) {
         q.label[v] = v;
+        q.final[v] = 0;
         q.parent[v] = v;
         q.count[v] = 1;
         q.off[v] = v;
@@ -129,6 +136,7 @@ __device__ __forceinline__ void round_end(const QArgs& q, cudaGraphConditionalHa
     q.ctr[C_GO] = go;
     q.ctr[C_ROUND] = r + 1;
     q.ctr[C_ROOTS] = q.ctr[C_BIG] = q.ctr[C_EDGES] = q.ctr[C_FAILS] = 0;
+    *giant_word(q.ctr) = 0;
     if (use_cond) cudaGraphSetConditional(cond, go);
 }
 
@@ -255,38 +263,58 @@ __global__ void __launch_bounds__(kTpb) k_q_roots(QArgs q) {
         }
         __syncthreads();
         if (cnt > 0) q.roots[s_base + s_warp[wid] + __popc(bal & ((1u << lane) - 1u))] = c;
-        if (cnt > q.M) q.slot[c] = atomicAdd(&q.ctr[C_BIG], 1u);
+        if (cnt > q.M && !q.final[c]) q.slot[c] = atomicAdd(&q.ctr[C_BIG], 1u);
+        if (cnt > q.M && cnt > q.V / 8 && !q.final[c])  // the largest, ties to the smallest id
+            atomicMax(giant_word(q.ctr), ((unsigned long long)cnt << 32) | (uint32_t)~c);
         if (c64 < q.V && cnt == 0 && q.trace) q.trace[(uint64_t)round * q.V + c] = -3;
         __syncthreads();  // s_warp and s_base are reused
     }
 }
 
 // XOR of CubeSketch `round` over the members of every component with more
-// than M members, into that component's accumulator slot.  Block b takes the
-// members [b * per_block, (b + 1) * per_block) of the grouped members array
-// and thread w word w of a CubeSketch (one coalesced pass over each member's
-// 84R bytes).  The block first resolves node and slot of up to blockDim of
-// its members at once (one round of dependent loads per blockDim members),
-// then streams their blocks kMergeDepth members at a time.  Members are
-// grouped by component, so a block meets each component as one run: it XORs
-// the run in a register and, at the run's end, stores it (a component that
-// lies wholly in the block's range) or XORs it into the slot with one atomic
-// per word (a component that spans blocks; slots are zero between rounds).
+// than M members, into that component's accumulator slot.
+//
+// The XOR of every node's CubeSketch is zero: an edge index is XORed into the
+// same bucket of both endpoints' sketches (the bucket depends on the index and
+// the column only).  So any one component is the XOR of every node outside
+// it.  The largest live component of more than V/8 members (the giant) is
+// merged that way, and its members are never read: every other node's block
+// goes into its own component's slot (when that component is live and has
+// more than M members) and into the giant's.
+//
+// The kernel walks the grouped members array without the giant's range (a
+// virtual position p is member p, or p + the giant's size past its offset);
+// block b takes positions [b * per, (b + 1) * per), thread w word w of a
+// CubeSketch (one coalesced pass over each node's 84R bytes).  The block
+// first resolves node and slot of up to blockDim of its nodes at once, then
+// streams their blocks kMergeDepth at a time.  A component is one run of the
+// array: its XOR is stored at the run's end when the component lies wholly in
+// the block's range, or XORed in with one atomic per word when it spans
+// blocks (slots are zero between rounds); the giant's part is XORed in once
+// per block.
 constexpr uint32_t kMergeMaxThreads = 704;  // 21R/2 words rounded up to a warp, R <= 64
 constexpr uint32_t kMergeDepth = 12;
 constexpr uint32_t kWhole = 0x80000000u;    // slot flag: the component lies in this block
+constexpr uint32_t kNone = 0xffffffffu;     // no slot of its own (node read for the giant only)
+constexpr uint32_t kSkip = 0xfffffffeu;     // node not read at all
 
 __global__ void __launch_bounds__(kMergeMaxThreads) k_q_merge(QArgs q) {
     __shared__ uint32_t s_node[kMergeMaxThreads], s_slot[kMergeMaxThreads];
     const uint32_t nw = 21u * q.R / 2u;  // u64 words of one CubeSketch (84R bytes)
-    const uint32_t w = threadIdx.x, round = q.ctr[C_ROUND], per_block = q.merge_per_block;
-    const uint64_t lo64 = (uint64_t)blockIdx.x * per_block;
-    if (lo64 >= q.V) return;  // block-uniform
-    const uint32_t lo = (uint32_t)lo64, hi = (uint32_t)(lo64 + per_block < q.V ? lo64 + per_block : q.V);
-    uint32_t cur = 0xffffffffu;  // slot (with kWhole) of the run being XORed
-    uint64_t x = 0;
+    const uint32_t w = threadIdx.x, round = q.ctr[C_ROUND];
+    const unsigned long long gw = *giant_word(q.ctr);
+    const bool has_giant = gw != 0;
+    const uint32_t giant = ~(uint32_t)gw;
+    const uint32_t g_off = has_giant ? q.off[giant] : 0u, g_cnt = has_giant ? q.count[giant] : 0u;
+    const uint32_t total = q.V - g_cnt;  // virtual positions
+    const uint32_t per = (total + gridDim.x - 1) / gridDim.x;
+    const uint64_t lo64 = (uint64_t)blockIdx.x * per;
+    if (lo64 >= total) return;  // block-uniform
+    const uint32_t lo = (uint32_t)lo64, hi = (uint32_t)(lo64 + per < total ? lo64 + per : total);
+    uint32_t cur = kNone;  // slot (with kWhole) of the run being XORed
+    uint64_t x = 0, xg = 0;
     auto flush = [&]() {
-        if (cur == 0xffffffffu || w >= nw) return;
+        if (cur == kNone || w >= nw) return;
         uint64_t* dst = q.acc + (uint64_t)(cur & ~kWhole) * nw + w;
         if (cur & kWhole) *dst = x;
         else if (x) atomicXor(reinterpret_cast<unsigned long long*>(dst), (unsigned long long)x);
@@ -295,11 +323,16 @@ __global__ void __launch_bounds__(kMergeMaxThreads) k_q_merge(QArgs q) {
         const uint32_t n = min(blockDim.x, hi - b);
         __syncthreads();  // the previous segment's s_node / s_slot are consumed
         if (w < n) {
-            const uint32_t node = q.members[b + w];
+            const uint32_t p = b + w;
+            const uint32_t node = q.members[p < g_off ? p : p + g_cnt];
             const uint32_t c = q.label[node];
             const uint32_t cnt = q.count[c], off = q.off[c], sl = q.slot[c];
+            const uint32_t voff = off < g_off ? off : off - g_cnt;  // the component's virtual offset
             s_node[w] = node;
-            s_slot[w] = cnt > q.M ? (sl | (off >= lo && off + cnt <= hi ? kWhole : 0u)) : 0xffffffffu;
+            if (cnt > q.M && !q.final[c])
+                s_slot[w] = sl | (voff >= lo && voff + cnt <= hi ? kWhole : 0u);
+            else
+                s_slot[w] = has_giant ? kNone : kSkip;
         }
         __syncthreads();
         for (uint32_t i0 = 0; i0 < n; i0 += kMergeDepth) {
@@ -307,15 +340,16 @@ __global__ void __launch_bounds__(kMergeMaxThreads) k_q_merge(QArgs q) {
 #pragma unroll
             for (uint32_t k = 0; k < kMergeDepth; ++k) {
                 const uint32_t i = i0 + k;
-                t[k] = (i < n && s_slot[i] != 0xffffffffu && w < nw)
+                t[k] = (i < n && s_slot[i] != kSkip && w < nw)
                            ? __ldg(reinterpret_cast<const uint64_t*>(q.s.cube(s_node[i], round)) + w)
                            : 0ull;
             }
 #pragma unroll
             for (uint32_t k = 0; k < kMergeDepth; ++k) {
                 const uint32_t i = i0 + k;
-                const uint32_t sl = i < n ? s_slot[i] : 0xffffffffu;
-                if (sl == 0xffffffffu) continue;
+                xg ^= t[k];
+                const uint32_t sl = i < n ? s_slot[i] : kSkip;
+                if (sl == kSkip || sl == kNone) continue;
                 if (sl != cur) {
                     flush();
                     cur = sl;
@@ -326,6 +360,9 @@ __global__ void __launch_bounds__(kMergeMaxThreads) k_q_merge(QArgs q) {
         }
     }
     flush();
+    if (has_giant && w < nw && xg)
+        atomicXor(reinterpret_cast<unsigned long long*>(q.acc + (uint64_t)q.slot[giant] * nw + w),
+                  (unsigned long long)xg);
 }
 
 // Sample, one warp per component.  A warp takes up to kSampleBatch
@@ -437,29 +474,37 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_q_sample(QArgs q) {
         const uint32_t nb = min(bsz, n_roots - base);
         // lane k < nb: component base + k, its size, member offset and source
         // (accumulator slot of a large component, else its first member)
-        uint32_t m_c = 0, m_cnt = 0, m_src = 0;
+        // (a final component, one that sampled EMPTY and that no sampled edge
+        // touched since, reports EMPTY again without a fetch)
+        uint32_t m_c = 0, m_cnt = 0, m_src = 0, m_live = 0;
         if (lane < nb) {
             m_c = q.roots[base + lane];
             m_cnt = q.count[m_c];
             const uint32_t off = q.off[m_c], sl = q.slot[m_c];
+            m_live = q.final[m_c] == 0;
             m_src = m_cnt > q.M ? sl : q.members[off];
         }
         {
             const uint32_t cnt = __shfl_sync(0xffffffffu, m_cnt, 0), src = __shfl_sync(0xffffffffu, m_src, 0);
-            fetch(bufs, single_src(cnt, src));
+            if (__shfl_sync(0xffffffffu, m_live, 0)) fetch(bufs, single_src(cnt, src));
             cp_async_commit();
         }
         for (uint32_t k = 0; k < nb; ++k) {
             const uint32_t c = __shfl_sync(0xffffffffu, m_c, k);
             const uint32_t cnt = __shfl_sync(0xffffffffu, m_cnt, k);
             const uint32_t src = __shfl_sync(0xffffffffu, m_src, k);
+            const bool live = __shfl_sync(0xffffffffu, m_live, k) != 0;
             // prefetch the next component of the batch into the other buffer
             // (its previous contents were consumed before the last __syncwarp)
             const uint32_t kn = k + 1 < nb ? k + 1 : k;
             const uint32_t cnt_n = __shfl_sync(0xffffffffu, m_cnt, kn);
             const uint32_t src_n = __shfl_sync(0xffffffffu, m_src, kn);
-            if (k + 1 < nb) fetch(bufs + ((k + 1) & 1) * stride, single_src(cnt_n, src_n));
+            const uint32_t live_n = __shfl_sync(0xffffffffu, m_live, kn);
+            if (k + 1 < nb && live_n) fetch(bufs + ((k + 1) & 1) * stride, single_src(cnt_n, src_n));
             cp_async_commit();
+            bool nz = false;
+            int64_t result = -1;  // warp-uniform
+            if (live) {
             uint64_t* cube = bufs + (k & 1) * stride + lead(single_src(cnt, src));
             const uint32_t* cube_g = reinterpret_cast<const uint32_t*>(cube + GZ_COLS * R);
             cp_async_wait<1>();  // component k's copies are done (this lane's) ...
@@ -473,8 +518,6 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_q_sample(QArgs q) {
                 }
             }
             __syncwarp();
-            bool nz = false;
-            int64_t result = -1;  // warp-uniform
             // columns in order; a column's rows come from the buffer only when
             // it is scanned (most components stop at the first column)
             for (int j = 0; j < GZ_COLS; ++j) {
@@ -531,6 +574,7 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_q_sample(QArgs q) {
                 }
             }
             __syncwarp();  // this buffer may be refilled by the next prefetch
+            }  // live
             if (lane == 0) {
                 int64_t r;
                 if (result >= 0) {
@@ -541,6 +585,7 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_q_sample(QArgs q) {
                     atomicAdd(&q.ctr[C_FAILS], 1u);
                 } else {
                     r = -1;
+                    if (live) q.final[c] = 1;  // EMPTY: final until a sampled edge touches it
                 }
                 q.res[c] = r;
                 if (q.trace) q.trace[(uint64_t)round * q.V + c] = r;
@@ -560,6 +605,8 @@ __global__ void k_q_link(QArgs q) {
         decode_edge(q, (uint64_t)r, uu, vv);
         const uint32_t a = q.label[uu], b = q.label[vv];
         const uint32_t t = a == c ? b : a;
+        q.final[a] = 0;  // both components take part in a merge
+        q.final[b] = 0;
         q.target[c] = t;
         dsu_unite(q.parent, c, t);
     }
@@ -666,6 +713,7 @@ gz_status query_setup(gz_handle* h) {
     for (auto p : arrs)
         if (e == cudaSuccess) e = alloc32(p, V);
     if (e == cudaSuccess) e = alloc32(&h->q_count, V + 1);
+    if (e == cudaSuccess) e = alloc32(&h->q_final, V);
     if (e == cudaSuccess) e = alloc32(&h->q_off, V + 1);
     if (e == cudaSuccess) e = alloc32(&h->q_pos, V + 1);
     if (e == cudaSuccess) e = alloc32(&h->q_forest, 2 * V);
@@ -738,13 +786,13 @@ static QArgs query_args(gz_handle* h) {
     q.K = h->K;
     q.R = h->R;
     q.M = kSlotAbove;
-    q.merge_per_block = 1;  // set where the merge is enqueued
     q.label = h->q_label;
     q.parent = h->q_parent;
     q.count = h->q_count;
     q.off = h->q_off;
     q.cursor = h->q_cursor;
     q.members = h->q_members;
+    q.final = h->q_final;
     q.roots = h->q_roots;
     q.target = h->q_target;
     q.slot = h->q_slot;
@@ -777,9 +825,7 @@ static void enqueue_grouping(gz_handle* h, const QArgs& q, cudaStream_t stm) {
     // wave of blocks
     const uint32_t mt = merge_threads(h->R);
     const uint32_t nblk = std::max<uint32_t>(1, std::min<uint32_t>((V + 31) / 32, h->sm_count * h->q_merge_occ));
-    QArgs qm = q;
-    qm.merge_per_block = (V + nblk - 1) / nblk;
-    k_q_merge<<<nblk, mt, 0, stm>>>(qm);
+    k_q_merge<<<nblk, mt, 0, stm>>>(q);
 }
 
 // u64 words per lane of the sampler's staging loads

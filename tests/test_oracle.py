@@ -610,3 +610,19 @@ def test_boruvka_empty_component_is_final():
     A, G = oracle.ingest(V, 3, u, v)
     res = oracle.boruvka(V, 3, A, G)
     assert res["labels"][9] == 5 and res["labels"][21] == 20
+
+
+def test_xor_of_every_node_sketch_is_zero():
+    """Every edge index lands in the same bucket of both endpoints' sketches
+    (depth and checksum depend on the index and the column only), so the XOR
+    of all node sketches is zero for any stream; the query merges a component
+    of more than V/2 members as the XOR of the nodes outside it."""
+    V = 300
+    u, v = S.random_stream(V, 5000, seed=17, n_distinct=2000)
+    A, G = oracle.ingest(V, 8, u, v)
+    assert np.any(A) and np.any(G)
+    assert not np.any(np.bitwise_xor.reduce(A, axis=0))
+    assert not np.any(np.bitwise_xor.reduce(G, axis=0))
+    # and a strict subset's XOR equals its complement's
+    inside = np.arange(V) < 200
+    assert np.array_equal(np.bitwise_xor.reduce(A[inside], axis=0), np.bitwise_xor.reduce(A[~inside], axis=0))
