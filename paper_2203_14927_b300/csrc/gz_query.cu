@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kTpb) k_q_roots(QArgs q) {
 // blocks (slots are zero between rounds); the giant's part is XORed in once
 // per block.
 constexpr uint32_t kMergeMaxThreads = 704;  // 21R/2 words rounded up to a warp, R <= 64
-constexpr uint32_t kMergeDepth = 12;
+constexpr uint32_t kMergeDepth = 10;
 constexpr uint32_t kWhole = 0x80000000u;    // slot flag: the component lies in this block
 constexpr uint32_t kNone = 0xffffffffu;     // no slot of its own (node read for the giant only)
 constexpr uint32_t kSkip = 0xfffffffeu;     // node not read at all
@@ -477,7 +477,10 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_q_sample(QArgs q) {
         // (a final component, one that sampled EMPTY and that no sampled edge
         // touched since, reports EMPTY again without a fetch)
         uint32_t m_c = 0, m_cnt = 0, m_src = 0, m_live = 0;
-        if (lane < nb) {
+        if (lane < nb && round == 0) {  // round 0: every vertex is its own live component
+            m_c = m_src = base + lane;
+            m_cnt = m_live = 1;
+        } else if (lane < nb) {
             m_c = q.roots[base + lane];
             m_cnt = q.count[m_c];
             const uint32_t off = q.off[m_c], sl = q.slot[m_c];
