@@ -275,9 +275,10 @@ gz_status gz_profile_read(gz_handle *h, gz_profile *out);
  *     otherwise it waits; a closed graph gives its memory back when its last
  *     request is done;
  *   - eviction: when a graph has waited 20 ms for memory, the least recently
- *     used resident graph with no pending request is checkpointed into
- *     pinned host memory (gz_checkpoint) and its device memory freed; its
- *     next request restores it (gz_restore), bit for bit;
+ *     used resident graph with no pending request (and all its sketches in
+ *     HBM) has its sketches copied into pinned host memory (a pool of 256 MB
+ *     chunks kept until gz_server_destroy) and its device memory freed; its
+ *     next request restores them into a fresh handle, bit for bit;
  *   - continuous batching: `slots` workers, each a host thread with its own
  *     CUDA stream, repeatedly take a resident graph with pending requests
  *     (oldest request first; finishing resident graphs is what frees memory),

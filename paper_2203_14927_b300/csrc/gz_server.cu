@@ -50,6 +50,7 @@ enum GraphState { WAITING = 0, RESIDENT = 1, RELEASED = 2, EVICTED = 3 };
 
 // a graph that cannot be admitted for this long evicts an idle resident one
 constexpr double kEvictAfterMs = 20.0;
+constexpr size_t kPinChunk = size_t(256) << 20;
 
 struct Graph {
     uint32_t V = 0;
@@ -62,8 +63,7 @@ struct Graph {
     gz_handle* h = nullptr;
     std::deque<Request> queue;
     double last_used_ms = 0;         // end of its last service
-    void* ckpt = nullptr;            // pinned host checkpoint of an evicted graph
-    size_t ckpt_bytes = 0;
+    std::vector<void*> chunks;       // an evicted graph's sketches, in pinned host chunks
     uint64_t evictions = 0;
 };
 
@@ -83,9 +83,10 @@ struct gz_server {
     uint64_t resident_bytes = 0, peak_bytes = 0, completed = 0, evictions = 0;
     uint64_t evicting_bytes = 0;  // resident bytes of graphs being checkpointed out
     double evict_ms = 0, restore_ms = 0;
-    // pinned checkpoint buffers of released graphs, kept for later evictions
-    // (pinning host memory costs far more than the copy into it)
-    std::vector<std::pair<void*, size_t>> spare_ckpt;
+    // pinned host memory for evicted sketches, in chunks of kPinChunk bytes
+    // shared by every graph and kept until the server is destroyed (pinning
+    // host memory costs far more than the copy into it)
+    std::vector<void*> pin_free, pin_all;
     uint64_t outstanding = 0;  // submitted, not completed
     uint32_t busy_workers = 0;
     bool stop = false;
@@ -119,7 +120,7 @@ Task pick(gz_server* s, uint32_t* gid) {
         Graph* g = s->graphs[i].get();
         if (g->busy || g->state == RELEASED) continue;
         if (g->queue.empty()) {
-            if (g->state == RESIDENT && !g->closed &&
+            if (g->state == RESIDENT && !g->closed && g->h && !g->h->tiered &&
                 (lru < 0 || g->last_used_ms < s->graphs[lru]->last_used_ms))
                 lru = (int)i;
             continue;
@@ -154,44 +155,81 @@ Task pick(gz_server* s, uint32_t* gid) {
     return NONE;
 }
 
-// Checkpoint an idle resident graph to pinned host memory and free its
-// device memory (outside the lock; the graph is marked busy).
-gz_status evict(gz_server* s, Graph* g) {
-    size_t need = 0;
-    gz_status st = gz_checkpoint_bytes(g->h, &need);
-    if (st == GZ_OK && g->ckpt_bytes < need) {
-        void* old = g->ckpt;
-        const size_t old_bytes = g->ckpt_bytes;
-        g->ckpt = nullptr;
-        g->ckpt_bytes = 0;
-        {  // the smallest spare buffer that fits, else a new one
-            std::lock_guard<std::mutex> lk(s->mu);
-            if (old) s->spare_ckpt.emplace_back(old, old_bytes);
-            int best = -1;
-            for (size_t i = 0; i < s->spare_ckpt.size(); ++i)
-                if (s->spare_ckpt[i].second >= need &&
-                    (best < 0 || s->spare_ckpt[i].second < s->spare_ckpt[best].second))
-                    best = (int)i;
-            if (best >= 0) {
-                g->ckpt = s->spare_ckpt[best].first;
-                g->ckpt_bytes = s->spare_ckpt[best].second;
-                s->spare_ckpt.erase(s->spare_ckpt.begin() + best);
-            }
-        }
-        if (!g->ckpt) {
-            if (cudaMallocHost(&g->ckpt, need) != cudaSuccess) {
-                g->ckpt = nullptr;
-                return GZ_ENOMEM;
-            }
-            g->ckpt_bytes = need;
+// n pinned chunks: spare ones first, new ones for the rest
+bool take_chunks(gz_server* s, size_t n, std::vector<void*>& out) {
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        while (out.size() < n && !s->pin_free.empty()) {
+            out.push_back(s->pin_free.back());
+            s->pin_free.pop_back();
         }
     }
-    if (st == GZ_OK) st = gz_checkpoint(g->h, g->ckpt, g->ckpt_bytes);
-    if (st == GZ_OK) {
-        gz_destroy(g->h);
+    while (out.size() < n) {
+        void* p = nullptr;
+        if (cudaMallocHost(&p, kPinChunk) != cudaSuccess) return false;
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->pin_all.push_back(p);
+        out.push_back(p);
+    }
+    return true;
+}
+
+void give_chunks(gz_server* s, std::vector<void*>& chunks) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (void* p : chunks) s->pin_free.push_back(p);
+    chunks.clear();
+}
+
+// Copy an idle resident graph's sketches into pinned host chunks and free its
+// device memory (outside the lock; the graph is marked busy).  The graph's
+// stream is idle and its last request's status already reported.
+gz_status evict_graph(gz_server* s, Graph* g) {
+    gz_handle* h = g->h;
+    gz_status st = gz_sync(h);
+    if (st != GZ_OK) return st;
+    const size_t bytes = (size_t)h->V * h->node_bytes;
+    std::vector<void*> ch;
+    if (!take_chunks(s, (bytes + kPinChunk - 1) / kPinChunk, ch)) {
+        give_chunks(s, ch);
+        return GZ_ENOMEM;
+    }
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < ch.size() && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(ch[i], h->d_sketch + i * kPinChunk, std::min(kPinChunk, bytes - i * kPinChunk),
+                            cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        give_chunks(s, ch);
+        return GZ_ECUDA;
+    }
+    g->chunks = std::move(ch);
+    gz_destroy(h);
+    g->h = nullptr;
+    return GZ_OK;
+}
+
+// A fresh handle with the evicted graph's sketches (same V, seed and
+// configuration, so the same hash keys); the chunks go back to the pool.
+gz_status restore_graph(gz_server* s, Graph* g, cudaStream_t stream) {
+    gz_status st = gz_create(g->V, g->seed, g->has_cfg ? &g->cfg : nullptr, stream, &g->h);
+    if (st != GZ_OK) {
         g->h = nullptr;
+        return st;
     }
-    return st;
+    gz_handle* h = g->h;
+    const size_t bytes = (size_t)h->V * h->node_bytes;
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < g->chunks.size() && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(h->d_sketch + i * kPinChunk, g->chunks[i], std::min(kPinChunk, bytes - i * kPinChunk),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        gz_destroy(h);
+        g->h = nullptr;
+        return GZ_ECUDA;
+    }
+    give_chunks(s, g->chunks);
+    return GZ_OK;
 }
 
 void worker_main(gz_server* s, int slot) {
@@ -221,7 +259,7 @@ void worker_main(gz_server* s, int slot) {
                 lk.unlock();
                 gz_set_stream(g->h, stream);
                 const double te = s->now_ms();
-                const gz_status est = evict(s, g);
+                const gz_status est = evict_graph(s, g);
                 lk.lock();
                 s->evict_ms += s->now_ms() - te;
                 g->busy = false;
@@ -234,9 +272,8 @@ void worker_main(gz_server* s, int slot) {
                     ++s->evictions;
                     if (g->closed && g->queue.empty()) {  // closed while it was copied out
                         g->state = RELEASED;
-                        s->spare_ckpt.emplace_back(g->ckpt, g->ckpt_bytes);
-                        g->ckpt = nullptr;
-                        g->ckpt_bytes = 0;
+                        for (void* p : g->chunks) s->pin_free.push_back(p);
+                        g->chunks.clear();
                     }
                 } else {
                     s->last_err = "eviction of graph " + std::to_string(gid) + " failed";
@@ -265,8 +302,7 @@ void worker_main(gz_server* s, int slot) {
             if (create_st != GZ_OK) g->h = nullptr;
         } else if (restore) {
             const double tr = s->now_ms();
-            create_st = gz_restore(g->ckpt, g->ckpt_bytes, g->has_cfg ? &g->cfg : nullptr, stream, &g->h);
-            if (create_st != GZ_OK) g->h = nullptr;
+            create_st = restore_graph(s, g, stream);
             std::lock_guard<std::mutex> lk(s->mu);
             s->restore_ms += s->now_ms() - tr;
         } else if (g->h) {
@@ -351,9 +387,8 @@ void worker_main(gz_server* s, int slot) {
                 g->state = RELEASED;
                 to_free = g->h;
                 g->h = nullptr;
-                if (g->ckpt) s->spare_ckpt.emplace_back(g->ckpt, g->ckpt_bytes);
-                g->ckpt = nullptr;
-                g->ckpt_bytes = 0;
+                for (void* p : g->chunks) s->pin_free.push_back(p);
+                g->chunks.clear();
             }
         }
         if (to_free) gz_destroy(to_free);
@@ -422,11 +457,9 @@ gz_status gz_server_destroy(gz_server* s) {
     }
     s->work_cv.notify_all();
     for (std::thread& t : s->workers) t.join();
-    for (auto& g : s->graphs) {
+    for (auto& g : s->graphs)
         if (g->h) gz_destroy(g->h);
-        if (g->ckpt) cudaFreeHost(g->ckpt);
-    }
-    for (auto& b : s->spare_ckpt) cudaFreeHost(b.first);
+    for (void* p : s->pin_all) cudaFreeHost(p);
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
     delete s;
     return GZ_OK;
@@ -515,9 +548,8 @@ gz_status gz_server_close_graph(gz_server* s, uint32_t graph) {
             g->state = RELEASED;
             to_free = g->h;
             g->h = nullptr;
-            if (g->ckpt) s->spare_ckpt.emplace_back(g->ckpt, g->ckpt_bytes);
-            g->ckpt = nullptr;
-            g->ckpt_bytes = 0;
+            for (void* p : g->chunks) s->pin_free.push_back(p);
+            g->chunks.clear();
         }
     }
     if (to_free) gz_destroy(to_free);
