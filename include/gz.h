@@ -367,9 +367,7 @@ gz_status gz_server_stats_read(gz_server *s, gz_server_stats *out);
 /* Change the HBM budget while the server runs.  A smaller budget than the
  * bytes now resident makes admissions wait (and idle graphs be evicted) until
  * the total fits; graphs registered with more bytes than the new budget wait
- * until it grows again.  Pinned checkpoint buffers of released graphs are
- * kept for later evictions until the server is destroyed.  GZ_EINVAL for a
- * zero budget. */
+ * until it grows again.  GZ_EINVAL for a zero budget. */
 gz_status gz_server_set_budget(gz_server *s, uint64_t hbm_budget);
 
 /* Reason of the most recent failed request ("" if none); valid until the next
