@@ -7,7 +7,9 @@
 //   merge    component sketch = XOR of the members' CubeSketch r, in an
 //            accumulator slot per component of two or more members (a
 //            block stores a component it holds whole and XORs its part of
-//            one that spans blocks in with atomics);
+//            one that spans blocks in with atomics); the largest component,
+//            once it holds more than V/8 nodes, as the XOR of every node
+//            outside it (the XOR of all node sketches is zero);
 //   sample   nested rows by suffix XOR, then the first bucket in the scan
 //            order of Fig. cube_code (columns, then rows ascending) that passes
 //            the checksum, decodes to an edge u < v < V and leaves the component;
@@ -18,7 +20,9 @@
 //            component id rejects exactly, per cycle, the edge of the cycle's
 //            largest component; cycles are found by pointer doubling with a
 //            running maximum.
-// A round that samples no edge ends the query.
+// A round that samples no edge ends the query.  A component whose sketch is
+// all zero (EMPTY) is final: later rounds report EMPTY for it without a merge
+// or a sample, until a sampled edge touches it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
