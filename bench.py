@@ -775,7 +775,8 @@ def serve_pass(srv, graphs, events, torch, gz, graph_cfg=None, one_at_a_time=Fal
            "query_p50_ms": float(np.percentile(q, 50)), "query_p99_ms": float(np.percentile(q, 99)),
            "queries": len(q), "requests": len(done), "errors": bad,
            "budget_gb": st["budget_bytes"] / 1e9, "evictions": st["evictions"] - st0["evictions"],
-           "evict_ms": st["evict_ms"] - st0["evict_ms"], "restore_ms": st["restore_ms"] - st0["restore_ms"]}
+           "evict_ms": st["evict_ms"] - st0["evict_ms"], "restore_ms": st["restore_ms"] - st0["restore_ms"],
+           "pinned_gb_new": (st["pinned_chunks"] - st0["pinned_chunks"]) * 0.25 * 2 ** 30 / 1e9}
     if bad:
         out["last_error"] = err
     return out
@@ -794,7 +795,10 @@ def serve_measure(graphs, budget_gb: float, slots: int, torch, gz, graph_cfg=Non
     ample = int(1.5 * foot) + (8 << 30)
     total_updates = sum(len(g["u"]) for g in graphs)
     events0 = serve_schedule(graphs, 1.0)
-    srv = gz.Server(hbm_budget=ample, slots=slots, max_batch=8)
+    # pinned host memory for two of the largest graphs' sketches, pinned before
+    # the passes (a server that has run a while holds such a pool)
+    big = max(gz.memory_bytes(g["V"], chunk_log2=20, no_pipeline=1) for g in graphs)
+    srv = gz.Server(hbm_budget=ample, slots=slots, max_batch=8, host_pool_mb=int(2 * big / 2 ** 20) + 256)
     try:
         serve_pass(srv, graphs, events0, torch, gz, graph_cfg)  # warm-up
         srv.set_budget(budget)

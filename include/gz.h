@@ -300,7 +300,9 @@ typedef struct {
     uint64_t hbm_budget; /* device bytes the server may hold for graphs (0 = 80% of free memory) */
     uint32_t slots;      /* worker threads / CUDA streams (0 = 4) */
     uint32_t max_batch;  /* most requests one worker takes from a graph at a time (0 = 64) */
-    uint32_t reserved[6];
+    uint32_t host_pool_mb; /* pinned host memory for evictions to pin at creation (pinning
+                              runs at a few GB/s; 0 = pin on demand) */
+    uint32_t reserved[5];
 } gz_server_config;
 
 typedef struct {
@@ -319,7 +321,7 @@ typedef struct {
     uint64_t completed_requests;
     uint64_t evictions;      /* graphs checkpointed to host memory to make room */
     uint32_t evicted_graphs; /* graphs held in host memory now */
-    uint32_t reserved;
+    uint32_t pinned_chunks;  /* 256 MB pinned host chunks the server holds for evictions */
     double evict_ms;         /* host time spent checkpointing evicted graphs out */
     double restore_ms;       /* host time spent restoring them */
 } gz_server_stats;

@@ -499,7 +499,7 @@ class DeviceKronStream:
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_uint64), ("slots", ctypes.c_uint32), ("max_batch", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 6)]
+                ("host_pool_mb", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
 
 
 class Completion(ctypes.Structure):
@@ -513,7 +513,7 @@ class ServerStats(ctypes.Structure):
                 ("budget_bytes", ctypes.c_uint64), ("graphs", ctypes.c_uint32),
                 ("resident_graphs", ctypes.c_uint32), ("waiting_graphs", ctypes.c_uint32),
                 ("pending_requests", ctypes.c_uint32), ("completed_requests", ctypes.c_uint64),
-                ("evictions", ctypes.c_uint64), ("evicted_graphs", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("evictions", ctypes.c_uint64), ("evicted_graphs", ctypes.c_uint32), ("pinned_chunks", ctypes.c_uint32),
                 ("evict_ms", ctypes.c_double), ("restore_ms", ctypes.c_double)]
 
 
@@ -521,9 +521,9 @@ class Server:
     """Many graphs resident on the current device (gz_server_* in include/gz.h):
     admission by an HBM budget, `slots` concurrent workers (streams)."""
 
-    def __init__(self, hbm_budget: int = 0, slots: int = 0, max_batch: int = 0):
+    def __init__(self, hbm_budget: int = 0, slots: int = 0, max_batch: int = 0, host_pool_mb: int = 0):
         cfg = ServerConfig()
-        cfg.hbm_budget, cfg.slots, cfg.max_batch = hbm_budget, slots, max_batch
+        cfg.hbm_budget, cfg.slots, cfg.max_batch, cfg.host_pool_mb = hbm_budget, slots, max_batch, host_pool_mb
         self._s = ctypes.c_void_p()
         st = lib().gz_server_create(ctypes.byref(cfg), ctypes.byref(self._s))
         if st != GZ_OK:

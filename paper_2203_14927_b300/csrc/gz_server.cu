@@ -433,6 +433,17 @@ gz_status gz_server_create(const gz_server_config* cfg, gz_server** out) {
         if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) == cudaSuccess && cur < keep)
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
+    // pinned chunks for evictions, pinned now rather than under load
+    for (uint64_t b = 0; b < (uint64_t)s->cfg.host_pool_mb << 20; b += kPinChunk) {
+        void* p = nullptr;
+        if (cudaMallocHost(&p, kPinChunk) != cudaSuccess) {
+            for (void* q : s->pin_all) cudaFreeHost(q);
+            delete s;
+            return GZ_ENOMEM;
+        }
+        s->pin_all.push_back(p);
+        s->pin_free.push_back(p);
+    }
     s->t0 = Clock::now();
     for (uint32_t i = 0; i < s->cfg.slots; ++i) {
         cudaStream_t st;
@@ -618,6 +629,7 @@ gz_status gz_server_stats_read(gz_server* s, gz_server_stats* out) {
     out->completed_requests = s->completed;
     out->evictions = s->evictions;
     out->evict_ms = s->evict_ms;
+    out->pinned_chunks = (uint32_t)s->pin_all.size();
     out->restore_ms = s->restore_ms;
     return GZ_OK;
 }
