@@ -313,3 +313,33 @@ def test_queries_during_the_stream_see_each_prefix():
         assert np.array_equal(labels, want["labels"]), i
         assert np.array_equal(labels, oracle.brute_cc(spec.V, u[:cuts[i]], v[:cuts[i]])), i
     _assert_same_sketches(g, A, G)
+
+
+def test_empty_component_stays_final_on_the_device():
+    """The rule that a component sampled EMPTY is final, on the device: with
+    the round-0 CubeSketches of 5 and 9 cleared in the device sketch array
+    (and in the oracle's copy), the pair reports EMPTY in round 1 too and
+    stays apart, sample for sample as the oracle does."""
+    import torch
+
+    class _Bytes:
+        def __init__(self, ptr, nbytes):
+            self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False),
+                                             "version": 3}
+
+    V, seed = 64, 3
+    u = np.array([5, 20], np.uint32)
+    v = np.array([9, 21], np.uint32)
+    A, G = oracle.ingest(V, seed, u, v)
+    A[[5, 9], 0] = 0
+    G[[5, 9], 0] = 0
+    g = _gpu_graph(V, seed, u, v)
+    info = g.info()
+    for node in (5, 9):  # CubeSketch 0 is the first 84R bytes of a node's sketch
+        t = torch.as_tensor(_Bytes(info["sketch_ptr"] + node * info["node_bytes"], 84 * info["R"]),
+                            device="cuda")
+        t.zero_()
+    torch.cuda.synchronize()
+    want = _assert_same_query(g, A, G, seed)
+    assert want["labels"][9] == 9 and want["labels"][21] == 20
+    assert want["samples"][1][5] == -1 and want["samples"][1][9] == -1
