@@ -32,3 +32,16 @@ def test_wide_segment_fraction_counts_records_of_high_nodes():
         got = bench.wide_segment_fraction(torch.from_numpy(u.astype(np.int32)),
                                           torch.from_numpy(v.astype(np.int32)), V, torch, block=555)
         assert abs(got - want) < 1e-12, V
+
+
+def test_serve_schedule_orders_each_graph_and_closes_it_last():
+    # two synthetic graphs: cut points of their update chunks
+    graphs = [{"cuts": [10, 25, 40]}, {"cuts": [7]}]
+    ev = bench.serve_schedule(graphs, 2.0)
+    assert [e[0] for e in ev] == sorted(e[0] for e in ev)
+    for gi, g in enumerate(graphs):
+        mine = [e for e in ev if e[1] == gi]
+        ups = [(e[3], e[4]) for e in mine if e[2] == "u"]
+        assert ups == list(zip([0] + g["cuts"][:-1], g["cuts"]))  # chunks in order, covering the stream
+        assert mine[-1][2] == "close" and mine[-2][2] == "q"      # a final query, then the close
+    assert bench.serve_schedule(graphs, 2.0) == ev                 # seeded
