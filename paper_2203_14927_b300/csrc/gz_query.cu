@@ -474,6 +474,7 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_q_sample(QArgs q) {
     // components per warp batch: up to kSampleBatch, fewer when the warps
     // outnumber the batches (late rounds have few components)
     const uint32_t bsz = max(1u, min(kSampleBatch, n_roots / nwarps));
+    uint32_t n_edges = 0, n_fails = 0;  // lane 0: this warp's sampled edges and FAIL results
     for (uint32_t base = warp * bsz; base < n_roots; base += nwarps * bsz) {
         const uint32_t nb = min(bsz, n_roots - base);
         // lane k < nb: component base + k, its size, member offset and source
@@ -586,10 +587,10 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_q_sample(QArgs q) {
                 int64_t r;
                 if (result >= 0) {
                     r = result;
-                    atomicAdd(&q.ctr[C_EDGES], 1u);
+                    ++n_edges;
                 } else if (nz) {
                     r = -2;
-                    atomicAdd(&q.ctr[C_FAILS], 1u);
+                    ++n_fails;
                 } else {
                     r = -1;
                     if (live) q.final[c] = 1;  // EMPTY: final until a sampled edge touches it
@@ -600,6 +601,10 @@ __global__ void __launch_bounds__(kSampleThreads, 4) k_q_sample(QArgs q) {
         }
         cp_async_wait<0>();
     }
+    // the round's counters once per warp (one atomic per component on the
+    // same two words would serialise in the L2)
+    if (lane == 0 && n_edges) atomicAdd(&q.ctr[C_EDGES], n_edges);
+    if (lane == 0 && n_fails) atomicAdd(&q.ctr[C_FAILS], n_fails);
 }
 
 __global__ void k_q_link(QArgs q) {
