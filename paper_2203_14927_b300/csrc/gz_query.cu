@@ -246,32 +246,41 @@ __global__ void __launch_bounds__(kGroupThreads) k_q_group(QArgs q) {
 constexpr uint32_t kTpb = 256;
 
 __global__ void __launch_bounds__(kTpb) k_q_roots(QArgs q) {
-    __shared__ uint32_t s_warp[kTpb / 32];
-    __shared__ uint32_t s_base;
+    __shared__ uint32_t s_warp[kTpb / 32], s_wbig[kTpb / 32];
+    __shared__ uint32_t s_base, s_bbase;
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, round = q.ctr[C_ROUND];
+    const uint32_t below = (1u << lane) - 1u;
     for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x; b < q.V; b += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t c64 = b + threadIdx.x;
         const uint32_t c = (uint32_t)c64;  // used only where c64 < V
         const uint32_t cnt = c64 < q.V ? q.count[c] : 0u;
+        const bool big = cnt > q.M && !q.final[c];
         const uint32_t bal = __ballot_sync(0xffffffffu, cnt > 0);
-        if (lane == 0) s_warp[wid] = __popc(bal);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t tot = 0;
-            for (uint32_t w = 0; w < kTpb / 32; ++w) {
-                const uint32_t n = s_warp[w];
-                s_warp[w] = tot;
-                tot += n;
-            }
-            s_base = tot ? atomicAdd(&q.ctr[C_ROOTS], tot) : 0u;
+        const uint32_t bbal = __ballot_sync(0xffffffffu, big);
+        if (lane == 0) {
+            s_warp[wid] = __popc(bal);
+            s_wbig[wid] = __popc(bbal);
         }
         __syncthreads();
-        if (cnt > 0) q.roots[s_base + s_warp[wid] + __popc(bal & ((1u << lane) - 1u))] = c;
-        if (cnt > q.M && !q.final[c]) q.slot[c] = atomicAdd(&q.ctr[C_BIG], 1u);
-        if (cnt > q.M && cnt > q.V / 8 && !q.final[c])  // the largest, ties to the smallest id
+        if (threadIdx.x == 0) {  // one reservation per block for roots and for slots
+            uint32_t tot = 0, btot = 0;
+            for (uint32_t w = 0; w < kTpb / 32; ++w) {
+                const uint32_t n = s_warp[w], nb = s_wbig[w];
+                s_warp[w] = tot;
+                s_wbig[w] = btot;
+                tot += n;
+                btot += nb;
+            }
+            s_base = tot ? atomicAdd(&q.ctr[C_ROOTS], tot) : 0u;
+            s_bbase = btot ? atomicAdd(&q.ctr[C_BIG], btot) : 0u;
+        }
+        __syncthreads();
+        if (cnt > 0) q.roots[s_base + s_warp[wid] + __popc(bal & below)] = c;
+        if (big) q.slot[c] = s_bbase + s_wbig[wid] + __popc(bbal & below);
+        if (big && cnt > q.V / 8)  // the largest, ties to the smallest id
             atomicMax(giant_word(q.ctr), ((unsigned long long)cnt << 32) | (uint32_t)~c);
         if (c64 < q.V && cnt == 0 && q.trace) q.trace[(uint64_t)round * q.V + c] = -3;
-        __syncthreads();  // s_warp and s_base are reused
+        __syncthreads();  // the shared counters are reused
     }
 }
 
